@@ -1,0 +1,520 @@
+"""FP64 CPU oracle for array BP-XOR coded matrix multiplication.
+
+TEST INFRASTRUCTURE ONLY.  This module is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py``.  The product path (the ``paper_1904_11563_gb300``
+package and its CUDA library) never imports, links or executes anything here,
+and this module imports nothing from the product.
+
+What it computes (Arslan, "Array BP-XOR Codes for Hierarchically Distributed
+Matrix Multiplication"):
+
+* code graphs -- the literal array codes of Table I and Table III
+  (Section III-A), the projection-geometry (Mojette) codes of Section III-C
+  built bin by bin from Eq. (moj1) with Construction A (option1) and
+  Construction B (option2), and a systematic Mojette array (k data columns
+  plus projection parities);
+* the belief-propagation (peeling) decoder of Section I-A, both as the
+  sequential one-node-at-a-time procedure the paper describes and as the
+  parallel "wave" reading used as the schedule contract (resolver = lowest
+  cell id among the cells that have exactly one unknown source at the start
+  of a round; sources of a round evaluated in ascending id);
+* the numeric path over real matrices: encode A_c = sum of the row blocks in
+  the support of cell c (XOR read as +), products P_c = A_c B, and the peel
+  C_s = P_r - sum_{t in supp(r), t != s} C_t (XOR read as -), all in FP64;
+* the uncoded reference C = A B and, per source, the integer expansion of
+  C_s over the surviving products with its amplification factor.
+
+Every function cites the passage it follows.  Nothing here is blocked, fused
+or reordered beyond what the definition states; a library primitive (numpy's
+FP64 matmul) serves as the product step.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Code graphs
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Code:
+    """A binary linear array code as a bipartite graph (Section I-A, III-A).
+
+    ``cells[c]`` is the sorted tuple of source ids XORed (here: summed) into
+    coded symbol ``c``; ``col_of_cell[c]`` is the code column (worker node)
+    holding it.  Cells are numbered column-major: column ascending, then
+    processor row / bin label ascending, empty bins dropped.
+    """
+
+    name: str
+    n: int
+    k: int
+    b: int
+    num_sources: int
+    cells: list
+    col_of_cell: list
+    # Per column: nominal height (Mojette b_i of Section III-C; array codes: b)
+    heights: list
+    # Per column: projection (p, q), or None for a data / literal column
+    proj: list = field(default_factory=list)
+    e: int = 0
+
+    @property
+    def num_cells(self) -> int:
+        return len(self.cells)
+
+    def cells_of_column(self, j):
+        return [c for c in range(self.num_cells) if self.col_of_cell[c] == j]
+
+    @property
+    def sigma(self) -> int:
+        """Maximum coded-symbol degree (Section III-A)."""
+        return max(len(c) for c in self.cells)
+
+    def eps(self) -> float:
+        """Worst-case coding overhead of Section III-B: over all choices of k
+        columns, (sum of their heights) / (k b) - 1.  The sum depends only on
+        the chosen heights, so the worst case is the k tallest columns."""
+        hs = sorted(self.heights, reverse=True)[: self.k]
+        return sum(hs) / (self.k * self.b) - 1.0
+
+
+def _literal_code(name, n, k, b, columns):
+    """Builds a code from columns of cells written with the paper's 1-based
+    v indices; source s = v - 1."""
+    cells, col_of_cell = [], []
+    for j, col in enumerate(columns):
+        for cell in col:
+            cells.append(tuple(sorted(v - 1 for v in cell)))
+            col_of_cell.append(j)
+    return Code(name=name, n=n, k=k, b=b, num_sources=b * k, cells=cells,
+                col_of_cell=col_of_cell, heights=[b] * n, proj=[None] * n,
+                e=n - k)
+
+
+def table1() -> Code:
+    """Table I (Example 1, Section III-A): the [5,2,2,2] code, sigma = 2,
+    four sources v1..v4 on n = 5 nodes with two processors each."""
+    columns = [
+        [(1,), (2, 3)],
+        [(2,), (1, 4)],
+        [(3,), (2, 4)],
+        [(4,), (1, 3)],
+        [(1, 2), (3, 4)],
+    ]
+    code = _literal_code("table1", 5, 2, 2, columns)
+    # The label's third entry cannot be the erasure count: the code decodes
+    # from any two of its five columns (Example 1), so t = n - k = 3.
+    code.e = 3
+    return code
+
+
+def table3() -> Code:
+    """Table III (Example 2, Section III-A): the [5,3,2,3] code, sigma = 2,
+    nine sources v1..v9 on n = 5 nodes with three processors each."""
+    columns = [
+        [(1,), (3, 4), (6, 7)],
+        [(1, 2), (4, 5), (7, 8)],
+        [(2, 3), (5, 6), (8, 9)],
+        [(7,), (9, 1), (4, 8)],
+        [(3,), (2, 6), (9, 5)],
+    ]
+    return _literal_code("table3", 5, 3, 3, columns)
+
+
+def _u(t: int) -> int:
+    """Discrete unit function of Eq. (moj1): 1 for t > 0, else 0."""
+    return 1 if t > 0 else 0
+
+
+def mojette_height(k: int, b: int, p: int, q: int) -> int:
+    """Projection length b_i = |p|(k-1) + |q|(b-1) + 1 (Section III-C)."""
+    return abs(p) * (k - 1) + abs(q) * (b - 1) + 1
+
+
+def mojette_bins(k: int, b: int, p: int, q: int):
+    """Bins of projection (p, q) of the k x b grid, from Eq. (moj1).
+
+    Pixel (z, l), z in [0, b), l in [0, k), is source s = z k + l.  The pixel
+    lands in the bin with label
+        (b-1) q u(q) + (k-1) p u(p) - z q - l p ,
+    i.e. the bin index m + (b-1) q u(q) + (k-1) p u(p) of Eq. (moj1) with the
+    Kronecker delta selecting m = -(z q + l p).  Returns a dict label -> sorted
+    list of sources (empty labels absent).
+    """
+    offset = (b - 1) * q * _u(q) + (k - 1) * p * _u(p)
+    bins: dict[int, list[int]] = {}
+    for z in range(b):
+        for l in range(k):
+            label = offset - z * q - l * p
+            bins.setdefault(label, []).append(z * k + l)
+    return {lab: sorted(v) for lab, v in bins.items()}
+
+
+def _projection_code(name, n, k, b, projections, data_columns=0, e=None):
+    """Columns: ``data_columns`` systematic columns (column l holds sources
+    z k + l, z ascending), then one column per projection with its bins in
+    ascending label order (Section III-C: each projection is a code column,
+    each bin a coded symbol)."""
+    cells, col_of_cell, heights, proj = [], [], [], []
+    j = 0
+    for l in range(data_columns):
+        for z in range(b):
+            cells.append((z * k + l,))
+            col_of_cell.append(j)
+        heights.append(b)
+        proj.append(None)
+        j += 1
+    for (p, q) in projections:
+        bins = mojette_bins(k, b, p, q)
+        for lab in sorted(bins):
+            cells.append(tuple(bins[lab]))
+            col_of_cell.append(j)
+        heights.append(mojette_height(k, b, p, q))
+        proj.append((p, q))
+        j += 1
+    assert j == n
+    return Code(name=name, n=n, k=k, b=b, num_sources=k * b, cells=cells,
+                col_of_cell=col_of_cell, heights=heights, proj=proj,
+                e=(n - k) if e is None else e)
+
+
+def construction_a_slopes(n: int):
+    """Construction A (Cons33, option1): q_i = 1 and p_i running over the n
+    consecutive integers -floor((n-1)/2) .. ceil((n-1)/2), ascending."""
+    lo = -((n - 1) // 2)
+    hi = -((-(n - 1)) // 2)  # ceil((n-1)/2)
+    ps = list(range(lo, hi + 1))
+    assert len(ps) == n
+    return [(p, 1) for p in ps]
+
+
+def construction_a(n: int, k: int, b: int) -> Code:
+    """Mojette code of Construction A on a k x b grid: any k projections
+    satisfy the Katz criterion through sum |q_i| = k, so t = n - k."""
+    return _projection_code(f"mojA_n{n}_k{k}_b{b}", n, k, b,
+                            construction_a_slopes(n), e=n - k)
+
+
+def _ceil_odd(x: int) -> int:
+    """Smallest odd integer >= x (the ceil_odd rounding of option2)."""
+    return x if x % 2 != 0 else x + 1
+
+
+def construction_b_slopes(n: int, q_e: int):
+    """Construction B (cons35, option2): q_i = 2^{q_e} and p_i the n
+    consecutive odd integers ceil_odd(-n+1), ..., ceil_odd(n-1)."""
+    lo, hi = _ceil_odd(-n + 1), _ceil_odd(n - 1)
+    ps = list(range(lo, hi + 1, 2))
+    assert len(ps) == n, (n, ps)
+    return [(p, 2 ** q_e) for p in ps]
+
+
+def construction_b(n: int, k: int, b: int, q_e: int) -> Code:
+    """Mojette code of Construction B: ceil(k / 2^{q_e}) projections satisfy
+    the Katz criterion through sum |q_i| >= k (Appendix B)."""
+    need = -(-k // (2 ** q_e))
+    return _projection_code(f"mojB_n{n}_k{k}_b{b}_q{q_e}", n, k, b,
+                            construction_b_slopes(n, q_e), e=n - need)
+
+
+def systematic_slopes(e: int):
+    """Parity slopes 0, +1, -1, +2, -2, ... with q = 1."""
+    ps = [0]
+    m = 1
+    while len(ps) < e:
+        ps.append(m)
+        if len(ps) < e:
+            ps.append(-m)
+        m += 1
+    return [(p, 1) for p in ps[:e]]
+
+
+def systematic_mojette(k: int, e: int, b: int) -> Code:
+    """Systematic Mojette array: the k x b data grid kept as k degree-one
+    columns, plus e projection parities (q = 1, slopes 0, +1, -1, ...)."""
+    return _projection_code(f"sysmoj_k{k}_e{e}_b{b}", k + e, k, b,
+                            systematic_slopes(e), data_columns=k, e=e)
+
+
+def lemma_a1_closed_form(t: int) -> int:
+    """Lemma A.1: sum of |p_i| over the t slopes of Construction A equals
+    (t^2 - 1)/4 for odd t and t^2/4 for even t."""
+    return (t * t - 1) // 4 if t % 2 else (t * t) // 4
+
+
+def lemma_b1_closed_form(t: int) -> int:
+    """Lemma B.1: sum of |p_i| over the t slopes of Construction B equals
+    (t^2 + 1)/2 for odd t and t^2/2 for even t."""
+    return (t * t + 1) // 2 if t % 2 else (t * t) // 2
+
+
+def sigma_formula(k: int, b: int, p: int, q: int) -> int:
+    """Theorem on the maximum projection degree (Section III-C):
+    sigma_i = min(ceil(b/|p|), ceil(k/|q|)), an infinite term dropped."""
+    terms = []
+    if p != 0:
+        terms.append(-(-b // abs(p)))
+    if q != 0:
+        terms.append(-(-k // abs(q)))
+    return min(terms)
+
+
+def katz_holds(k: int, b: int, projections) -> bool:
+    """Katz criterion (Section III-C): sum |p_i| >= b or sum |q_i| >= k."""
+    return (sum(abs(p) for p, _ in projections) >= b
+            or sum(abs(q) for _, q in projections) >= k)
+
+
+# --------------------------------------------------------------------------
+# Belief-propagation (peeling) decoders
+# --------------------------------------------------------------------------
+
+
+def surviving_cells(code: Code, erased_cols) -> list:
+    """Cells of the columns that did not straggle."""
+    erased = set(int(j) for j in erased_cols)
+    return [c for c in range(code.num_cells) if code.col_of_cell[c] not in erased]
+
+
+def sequential_peel(code: Code, cell_subset, pick=None) -> set:
+    """The BP decoder exactly as Section I-A describes it: start with every
+    information node NULL; repeatedly take a coded node of degree one, copy
+    it into its neighbour and remove that neighbour's edges from every coded
+    node; stop when nothing is NULL (success) or no degree-one node is left
+    (failure).  ``pick`` chooses among the current degree-one nodes (default:
+    the first); returns the set of recovered sources."""
+    residual = {c: set(code.cells[c]) for c in cell_subset}
+    known: set = set()
+    while len(known) < code.num_sources:
+        ones = [c for c, r in residual.items() if len(r) == 1]
+        if not ones:
+            break
+        c = ones[0] if pick is None else pick(ones)
+        (s,) = residual[c]
+        known.add(s)
+        for r in residual.values():
+            r.discard(s)
+    return known
+
+
+@dataclass
+class Schedule:
+    """Result of the wave peel: per source its depth (round, 0 = not
+    recovered) and resolver cell (-1 = none); ``order`` lists (s, resolver,
+    depth) sorted by (depth, s)."""
+
+    ok: bool
+    depth: list
+    resolver: list
+    order: list
+
+    @property
+    def num_waves(self) -> int:
+        return max(self.depth) if self.depth else 0
+
+    @property
+    def recovered(self) -> list:
+        return [1 if d > 0 else 0 for d in self.depth]
+
+
+def wave_schedule_naive(code: Code, cell_subset) -> Schedule:
+    """Parallel-round reading of the Section I-A decoder, written out plainly.
+
+    Round r looks at every surviving cell with exactly one unknown source at
+    the start of the round; each such source takes as resolver the lowest
+    such cell id and gets depth r.  A round that recovers nothing ends the
+    peel.  Cost O(rounds x edges): for small codes."""
+    S = code.num_sources
+    depth = [0] * S
+    resolver = [-1] * S
+    cells = sorted(cell_subset)
+    r = 0
+    while True:
+        r += 1
+        found: dict = {}
+        for c in cells:
+            unknown = [t for t in code.cells[c] if depth[t] == 0]
+            if len(unknown) == 1:
+                s = unknown[0]
+                if s not in found or c < found[s]:
+                    found[s] = c
+        if not found:
+            break
+        for s, c in found.items():
+            depth[s] = r
+            resolver[s] = c
+    order = sorted(((s, resolver[s], depth[s]) for s in range(S) if depth[s] > 0),
+                   key=lambda x: (x[2], x[0]))
+    return Schedule(ok=all(d > 0 for d in depth), depth=depth,
+                    resolver=resolver, order=order)
+
+
+def wave_schedule(code: Code, cell_subset) -> Schedule:
+    """Same contract as ``wave_schedule_naive`` but each round only revisits
+    the cells whose unknown count just dropped to one (the count of unknown
+    sources per cell is kept up to date), so large codes finish in seconds.
+    Tests pin the two against each other."""
+    S = code.num_sources
+    depth = [0] * S
+    resolver = [-1] * S
+    alive = sorted(cell_subset)
+    cells_of_src: list = [[] for _ in range(S)]
+    unknown_cnt = {}
+    for c in alive:
+        unknown_cnt[c] = len(code.cells[c])
+        for t in code.cells[c]:
+            cells_of_src[t].append(c)
+    frontier = [c for c in alive if unknown_cnt[c] == 1]
+    r = 0
+    while frontier:
+        r += 1
+        found: dict = {}
+        for c in frontier:
+            if unknown_cnt[c] != 1:
+                continue
+            unknown = [t for t in code.cells[c] if depth[t] == 0]
+            s = unknown[0]
+            if s not in found or c < found[s]:
+                found[s] = c
+        if not found:
+            break
+        nxt = []
+        for s, c in found.items():
+            depth[s] = r
+            resolver[s] = c
+        for s in found:
+            for c in cells_of_src[s]:
+                unknown_cnt[c] -= 1
+                if unknown_cnt[c] == 1:
+                    nxt.append(c)
+        frontier = nxt
+    order = sorted(((s, resolver[s], depth[s]) for s in range(S) if depth[s] > 0),
+                   key=lambda x: (x[2], x[0]))
+    return Schedule(ok=all(d > 0 for d in depth), depth=depth,
+                    resolver=resolver, order=order)
+
+
+def decodable(code: Code, erased_cols) -> bool:
+    return wave_schedule(code, surviving_cells(code, erased_cols)).ok
+
+
+# --------------------------------------------------------------------------
+# Numeric path over real matrices (XOR read as +, its inverse as -)
+# --------------------------------------------------------------------------
+
+
+def row_block(A: np.ndarray, s: int, h: int) -> np.ndarray:
+    """Source s = rows [s h, (s+1) h) of A (Remark 2.1 partitioning); rows
+    past the end of A read as zero (padding of the last blocks)."""
+    M, K = A.shape
+    out = np.zeros((h, K), dtype=np.float64)
+    lo, hi = s * h, min((s + 1) * h, M)
+    if lo < hi:
+        out[: hi - lo] = A[lo:hi]
+    return out
+
+
+def encode(code: Code, A: np.ndarray, h: int, cell: int) -> np.ndarray:
+    """Worker-side encoding (Section III-A, Example 1): the coded operand of
+    a cell is the sum of its sources' row blocks, in ascending source id,
+    in FP64 from the given inputs."""
+    A64 = np.asarray(A, dtype=np.float64)
+    acc = np.zeros((h, A64.shape[1]), dtype=np.float64)
+    for s in code.cells[cell]:
+        acc += row_block(A64, s, h)
+    return acc
+
+
+def coded_products(code: Code, A: np.ndarray, B: np.ndarray, h: int, cells):
+    """P_c = A_c B for every listed cell (the sigma dot products a processor
+    executes, Section III-A), FP64.  Returns {cell: h x N array}."""
+    B64 = np.asarray(B, dtype=np.float64)
+    return {c: encode(code, A, h, c) @ B64 for c in cells}
+
+
+def peel_decode(code: Code, products: dict, sched: Schedule, h: int, N: int):
+    """Numeric BP peel along ``sched``: for each (s, r, d) in order,
+    C_s = P_r - sum_{t in supp(r), t != s, ascending} C_t.  Returns
+    {s: h x N FP64} for the recovered sources."""
+    C: dict = {}
+    for s, r, _d in sched.order:
+        acc = products[r].copy()
+        for t in code.cells[r]:
+            if t != s:
+                acc -= C[t]
+        C[s] = acc
+    return C
+
+
+def reference_product(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """The uncoded product A B in FP64."""
+    return np.asarray(A, dtype=np.float64) @ np.asarray(B, dtype=np.float64)
+
+
+def coded_matmul(code: Code, A: np.ndarray, B: np.ndarray, h: int, erased_cols):
+    """Whole path: schedule, encode, products of the surviving cells, peel.
+    Returns (C as an (S h) x N FP64 array with unrecovered blocks NaN,
+    schedule)."""
+    cells = surviving_cells(code, erased_cols)
+    sched = wave_schedule(code, cells)
+    N = B.shape[1]
+    used = sorted(set(r for _s, r, _d in sched.order))
+    P = coded_products(code, A, B, h, used)
+    Cd = peel_decode(code, P, sched, h, N)
+    C = np.full((code.num_sources * h, N), np.nan)
+    for s, blk in Cd.items():
+        C[s * h:(s + 1) * h] = blk
+    return C, sched
+
+
+def expansion(code: Code, sched: Schedule) -> dict:
+    """Integer expansion of every recovered C_s over the products: the map
+    cell -> coefficient with C_s = sum_c coef_c P_c, following the peel."""
+    coef: dict = {}
+    for s, r, _d in sched.order:
+        e = {r: 1}
+        for t in code.cells[r]:
+            if t != s:
+                for c, v in coef[t].items():
+                    e[c] = e.get(c, 0) - v
+        coef[s] = {c: v for c, v in e.items() if v != 0}
+    return coef
+
+
+def amplification(code: Code, sched: Schedule, products: dict, C: dict) -> dict:
+    """kappa_s = sum_c |coef_{s,c}| ||P_c||_F / ||C_s||_F: how much the
+    rounding error of the products can be magnified on the way to C_s."""
+    coef = expansion(code, sched)
+    out = {}
+    for s, e in coef.items():
+        num = sum(abs(v) * np.linalg.norm(products[c]) for c, v in e.items())
+        den = np.linalg.norm(C[s])
+        out[s] = float(num / den) if den > 0 else float("inf")
+    return out
+
+
+def all_erasure_patterns(n: int, max_e: int):
+    """Every set of at most max_e erased columns."""
+    for e in range(max_e + 1):
+        yield from itertools.combinations(range(n), e)
+
+
+def reference_block(A: np.ndarray, B: np.ndarray, s: int, h: int) -> np.ndarray:
+    """C_s = A_s B in FP64 for one source (sampled checks at full size)."""
+    return row_block(np.asarray(A, dtype=np.float64), s, h) @ np.asarray(B, dtype=np.float64)
+
+
+def eps_construction_a_closed_form(n: int, k: int, b: int) -> float:
+    """Exact worst-case overhead of Construction A (Appendix A, before the
+    bounds): (k-1)/(2 k b) (phi(n) + phi(n-1) - phi(n-k) - phi(n-k-1)),
+    phi(x) = floor(x/2)(floor(x/2)+1)."""
+    def phi(x):
+        return (x // 2) * (x // 2 + 1) if x >= 0 else 0
+    return (k - 1) / (2 * k * b) * (phi(n) + phi(n - 1) - phi(n - k) - phi(n - k - 1))
+

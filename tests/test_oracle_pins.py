@@ -1,0 +1,451 @@
+"""Pins for the FP64 oracle: what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself -- a table
+or number the paper prints (tests/golden/), a closed form, an independent
+characterisation, or brute force on tiny inputs -- so that a dropped term, a
+wrong sign or index, or a transposed operand in the oracle fails here.
+"""
+import itertools
+import os
+import random
+
+import numpy as np
+import pytest
+
+from oracle import bpx_oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_table(name):
+    cols = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            _node, cells = line.split(":", 1)
+            col = []
+            for cell in cells.split(";"):
+                vs = [int(v.strip()[1:]) - 1 for v in cell.split("+")]
+                col.append(tuple(sorted(vs)))
+            cols.append(col)
+    return cols
+
+
+def _claims():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_claims.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = (x.strip() for x in line.split("=", 1))
+            out[k] = [int(x) for x in v.split(",")] if "," in v else int(v)
+    return out
+
+
+CLAIMS = _claims()
+
+
+# ---------------------------------------------------------------- Table I / III
+
+@pytest.mark.parametrize("fn,fixture", [(o.table1, "table1.txt"), (o.table3, "table3.txt")])
+def test_literal_tables_match_transcription(fn, fixture):
+    code = fn()
+    cols = _read_table(fixture)
+    assert code.n == len(cols)
+    got = [[code.cells[c] for c in code.cells_of_column(j)] for j in range(code.n)]
+    assert got == cols
+    # column-major numbering
+    assert code.col_of_cell == sorted(code.col_of_cell)
+
+
+def test_table1_any_two_columns_decode():
+    """Example 1: any two of the five nodes suffice; no single node does."""
+    code = o.table1()
+    m = CLAIMS["table1_min_columns"]
+    for keep in itertools.combinations(range(5), m):
+        erased = [j for j in range(5) if j not in keep]
+        assert o.decodable(code, erased), keep
+    for keep in itertools.combinations(range(5), m - 1):
+        erased = [j for j in range(5) if j not in keep]
+        assert not o.decodable(code, erased)
+
+
+def test_table1_recovery_threshold_is_seven():
+    """Example 1: every 7 of the 10 processor outputs decode; some 6 do not."""
+    code = o.table1()
+    thr = CLAIMS["table1_recovery_threshold"]
+    for sub in itertools.combinations(range(code.num_cells), thr):
+        assert o.wave_schedule(code, sub).ok
+    assert any(not o.wave_schedule(code, sub).ok
+               for sub in itertools.combinations(range(code.num_cells), thr - 1))
+
+
+def test_table3_block_mds():
+    """Example 2: [5,3,2,3] decodes from any 3 of its 5 columns."""
+    code = o.table3()
+    m = CLAIMS["table3_min_columns"]
+    for keep in itertools.combinations(range(5), m):
+        erased = [j for j in range(5) if j not in keep]
+        assert o.decodable(code, erased), keep
+    # and from no 2 columns (3 erasures exceed t = 2)
+    for keep in itertools.combinations(range(5), m - 1):
+        erased = [j for j in range(5) if j not in keep]
+        assert not o.decodable(code, erased)
+
+
+def test_literal_sigma():
+    assert o.table1().sigma == CLAIMS["table1_sigma"]
+    assert o.table3().sigma == CLAIMS["table3_sigma"]
+
+
+# ---------------------------------------------------------------- Mojette
+
+def test_fig2_heights():
+    k, b = CLAIMS["fig2_k"], CLAIMS["fig2_b"]
+    heights = []
+    for p, q in [(-1, 1), (0, 1), (1, 1)]:
+        bins = o.mojette_bins(k, b, p, q)
+        # every label lies in [0, b_i) and the label range has b_i entries
+        assert min(bins) == 0
+        heights.append(max(bins) + 1)
+        assert heights[-1] == o.mojette_height(k, b, p, q)
+    assert heights == CLAIMS["fig2_heights"]
+
+
+def _brute_lines(k, b, p, q):
+    """Groups grid pixels by brute force: two pixels share a bin iff their
+    difference is a multiple of the direction (p, -q) in (z, l).  Independent
+    of the label formula of Eq. (moj1)."""
+    pix = [(z, l) for z in range(b) for l in range(k)]
+    parent = {x: x for x in pix}
+
+    def find(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    for (z, l) in pix:
+        z2, l2 = z + p, l - q
+        if 0 <= z2 < b and 0 <= l2 < k:
+            parent[find((z2, l2))] = find((z, l))
+    groups = {}
+    for x in pix:
+        groups.setdefault(find(x), []).append(x[0] * k + x[1])
+    return sorted(tuple(sorted(g)) for g in groups.values())
+
+
+@pytest.mark.parametrize("k,b", [(3, 4), (4, 3), (5, 7), (2, 6)])
+@pytest.mark.parametrize("p,q", [(-1, 1), (0, 1), (1, 1), (2, 1), (-3, 1), (1, 2), (-1, 2), (3, 2), (5, 4), (1, 0)])
+def test_bins_are_lines_of_direction(k, b, p, q):
+    """Eq. (moj1) puts two pixels in one bin iff they lie on one discrete line
+    of direction (p, q); a sign error in the label formula breaks this."""
+    bins = o.mojette_bins(k, b, p, q)
+    got = sorted(tuple(v) for v in bins.values())
+    assert got == _brute_lines(k, b, p, q)
+    h = o.mojette_height(k, b, p, q)
+    assert all(0 <= lab < h for lab in bins)
+    assert min(bins) == 0 and max(bins) == h - 1
+
+
+@pytest.mark.parametrize("k,b", [(3, 4), (6, 5), (8, 8), (24, 40), (5, 17)])
+@pytest.mark.parametrize("p,q", [(0, 1), (1, 1), (-1, 1), (2, 1), (-3, 1), (1, 2), (3, 4), (-5, 2)])
+def test_sigma_formula_is_max_bin(k, b, p, q):
+    """Theorem on sigma_i: the largest bin has min(ceil(b/|p|), ceil(k/|q|))
+    pixels."""
+    bins = o.mojette_bins(k, b, p, q)
+    assert max(len(v) for v in bins.values()) == o.sigma_formula(k, b, p, q)
+
+
+def test_lemma_a1_and_a002620():
+    seq = CLAIMS["a002620_prefix"]
+    for t in range(1, len(seq)):
+        s = sum(abs(p) for p, _ in o.construction_a_slopes(t))
+        assert s == seq[t] == o.lemma_a1_closed_form(t)
+    for t in range(1, 60):
+        assert sum(abs(p) for p, _ in o.construction_a_slopes(t)) == o.lemma_a1_closed_form(t)
+
+
+def test_lemma_b1():
+    for t in range(1, 60):
+        ps = [p for p, _ in o.construction_b_slopes(t, 1)]
+        assert all(p % 2 != 0 for p in ps) and len(set(ps)) == t
+        assert ps == list(range(ps[0], ps[0] + 2 * t, 2))  # consecutive odds
+        assert sum(abs(p) for p in ps) == o.lemma_b1_closed_form(t)
+
+
+def test_construction_a_slope_set():
+    # Construction A's set is n consecutive integers around zero, all coprime to q=1
+    for n in range(1, 40):
+        ps = [p for p, _ in o.construction_a_slopes(n)]
+        assert ps == list(range(ps[0], ps[0] + n))
+        assert -ps[0] == (n - 1) // 2 and ps[-1] == n // 2
+
+
+@pytest.mark.parametrize("n,k,b", [(5, 3, 4), (6, 4, 5), (8, 6, 6), (7, 4, 10), (12, 9, 100),
+                                   (32, 24, 683), (32, 24, 86), (9, 3, 7)])
+def test_eps_construction_a_closed_form(n, k, b):
+    """Appendix A: exact worst-case overhead of Construction A.  The oracle's
+    eps comes from the column heights; for small n also brute-force every
+    k-subset of columns."""
+    code = o.construction_a(n, k, b)
+    closed = o.eps_construction_a_closed_form(n, k, b)
+    assert code.eps() == pytest.approx(closed, rel=1e-12, abs=1e-15)
+    if n <= 12:
+        worst = max(sum(code.heights[j] for j in sub)
+                    for sub in itertools.combinations(range(n), k)) / (k * b) - 1
+        assert worst == pytest.approx(closed, rel=1e-12, abs=1e-15)
+    # Lemma A.1 bounds of Appendix A
+    lo = (k - 1) / (4 * k * b) * (2 * k * n - k * k - 1)
+    hi = (k - 1) / (4 * k * b) * (2 * k * n - k * k + 1)
+    assert lo - 1e-12 <= closed <= hi + 1e-12
+
+
+def test_heights_equal_label_ranges():
+    for code in [o.construction_a(9, 5, 11), o.construction_b(7, 6, 9, 1), o.systematic_mojette(8, 3, 8)]:
+        for j, pq in enumerate(code.proj):
+            if pq is None:
+                continue
+            cells = [code.cells[c] for c in code.cells_of_column(j)]
+            bins = o.mojette_bins(code.k, code.b, *pq)
+            assert len(cells) == len(bins)
+            assert max(bins) + 1 == code.heights[j]
+
+
+# ---------------------------------------------------------------- Katz criterion
+
+@pytest.mark.parametrize("k,b", [(3, 4), (4, 3), (4, 5), (5, 4), (3, 7)])
+def test_katz_criterion_iff_peel(k, b):
+    """Katz criterion: every projection subset satisfying it decodes by BP.
+    The converse is tested, not assumed: a subset failing it leaves a ghost
+    (the grid is not determined), so no decoder, BP included, can succeed."""
+    directions = [(0, 1), (1, 1), (-1, 1), (2, 1), (-2, 1), (1, 2), (-1, 2), (3, 1), (1, 0)]
+    for r in range(1, 5):
+        for sub in itertools.combinations(directions, r):
+            code = o._projection_code("katz", len(sub), k, b, list(sub))
+            ok = o.wave_schedule(code, range(code.num_cells)).ok
+            assert ok == o.katz_holds(k, b, sub), sub
+
+
+def _ghost_free(k, b, sub):
+    """Linear-algebra check (rank over the rationals) that the projections
+    determine the grid -- independent of BP."""
+    rows = []
+    for p, q in sub:
+        for v in o.mojette_bins(k, b, p, q).values():
+            r = np.zeros(k * b)
+            r[v] = 1
+            rows.append(r)
+    return np.linalg.matrix_rank(np.array(rows)) == k * b
+
+
+@pytest.mark.parametrize("k,b", [(3, 4), (4, 4)])
+def test_katz_matches_rank(k, b):
+    directions = [(0, 1), (1, 1), (-1, 1), (2, 1), (1, 2), (1, 0)]
+    for r in range(1, 4):
+        for sub in itertools.combinations(directions, r):
+            assert _ghost_free(k, b, sub) == o.katz_holds(k, b, sub), sub
+
+
+# ---------------------------------------------------------------- decodability
+
+@pytest.mark.parametrize("n,k,b", [(5, 3, 4), (6, 4, 5), (8, 6, 6), (7, 4, 10)])
+def test_construction_a_any_k_projections(n, k, b):
+    code = o.construction_a(n, k, b)
+    for erased in itertools.combinations(range(n), n - k):
+        assert o.decodable(code, erased)
+
+
+@pytest.mark.parametrize("n,k,b,q_e", [(5, 6, 5, 1), (6, 8, 4, 2), (4, 7, 6, 1)])
+def test_construction_b_ceil_k_over_q_projections(n, k, b, q_e):
+    """Appendix B: ceil(k / 2^{q_e}) projections of Construction B decode."""
+    code = o.construction_b(n, k, b, q_e)
+    need = -(-k // 2 ** q_e)
+    assert need <= n
+    for keep in itertools.combinations(range(n), need):
+        erased = [j for j in range(n) if j not in keep]
+        assert o.decodable(code, erased), keep
+
+
+@pytest.mark.parametrize("k,b,e", [(9, 6, 3), (8, 8, 3), (8, 4, 3), (12, 6, 4), (20, 4, 2), (6, 5, 5)])
+def test_systematic_mojette_tolerates_e(k, b, e):
+    code = o.systematic_mojette(k, e, b)
+    for erased in itertools.combinations(range(k + e), e):
+        assert o.decodable(code, erased)
+
+
+# ---------------------------------------------------------------- peel contract
+
+def _fixed_point_depth(code, cells):
+    """Depth by value iteration: depth(s) = 1 + min over surviving cells c
+    containing s of max_{t in c, t != s} depth(t) (max of nothing = 0);
+    unrecoverable sources stay at infinity.  Independent of the round
+    procedure."""
+    INF = 10 ** 9
+    S = code.num_sources
+    d = [INF] * S
+    changed = True
+    while changed:
+        changed = False
+        for c in cells:
+            cs = code.cells[c]
+            for s in cs:
+                m = max([d[t] for t in cs if t != s], default=0)
+                if m < INF and m + 1 < d[s]:
+                    d[s] = m + 1
+                    changed = True
+    return d
+
+
+def _random_codes():
+    rng = random.Random(7)
+    yield o.table1()
+    yield o.table3()
+    yield o.systematic_mojette(8, 3, 8)
+    yield o.construction_a(7, 4, 10)
+    yield o.construction_b(6, 8, 4, 2)
+    # random sparse codes
+    for _ in range(6):
+        S = rng.randint(3, 12)
+        n = rng.randint(3, 7)
+        cells, cols = [], []
+        for j in range(n):
+            for _ in range(rng.randint(1, 4)):
+                deg = rng.randint(1, min(3, S))
+                cells.append(tuple(sorted(rng.sample(range(S), deg))))
+                cols.append(j)
+        yield o.Code("rand", n, 1, 1, S, cells, cols, [1] * n, [None] * n, 1)
+
+
+def test_wave_contract_fixed_point_and_resolver():
+    rng = random.Random(3)
+    for code in _random_codes():
+        for _ in range(12):
+            erased = [j for j in range(code.n) if rng.random() < 0.3]
+            cells = o.surviving_cells(code, erased)
+            sch = o.wave_schedule(code, cells)
+            naive = o.wave_schedule_naive(code, cells)
+            assert sch.depth == naive.depth and sch.resolver == naive.resolver
+            assert sch.order == naive.order
+            fp = _fixed_point_depth(code, cells)
+            for s in range(code.num_sources):
+                if sch.depth[s] == 0:
+                    assert fp[s] >= 10 ** 9
+                    continue
+                assert sch.depth[s] == fp[s]
+                # resolver: lowest surviving cell containing s whose other
+                # members are all recovered in earlier rounds
+                ok = [c for c in cells if s in code.cells[c]
+                      and all(sch.depth[t] != 0 and sch.depth[t] < sch.depth[s]
+                              for t in code.cells[c] if t != s)]
+                assert sch.resolver[s] == min(ok)
+            keys = [(d, s) for s, _r, d in sch.order]
+            assert keys == sorted(keys)
+
+
+def test_sequential_peel_same_stopping_set():
+    """The final recovered set does not depend on the order in which
+    degree-one nodes are taken (the peeling stopping set is unique)."""
+    rng = random.Random(11)
+    for code in _random_codes():
+        for _ in range(10):
+            erased = [j for j in range(code.n) if rng.random() < 0.4]
+            cells = o.surviving_cells(code, erased)
+            wave = {s for s in range(code.num_sources) if o.wave_schedule(code, cells).depth[s] > 0}
+            for _ in range(3):
+                seq = o.sequential_peel(code, cells, pick=lambda xs: rng.choice(xs))
+                assert seq == wave
+
+
+def test_undecodable_patterns_reported():
+    code = o.table1()
+    for erased in itertools.combinations(range(5), 4):
+        sch = o.wave_schedule(code, o.surviving_cells(code, erased))
+        assert not sch.ok
+        assert 0 < sum(sch.recovered) < code.num_sources or sum(sch.recovered) == 0
+
+
+# ---------------------------------------------------------------- numerics
+
+def _int_inputs(rng, M, K, N, lim=3):
+    A = rng.integers(-lim, lim + 1, size=(M, K)).astype(np.float32)
+    B = rng.integers(-lim, lim + 1, size=(K, N)).astype(np.float32)
+    return A, B
+
+
+@pytest.mark.parametrize("maker,h", [(o.table1, 4), (o.table3, 3), (lambda: o.systematic_mojette(8, 3, 8), 2),
+                                     (lambda: o.construction_a(7, 4, 10), 1)])
+def test_integer_inputs_decode_exactly(maker, h):
+    """Integer inputs keep every FP64 intermediate exact, so the decoded C
+    must equal A B bit for bit, whatever the depth."""
+    code = maker()
+    rng = np.random.default_rng(5)
+    M, K, N = code.num_sources * h, 24, 20
+    A, B = _int_inputs(rng, M, K, N)
+    ref = o.reference_product(A, B)
+    for erased in list(o.all_erasure_patterns(code.n, code.e))[:40]:
+        C, sch = o.coded_matmul(code, A, B, h, erased)
+        assert sch.ok
+        assert np.array_equal(C, ref)
+
+
+def test_padded_rows_read_as_zero():
+    code = o.table3()
+    rng = np.random.default_rng(2)
+    h = 4
+    M = code.num_sources * h - 3   # last block ragged
+    A, B = _int_inputs(rng, M, 16, 8)
+    C, sch = o.coded_matmul(code, A, B, h, [1, 3])
+    assert sch.ok
+    assert np.array_equal(C[:M], o.reference_product(A, B))
+    assert np.all(C[M:] == 0)
+
+
+def test_random_inputs_error_within_amplification():
+    """Random normal inputs: the decoded blocks match A B to within a small
+    multiple of the FP64 unit roundoff times each source's amplification."""
+    code = o.table3()
+    rng = np.random.default_rng(9)
+    h, K, N = 6, 40, 12
+    A = rng.standard_normal((code.num_sources * h, K)).astype(np.float32)
+    B = rng.standard_normal((K, N)).astype(np.float32)
+    ref = o.reference_product(A, B)
+    for erased in o.all_erasure_patterns(code.n, 2):
+        cells = o.surviving_cells(code, erased)
+        sch = o.wave_schedule(code, cells)
+        P = o.coded_products(code, A, B, h, cells)
+        Cd = o.peel_decode(code, P, sch, h, N)
+        kap = o.amplification(code, sch, P, Cd)
+        for s, blk in Cd.items():
+            r = ref[s * h:(s + 1) * h]
+            err = np.linalg.norm(blk - r) / np.linalg.norm(r)
+            assert err <= 1e-12 * max(1.0, kap[s])
+
+
+def test_systematic_no_erasure_is_copy():
+    """e = 0 on a systematic code: every source is resolved by its own
+    degree-one data cell at depth 1, so decoding is a copy of P."""
+    code = o.systematic_mojette(5, 2, 3)
+    sch = o.wave_schedule(code, range(code.num_cells))
+    assert sch.ok and sch.num_waves == 1
+    for s, r, d in sch.order:
+        assert code.cells[r] == (s,) and d == 1
+
+
+def test_expansion_reproduces_products():
+    """The integer expansion of C_s over the products, applied to the
+    products, gives C_s back (exactly, on integer data)."""
+    code = o.systematic_mojette(6, 3, 4)
+    rng = np.random.default_rng(4)
+    h = 2
+    A, B = _int_inputs(rng, code.num_sources * h, 10, 6)
+    erased = [0, 2, 4]
+    cells = o.surviving_cells(code, erased)
+    sch = o.wave_schedule(code, cells)
+    P = o.coded_products(code, A, B, h, cells)
+    Cd = o.peel_decode(code, P, sch, h, 6)
+    for s, e in o.expansion(code, sch).items():
+        tot = sum(v * P[c] for c, v in e.items())
+        assert np.array_equal(tot, Cd[s])
