@@ -1,0 +1,424 @@
+"""Benchmark: coded A.B with e erasures (array BP-XOR code), one JSON line.
+
+Workload (``sysmoj_8192``): systematic Mojette array code n = 11 (k = 8 data
+columns of an 8 x 8 source grid, e = 3 parity projections), h = 128-row
+source blocks, A and B 8192 x 8192 FP32 iid N(0,1); step i erases 3 columns
+drawn from seed 2000 + (i mod 100) (100 trials).  One step = the whole hot
+path: symbolic peel, encode + coded products, numeric peel.
+
+value = useful 2MNK FLOP / step time of the headline precision (split-BF16x3
+on tcgen05 when the build has it, else plain FP32), with inputs resident in
+HBM (A, B = 256 MB each, larger than L2).  The FP32 CUDA-core path is timed
+beside it.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as ct
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "useful TFLOP/s of coded A·B w/ e erasures, BF16x3 vs FP32; rel. error"
+WORKLOAD = "sysmoj_8192"
+
+
+def _parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gemm-config", type=int, default=0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def _config(wl):
+    return {"workload": WORKLOAD,
+            "code": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, slopes 0,+1,-1)",
+            "M": wl["M"], "N": wl["N"], "K": wl["K"], "h": wl["h"], "erasures": wl["e"],
+            "trials": wl["trials"], "mask_seeds": f"{wl['mask_seed_base']}+t, t=step mod {wl['trials']}",
+            "inputs": "A, B iid N(0,1) FP32, seeded",
+            "l2": "inputs larger than L2 (A, B 256 MB each; no flush)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class StageEvents:
+    """CUDA events the library records around each kernel of a step."""
+
+    def __init__(self, bpx, steps):
+        self.rt = ct.CDLL("libcudart.so.13")
+        self.rt.cudaEventCreate.argtypes = [ct.POINTER(ct.c_void_p)]
+        self.rt.cudaEventElapsedTime.argtypes = [ct.POINTER(ct.c_float), ct.c_void_p, ct.c_void_p]
+        self.rt.cudaEventDestroy.argtypes = [ct.c_void_p]
+        self.n = 2 * bpx.NUM_STAGES
+        self.arrays = []
+        for _ in range(steps):
+            arr = (ct.c_void_p * self.n)()
+            for i in range(self.n):
+                ev = ct.c_void_p()
+                assert self.rt.cudaEventCreate(ct.byref(ev)) == 0
+                arr[i] = ev
+            self.arrays.append(arr)
+
+    def ptr(self, i):
+        return ct.cast(self.arrays[i], ct.POINTER(ct.c_void_p))
+
+    def stage_ms(self, i, stage):
+        a = self.arrays[i]
+        ms = ct.c_float()
+        rc = self.rt.cudaEventElapsedTime(ct.byref(ms), a[2 * stage], a[2 * stage + 1])
+        return ms.value if rc == 0 else None
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+
+def _oracle_sample(A, B, h, mask, ncols):
+    """Runs the FP64 oracle's whole coded path on the first ncols columns of
+    B (the path is columnwise separable); returns seconds."""
+    from oracle import bpx_oracle as o
+    code = o.systematic_mojette(8, 3, 8)
+    t0 = time.perf_counter()
+    C, sch = o.coded_matmul(code, A, B[:, :ncols], h, list(np.nonzero(mask)[0]))
+    dt = time.perf_counter() - t0
+    assert sch.ok
+    return dt
+
+
+def _cores():
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+def cpu_baseline(A, B, wl, budget_s=12.0):
+    """The oracle as it stands on a bounded column sample of the workload."""
+    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+    from paper_1904_11563_gb300 import workloads as W
+    mask = W.erasure_mask(11, 3, wl["mask_seed_base"])
+    cols = 256
+    t = _oracle_sample(A, B, h, mask, cols)
+    total_t, total_cols = t, cols
+    while total_t < budget_s and total_cols + cols <= N:
+        total_t += _oracle_sample(A, B, h, mask, cols)
+        total_cols += cols
+    useful = 2.0 * M * K * total_cols
+    return {"value": useful / total_t / 1e12, "unit": "TFLOP/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"oracle FP64 coded path (numpy BLAS) on {total_cols} of {N} columns of B, "
+                      f"trial mask seed {wl['mask_seed_base']}, {total_t:.1f} s"}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1904_11563_gb300 import workloads as W
+    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+    A = W.matrix((M, K), "normal", 2)
+    B = W.matrix((K, N), "normal", 3)
+    cols = 128
+    warm = max(args.warmup, 3)
+    times = []
+    for i in range(warm + args.steps):
+        mask = W.erasure_mask(11, 3, wl["mask_seed_base"] + (i % wl["trials"]))
+        dt = _oracle_sample(A, B, h, mask, cols)
+        if i >= warm:
+            times.append(dt)
+    tot = sum(times)
+    val = 2.0 * M * K * cols * len(times) / tot / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(wl),
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": _cores(), "kind": "oracle",
+                             "sample": f"each step: oracle FP64 coded path on {cols} of {N} columns of B"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args, wl):
+    import torch
+    from paper_1904_11563_gb300 import build as B_
+    B_.build()
+    from paper_1904_11563_gb300 import bpx
+    from paper_1904_11563_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+    code = bpx.Code.systematic(8, 3, 8)
+    A, Bm = W.device_inputs(M, K, N, "normal", 2, device=dev)
+    masks = torch.from_numpy(np.stack([W.erasure_mask(11, 3, wl["mask_seed_base"] + t)
+                                       for t in range(wl["trials"])])).to(dev)
+    warm = max(args.warmup, 3)
+    steps = args.steps
+
+    # the headline precision
+    precs = []
+    if args.precision == "auto":
+        precs = ["bf16x3", "fp32"]
+    else:
+        precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
+    results = {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if cvd and cvd.split(",")[0].strip().isdigit():
+        gpu_index = int(cvd.split(",")[local].strip())
+
+    surv_rows = []
+    for t in range(wl["trials"]):
+        m = W.erasure_mask(11, 3, wl["mask_seed_base"] + t)
+        surv = sum(int(h_) for j, h_ in enumerate([8] * 8 + [8, 15, 15]) if not m[j])
+        surv_rows.append(surv * h)
+
+    for prec in precs:
+        P = bpx.PRECISIONS[prec]
+        try:
+            ws = bpx.Workspace(code, M, N, K, h, P, device=dev)
+        except bpx.BpxError:
+            continue
+        C = bpx.alloc_C(code, h, N, dev)
+        info = torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device=dev)
+        opts = bpx.default_opts(gemm_config=args.gemm_config)
+        try:
+            for i in range(warm):
+                bpx.coded_matmul(code, A, Bm, h, P, masks[i % wl["trials"]], ws, C=C, opts=opts, info=info)
+            torch.cuda.synchronize()
+        except bpx.BpxError as e:
+            if e.code == bpx.ERR_UNSUPPORTED:
+                continue
+            raise
+        sev = StageEvents(bpx, steps)
+        clocks = ClockSampler(gpu_index)
+        clocks.start()
+        time.sleep(0.3)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for i in range(steps):
+            o = bpx.default_opts(gemm_config=args.gemm_config)
+            o.stage_events = sev.ptr(i)
+            bpx.coded_matmul(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o, info=info)
+        t1.record()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ck = clocks.stop()
+        ms = t0.elapsed_time(t1)
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        inf = info.cpu().numpy()
+        assert inf[bpx.INFO_STATUS] == bpx.OK, inf
+        stage = {}
+        for si, nm in enumerate(bpx.STAGE_NAMES):
+            vals = [sev.stage_ms(i, si) for i in range(steps)]
+            vals = [v for v in vals if v is not None and v > 0]
+            stage[nm] = sum(vals) / len(vals) if vals else 0.0
+        rows_t = [surv_rows[(warm + i) % wl["trials"]] for i in range(steps)]
+        results[prec] = dict(ms=ms / steps, stage=stage, clocks=ck, ws=ws, C=C, rows=rows_t)
+
+    if not results:
+        raise RuntimeError("no precision could run")
+    head = "bf16x3" if "bf16x3" in results else list(results)[0]
+    useful = 2.0 * M * N * K
+    R = results[head]
+    value = world * useful / (R["ms"] * 1e-3) / 1e12
+
+    # relative error per block on sampled sources vs FP64 reference blocks
+    rel = {}
+    if rank == 0:
+        from oracle import bpx_oracle as o
+        Ah = A.cpu().numpy()
+        Bh = Bm.cpu().numpy().astype(np.float64)
+        last_mask = W.erasure_mask(11, 3, wl["mask_seed_base"] + ((warm + steps - 1) % wl["trials"]))
+        ref = o.systematic_mojette(8, 3, 8)
+        sch = o.wave_schedule(ref, o.surviving_cells(ref, list(np.nonzero(last_mask)[0])))
+        deep = sorted(range(64), key=lambda s: -sch.depth[s])
+        direct = [s for s in range(64) if sch.depth[s] == 1]
+        samples = sorted(set(deep[:3] + direct[:1]))
+        refs = {s: o.row_block(Ah, s, h) @ Bh for s in samples}
+        for prec, r in results.items():
+            Cn = r["C"]
+            errs = []
+            for s in samples:
+                blk = Cn[s * h:(s + 1) * h].double().cpu().numpy()
+                errs.append(float(np.linalg.norm(blk - refs[s]) / np.linalg.norm(refs[s])))
+            rel[prec] = {"max": max(errs), "sources": samples,
+                         "depths": [sch.depth[s] for s in samples]}
+
+    # roofline of the dominant kernel (the coded GEMM)
+    import json as _j
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _j.load(open(pk))
+    gemm_ms = R["stage"]["gemm"]
+    rows_mean = sum(R["rows"]) / len(R["rows"])
+    clk = R["clocks"].get("sm_mhz") or 0
+    if head in ("bf16x3", "bf16"):
+        mult = 3 if head == "bf16x3" else 1
+        flops = 2.0 * rows_mean * N * K * mult
+        achieved = flops / (gemm_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if peaks else "fallback",
+                "kernel": "coded tcgen05 GEMM", "work_per_launch": "2 x coded rows x N x K x %d MMA flops" % mult}
+    else:
+        flops = 2.0 * rows_mean * N * K
+        achieved = flops / (gemm_ms * 1e-3) / 1e12
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"FFMA: {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz",
+                "kernel": "coded FP32 SIMT GEMM", "work_per_launch": "2 x coded rows x N x K"}
+    # decode GB/s: compulsory bytes of the peel (read each non-direct
+    # resolver's product and every other block it subtracts, write C_s)
+    peel_ms = R["stage"]["peel"]
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": R["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": head, "data": "synthetic", "config": _config(wl)}
+    line["stages_ms"] = R["stage"]
+    for prec, r in results.items():
+        line[f"{prec}_tflops"] = world * useful / (r["ms"] * 1e-3) / 1e12
+        line[f"{prec}_ms_per_step"] = r["ms"]
+    if "bf16x3" in results and "fp32" in results:
+        line["speedup_bf16x3_vs_fp32"] = results["fp32"]["ms"] / results["bf16x3"]["ms"]
+    line["rel_err"] = rel
+    line["roofline"] = roof
+    line["peel_ms"] = peel_ms
+    line["clocks"] = R["clocks"]
+    per_step = {"bf16x3": 5, "bf16": 5, "fp32": 3}[head]
+    line["gpu_launches"] = per_step * steps
+
+    # end to end through the host entry point (pinned host buffers)
+    if not args.no_e2e and rank == 0:
+        P = bpx.PRECISIONS[head]
+        hA = A.cpu().pin_memory()
+        hB = Bm.cpu().pin_memory()
+        hC = torch.empty((M, N), dtype=torch.float32).pin_memory()
+        dA = torch.empty_like(A)
+        dB = torch.empty_like(Bm)
+        dmask = torch.empty(11, dtype=torch.uint8, device=dev)
+        hmasks = [torch.from_numpy(W.erasure_mask(11, 3, wl["mask_seed_base"] + t)).pin_memory()
+                  for t in range(wl["trials"])]
+        ws = R["ws"]
+        dC = R["C"]
+        e2e_steps = max(3, min(steps, 10))
+        for i in range(2):
+            bpx.coded_matmul_host(code, hA, hB, h, P, hmasks[i], hC, dA, dB, dmask, dC, ws)
+        t_s = time.perf_counter()
+        for i in range(e2e_steps):
+            rc, _ = bpx.coded_matmul_host(code, hA, hB, h, P, hmasks[i % wl["trials"]], hC, dA, dB,
+                                          dmask, dC, ws)
+            assert rc == bpx.OK
+        dt = (time.perf_counter() - t_s) / e2e_steps
+        line["e2e"] = {"value": useful / dt / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": 4 * (M * K + K * N) + 11,
+                       "d2h_bytes_per_step": 4 * M * N + 4 * bpx.INFO_LEN,
+                       "ms_per_step": dt * 1e3, "api": "bpx_coded_matmul_host"}
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        Ah = A.cpu().numpy()
+        Bh = Bm.cpu().numpy()
+        line["cpu_baseline"] = cpu_baseline(Ah, Bh, wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _parse()
+    from paper_1904_11563_gb300 import workloads as W
+    wl = W.WORKLOADS[WORKLOAD]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

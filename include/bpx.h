@@ -1,0 +1,239 @@
+/*
+ * bpx.h -- C ABI of libbpx: array BP-XOR coded matrix multiplication on one
+ * GB300 GPU (sm_103a).
+ *
+ * The library computes C = A B for A (M x K) and B (K x N), FP32 row-major,
+ * the way the coded scheme of Arslan, "Array BP-XOR Codes for Hierarchically
+ * Distributed Matrix Multiplication", does it:
+ *
+ *   - A is cut into S = b k row blocks ("source symbols") of h rows each
+ *     (Section II, Remark 2.1); block s is rows [s h, (s+1) h).  Rows past
+ *     M read as zero.
+ *   - Each coded symbol ("cell") c of an array code holds the XOR -- here the
+ *     real sum -- of the blocks in its support (Section III-A, Definition of
+ *     the [n,k,t,b] array BP-XOR code; Eq. (moj1) for projection codes).
+ *     Cells are grouped into n code columns (worker nodes).
+ *   - Every cell of a column that did not straggle yields its coded product
+ *     P_c = (sum_{s in supp(c)} A_s) B (Section III-A, Example 1: a processor
+ *     executes at most sigma dot products of summed operands).
+ *   - The sink rebuilds every C_s = A_s B by belief-propagation peeling
+ *     (Section I-A): a cell with one unknown source resolves it by
+ *     subtraction, C_s = P_r - sum_{t in supp(r), t != s} C_t.
+ *
+ * Workers and stragglers are emulated: an erasure mask over the n columns
+ * says which workers straggled.
+ *
+ * Conventions for every call
+ *   - Pointers named d_* are device pointers (cudaMalloc'd or torch-owned,
+ *     on the current device); h_* are host pointers.  The caller owns every
+ *     buffer and the stream.  The library allocates no device memory: all
+ *     per-call state lives in a caller-provided workspace (see
+ *     bpx_workspace_bytes / bpx_workspace_init).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) unless stated otherwise.  The return value reports
+ *     argument and launch errors only; the decode outcome lands in a device
+ *     int32 info array (BPX_INFO_*), which synchronous calls also return.
+ *   - Every return value is a bpx_status.  On failure bpx_last_error() gives
+ *     a thread-local message.  No C++ exception crosses the ABI.
+ *   - Alignment: all device buffers 16-byte aligned; the workspace 256-byte
+ *     aligned.  N must be a multiple of 4 and K a multiple of 8.
+ */
+#ifndef BPX_H
+#define BPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bpx_code bpx_code; /* opaque, host-side, library-owned */
+typedef void* bpx_stream;         /* a cudaStream_t */
+
+/* Code families (Section III). */
+enum bpx_variant {
+  BPX_TABLE1 = 0,     /* Table I, the [5,2,2,2] code: n=5, k=2, b=2, tolerates 3 erasures */
+  BPX_TABLE3 = 1,     /* Table III, the [5,3,2,3] code: n=5, k=3, b=3, tolerates 2 */
+  BPX_SYSTEMATIC = 2, /* systematic Mojette array: k data columns of the k x b grid + e
+                         projection parities (q=1, slopes 0,+1,-1,+2,...), n = k + e */
+  BPX_MOJETTE_A = 3,  /* Construction A (Cons33): n projections q=1,
+                         p = -floor((n-1)/2)..ceil((n-1)/2) of the k x b grid; e = n - k */
+  BPX_MOJETTE_B = 4   /* Construction B (cons35): n projections q=2^q_e, p = n consecutive
+                         odd integers from ceil_odd(1-n); e = n - ceil(k / 2^q_e) */
+};
+
+/* Arithmetic of the coded products.  FP32 accumulation in every case. */
+enum bpx_precision {
+  BPX_FP32 = 0,   /* plain FP32 FFMA (CUDA cores), encode fused into the operand load */
+  BPX_BF16 = 1,   /* coded A and B rounded to bf16, one tcgen05 MMA per k-step */
+  BPX_BF16X3 = 2, /* split bf16: a = a_hi + a_lo; hi*hi + hi*lo + lo*hi on tcgen05 */
+  BPX_MXFP8 = 3   /* E4M3 with one UE8M0 scale per 32 K-elements (tcgen05 block-scaled) */
+};
+
+enum bpx_status {
+  BPX_OK = 0,
+  BPX_ERR_INVAL = 1,       /* bad argument (size, alignment, null pointer, variant) */
+  BPX_ERR_UNSUPPORTED = 2, /* valid request this build cannot run */
+  BPX_ERR_UNDECODABLE = 3, /* peeling stopped before every source was recovered */
+  BPX_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out; the kernel exited cleanly */
+  BPX_ERR_CUDA = 5,        /* a CUDA runtime call failed (message in bpx_last_error) */
+  BPX_ERR_NOMEM = 6        /* workspace smaller than bpx_workspace_bytes */
+};
+
+/* Device info array written by bpx_schedule / bpx_coded_matmul (int32[BPX_INFO_LEN]). */
+enum bpx_info_index {
+  BPX_INFO_STATUS = 0,      /* BPX_OK or BPX_ERR_UNDECODABLE (or BPX_ERR_TIMEOUT) */
+  BPX_INFO_RECOVERED = 1,   /* number of recovered sources */
+  BPX_INFO_WAVES = 2,       /* number of peel rounds (maximum depth) */
+  BPX_INFO_SURVIVING = 3,   /* number of cells in non-erased columns */
+  BPX_INFO_DIRECT = 4,      /* sources resolved at depth 1 (written by the GEMM epilogue) */
+  BPX_INFO_DEVICE_ERR = 5,  /* 0, or the BPX_ERR_* a kernel's self-check raised */
+  BPX_INFO_LEN = 16
+};
+
+typedef struct {
+  int variant, n, k, e, b, q_e;
+  int num_sources; /* S = b k */
+  int num_cells;   /* coded symbols over all columns (empty Mojette bins dropped) */
+  int num_edges;   /* sum of cell degrees */
+  int sigma;       /* maximum cell degree (Section III-A; Section III-C theorem) */
+  double eps;      /* worst-case coding overhead eps(b,n) of Section III-B: over all
+                      choices of k columns, sum of their heights / (k b) - 1 */
+  /* Host views owned by the code handle, valid until bpx_code_free. */
+  const int32_t* col_ptr;     /* [n+1]: cells of column j are [col_ptr[j], col_ptr[j+1]) */
+  const int32_t* cell_ptr;    /* [num_cells+1]: support of cell c is cell_src[cell_ptr[c] ..] */
+  const int32_t* cell_src;    /* [num_edges]: source ids, ascending within a cell */
+  const int32_t* col_of_cell; /* [num_cells] */
+  const int32_t* heights;     /* [n]: column heights b_i = |p|(k-1) + |q|(b-1) + 1 (III-C) */
+  const int32_t* proj_p;      /* [n]: projection p of each column (0 for data columns) */
+  const int32_t* proj_q;      /* [n]: projection q of each column (0 for data columns) */
+} bpx_code_info;
+
+typedef struct {
+  int direct_write;     /* 1 (default): the product epilogue writes each depth-1 resolver
+                           straight into its C block, so the peel skips those sources */
+  int compensate_depth; /* sources deeper than this are peeled in FP64 before one rounding;
+                           < 0 (default -1): never */
+  int peel_ctas;        /* 0 = auto (a multiple of the SM count) */
+  int gemm_config;      /* 0 = auto; otherwise a tile configuration id of the tensor-core GEMM */
+  void* const* stage_events; /* NULL, or cudaEvent_t[2 * BPX_NUM_STAGES] created by the caller:
+                                events 2i / 2i+1 are recorded on the stream right before / after
+                                stage i (enum bpx_stage).  Used to time kernels in place. */
+} bpx_opts;
+
+/* Stages of the hot path, in launch order (for bpx_opts.stage_events). */
+enum bpx_stage {
+  BPX_STAGE_SCHEDULE = 0, /* a1 symbolic peel */
+  BPX_STAGE_B_PREP = 1,   /* B split / quantize (tensor-core paths) */
+  BPX_STAGE_A_PREP = 2,   /* encode + split / quantize of the coded operand (tensor-core paths) */
+  BPX_STAGE_GEMM = 3,     /* coded products (FP32 path: encode fused here) */
+  BPX_STAGE_PEEL = 4,     /* a4 numeric peel */
+  BPX_NUM_STAGES = 5
+};
+
+/* ---------------------------------------------------------------- code graph */
+
+/* Builds the code graph of a family of Section III (host only, no GPU needed).
+ *   Table I / III: (n,k,b) must be (5,2,2) / (5,3,3); e may be -1.
+ *   BPX_SYSTEMATIC: n = k + e data + parity columns on the k x b grid.
+ *   BPX_MOJETTE_A / _B: n projections of the k x b grid; q_e >= 1 for _B.
+ * e = -1 derives the tolerated erasures; otherwise it must match.
+ * Cell numbering: column ascending, then processor row / bin label ascending;
+ * bins are placed by Eq. (moj1): pixel (z,l), z in [0,b), l in [0,k), is source
+ * s = z k + l, label (b-1) q u(q) + (k-1) p u(p) - z q - l p.  Empty bins are
+ * dropped.  *out receives a handle to release with bpx_code_free.
+ * Errors: BPX_ERR_INVAL for inconsistent parameters or more than 2^24 sources. */
+int bpx_code_build(int variant, int n, int k, int e, int b, int q_e, bpx_code** out);
+
+/* Fills *out with sizes and host views of the graph (see bpx_code_info). */
+int bpx_code_info_get(const bpx_code* code, bpx_code_info* out);
+
+/* Releases the handle (NULL is a no-op). */
+void bpx_code_free(bpx_code* code);
+
+/* Thread-local text of the last error raised on this thread. */
+const char* bpx_last_error(void);
+
+/* ---------------------------------------------------------------- workspace */
+
+/* Device bytes needed by the calls below for this code, shapes and precision
+ * (graph copy + peel plan + operand staging for the tensor-core paths). */
+size_t bpx_workspace_bytes(const bpx_code* code, int M, int N, int K, int h, int precision);
+
+/* Binds a workspace to a code: uploads the graph (stream-ordered copies from
+ * the handle's host arrays; the call synchronizes `stream` before returning so
+ * the handle may be freed afterwards).  Once per workspace.  BPX_ERR_NOMEM if
+ * ws_bytes is too small for bpx_workspace_bytes(code, 0, 0, 0, 1, BPX_FP32). */
+int bpx_workspace_init(const bpx_code* code, void* d_ws, size_t ws_bytes, bpx_stream stream);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* a1. Symbolic peel (Section I-A decoder, parallel-round reading): from the
+ * device erasure mask d_erasure_mask[n] (1 = column straggled) computes the
+ * surviving cells and, round by round, every source whose surviving cell has
+ * exactly one unknown source left: resolver = the lowest such cell id,
+ * depth = the round.  Writes the plan into the workspace.  Optional outputs
+ * (NULL to skip): d_peel_order int32[3 S] = (source, resolver, depth) sorted
+ * by (depth, source), unused entries -1; d_recovered uint8[S]; d_info
+ * int32[BPX_INFO_LEN].  Undecodable masks are not an error of the call: the
+ * info array says BPX_ERR_UNDECODABLE and the partial plan stays usable. */
+int bpx_schedule(const bpx_code* code, const uint8_t* d_erasure_mask, void* d_ws, size_t ws_bytes,
+                 int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, bpx_stream stream);
+
+/* a2. Worker-side encode, materialized (Section III-A, Example 1: the nodes
+ * form the sums themselves): for the i-th surviving cell c (ascending id, as
+ * planned by bpx_schedule) writes rows [i h, (i+1) h) of d_A_coded (K columns,
+ * FP32) = sum over s in supp(c), ascending, of A_s.  d_A_coded must hold
+ * num_cells h rows; rows past the surviving count are left untouched. */
+int bpx_encode(const bpx_code* code, const float* d_A, int M, int K, int h, const void* d_ws,
+               float* d_A_coded, bpx_stream stream);
+
+/* a3. Coded products (Section III-A): P_c = A_c B for every surviving cell,
+ * in the given precision, the encode sums formed on the way into the GEMM.
+ * P_c goes to d_products + c h N (d_products: num_cells h N floats, row-major
+ * h x N per cell), except that with d_C non-NULL the product of each depth-1
+ * resolver goes straight to its source block d_C + s h N.  Requires the plan
+ * of bpx_schedule in d_ws. */
+int bpx_coded_products(const bpx_code* code, const float* d_A, const float* d_B, int M, int N,
+                       int K, int h, int precision, void* d_ws, size_t ws_bytes,
+                       float* d_products, float* d_C, const bpx_opts* opts, bpx_stream stream);
+
+/* a4. Numeric peel (Section I-A, XOR read as subtraction): along the planned
+ * schedule, C_s = P_r - sum_{t in supp(r), t != s, ascending} C_t for every
+ * recovered source.  d_C holds S h rows of N floats (rows >= M are scratch for
+ * zero-padded blocks).  direct_written = 1 when bpx_coded_products already
+ * wrote the depth-1 sources into d_C.  Unrecovered blocks are left untouched. */
+int bpx_peel_decode(const bpx_code* code, const float* d_products, int N, int h, float* d_C,
+                    int direct_written, const bpx_opts* opts, const void* d_ws, bpx_stream stream);
+
+/* The whole path for one erasure pattern: schedule, encode + products, peel.
+ * d_products may be NULL when ws was sized for it (products then live in the
+ * workspace).  d_info as in bpx_schedule. */
+int bpx_coded_matmul(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K,
+                     int h, int precision, const uint8_t* d_erasure_mask, float* d_C,
+                     const bpx_opts* opts, void* d_ws, size_t ws_bytes, int32_t* d_info,
+                     bpx_stream stream);
+
+/* End-to-end from host memory: copies h_A, h_B and h_erasure_mask into the
+ * caller's device buffers d_A, d_B, d_mask (M K, K N, n elements), runs
+ * bpx_coded_matmul into d_C (S h x N), copies the first M rows of C into h_C
+ * and the info array into h_info (int32[BPX_INFO_LEN]), then synchronizes the
+ * stream.  Returns the decode status (BPX_OK / BPX_ERR_UNDECODABLE / ...).
+ * Host buffers should be page-locked for full copy bandwidth. */
+int bpx_coded_matmul_host(const bpx_code* code, const float* h_A, const float* h_B, int M, int N,
+                          int K, int h, int precision, const uint8_t* h_erasure_mask, float* h_C,
+                          float* d_A, float* d_B, uint8_t* d_mask, float* d_C, const bpx_opts* opts,
+                          void* d_ws, size_t ws_bytes, int32_t* h_info, bpx_stream stream);
+
+/* Default options (direct_write = 1, compensate_depth = -1, autos). */
+bpx_opts bpx_default_opts(void);
+
+/* Library version and the architecture it was compiled for ("sm_103a"). */
+const char* bpx_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPX_H */

@@ -77,10 +77,12 @@ class Code:
         return max(len(c) for c in self.cells)
 
     def eps(self) -> float:
-        """Worst-case coding overhead of Section III-B: over all choices of k
-        columns, (sum of their heights) / (k b) - 1.  The sum depends only on
-        the chosen heights, so the worst case is the k tallest columns."""
-        hs = sorted(self.heights, reverse=True)[: self.k]
+        """Worst-case coding overhead of Section III-B: over every set of
+        columns large enough to decode (n - e of them: k for Construction A
+        and the array codes, ceil(k / 2^{q_e}) for Construction B, as in
+        Appendix B), (sum of their heights) / (k b) - 1.  The sum depends
+        only on the chosen heights, so the worst case is the tallest ones."""
+        hs = sorted(self.heights, reverse=True)[: self.n - self.e]
         return sum(hs) / (self.k * self.b) - 1.0
 
 
@@ -424,10 +426,9 @@ def encode(code: Code, A: np.ndarray, h: int, cell: int) -> np.ndarray:
     """Worker-side encoding (Section III-A, Example 1): the coded operand of
     a cell is the sum of its sources' row blocks, in ascending source id,
     in FP64 from the given inputs."""
-    A64 = np.asarray(A, dtype=np.float64)
-    acc = np.zeros((h, A64.shape[1]), dtype=np.float64)
+    acc = np.zeros((h, A.shape[1]), dtype=np.float64)
     for s in code.cells[cell]:
-        acc += row_block(A64, s, h)
+        acc += row_block(A, s, h)
     return acc
 
 
@@ -505,9 +506,23 @@ def all_erasure_patterns(n: int, max_e: int):
         yield from itertools.combinations(range(n), e)
 
 
+def eps_construction_b_closed_form(n: int, k: int, b: int, q_e: int) -> float:
+    """Exact worst-case overhead of Construction B: the t = ceil(k / 2^{q_e})
+    tallest projections have heights |p|(k-1) + 2^{q_e}(b-1) + 1, and the
+    sum of their |p| is the Lemma B.1 sum over n slopes minus the one over
+    the n - t slopes nearest zero, so
+    eps = ((k-1)(L(n) - L(n-t)) + t (2^{q_e}(b-1) + 1)) / (k b) - 1,
+    L = Lemma B.1.  (Appendix B writes the |p| sums with Appendix A's phi;
+    Lemma B.1 is the sum for this slope set.)"""
+    t = -(-k // 2 ** q_e)
+    L = lemma_b1_closed_form
+    Lnt = L(n - t) if n - t > 0 else 0
+    return ((k - 1) * (L(n) - Lnt) + t * (2 ** q_e * (b - 1) + 1)) / (k * b) - 1.0
+
+
 def reference_block(A: np.ndarray, B: np.ndarray, s: int, h: int) -> np.ndarray:
     """C_s = A_s B in FP64 for one source (sampled checks at full size)."""
-    return row_block(np.asarray(A, dtype=np.float64), s, h) @ np.asarray(B, dtype=np.float64)
+    return row_block(A, s, h) @ np.asarray(B, dtype=np.float64)
 
 
 def eps_construction_a_closed_form(n: int, k: int, b: int) -> float:

@@ -1,0 +1,285 @@
+"""Python binding of libbpx (ctypes): argument marshalling only.
+
+Every call forwards to the C ABI declared in ``include/bpx.h``; every step of
+the hot path runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current stream.  The binding fails loudly when the library
+has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbpx.so")
+
+# enums of bpx.h
+TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B = 0, 1, 2, 3, 4
+FP32, BF16, BF16X3, MXFP8 = 0, 1, 2, 3
+OK, ERR_INVAL, ERR_UNSUPPORTED, ERR_UNDECODABLE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(7)
+INFO_STATUS, INFO_RECOVERED, INFO_WAVES, INFO_SURVIVING, INFO_DIRECT, INFO_DEVICE_ERR = range(6)
+INFO_LEN = 16
+
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "mxfp8": MXFP8}
+
+
+class BpxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bpx error {code}: {msg}")
+        self.code = code
+
+
+class _CodeInfo(ct.Structure):
+    _fields_ = [
+        ("variant", ct.c_int), ("n", ct.c_int), ("k", ct.c_int), ("e", ct.c_int),
+        ("b", ct.c_int), ("q_e", ct.c_int), ("num_sources", ct.c_int),
+        ("num_cells", ct.c_int), ("num_edges", ct.c_int), ("sigma", ct.c_int),
+        ("eps", ct.c_double),
+        ("col_ptr", ct.POINTER(ct.c_int32)), ("cell_ptr", ct.POINTER(ct.c_int32)),
+        ("cell_src", ct.POINTER(ct.c_int32)), ("col_of_cell", ct.POINTER(ct.c_int32)),
+        ("heights", ct.POINTER(ct.c_int32)), ("proj_p", ct.POINTER(ct.c_int32)),
+        ("proj_q", ct.POINTER(ct.c_int32)),
+    ]
+
+
+class Opts(ct.Structure):
+    _fields_ = [("direct_write", ct.c_int), ("compensate_depth", ct.c_int),
+                ("peel_ctas", ct.c_int), ("gemm_config", ct.c_int),
+                ("stage_events", ct.POINTER(ct.c_void_p))]
+
+
+STAGE_SCHEDULE, STAGE_B_PREP, STAGE_A_PREP, STAGE_GEMM, STAGE_PEEL = range(5)
+NUM_STAGES = 5
+STAGE_NAMES = ["schedule", "b_prep", "a_prep", "gemm", "peel"]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libbpx.so (built in-tree by ``build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "paper_1904_11563_gb300.build.build() (no CPU fallback exists)")
+    L = ct.CDLL(LIB_PATH)
+    vp, i, sz, f32p = ct.c_void_p, ct.c_int, ct.c_size_t, ct.c_void_p
+    sig = {
+        "bpx_code_build": (i, [i, i, i, i, i, i, ct.POINTER(vp)]),
+        "bpx_code_info_get": (i, [vp, ct.POINTER(_CodeInfo)]),
+        "bpx_code_free": (None, [vp]),
+        "bpx_last_error": (ct.c_char_p, []),
+        "bpx_workspace_bytes": (sz, [vp, i, i, i, i, i]),
+        "bpx_workspace_init": (i, [vp, vp, sz, vp]),
+        "bpx_schedule": (i, [vp, vp, vp, sz, vp, vp, vp, vp]),
+        "bpx_encode": (i, [vp, f32p, i, i, i, vp, f32p, vp]),
+        "bpx_coded_products": (i, [vp, f32p, f32p, i, i, i, i, i, vp, sz, f32p, f32p,
+                                   ct.POINTER(Opts), vp]),
+        "bpx_peel_decode": (i, [vp, f32p, i, i, f32p, i, ct.POINTER(Opts), vp, vp]),
+        "bpx_coded_matmul": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts),
+                                 vp, sz, vp, vp]),
+        "bpx_coded_matmul_host": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
+                                      f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
+        "bpx_default_opts": (Opts, []),
+        "bpx_build_info": (ct.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        raise BpxError(rc, lib().bpx_last_error().decode())
+    return rc
+
+
+def default_opts(**kw) -> Opts:
+    o = lib().bpx_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Code:
+    """A code graph built by the library (bpx_code_build)."""
+
+    def __init__(self, variant, n, k, b, e=-1, q_e=0):
+        self._h = None
+        h = ct.c_void_p()
+        _check(lib().bpx_code_build(variant, n, k, e, b, q_e, ct.byref(h)))
+        self._h = h
+        info = _CodeInfo()
+        _check(lib().bpx_code_info_get(h, ct.byref(info)))
+        self.variant, self.n, self.k, self.e, self.b, self.q_e = (
+            info.variant, info.n, info.k, info.e, info.b, info.q_e)
+        self.num_sources, self.num_cells, self.num_edges = info.num_sources, info.num_cells, info.num_edges
+        self.sigma, self.eps = info.sigma, info.eps
+
+        def arr(p, n):
+            return np.ctypeslib.as_array(p, shape=(n,)).copy() if n > 0 else np.zeros(0, np.int32)
+
+        self.col_ptr = arr(info.col_ptr, self.n + 1)
+        self.cell_ptr = arr(info.cell_ptr, self.num_cells + 1)
+        self.cell_src = arr(info.cell_src, self.num_edges)
+        self.col_of_cell = arr(info.col_of_cell, self.num_cells)
+        self.heights = arr(info.heights, self.n)
+        self.proj_p = arr(info.proj_p, self.n)
+        self.proj_q = arr(info.proj_q, self.n)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def cells(self):
+        return [tuple(int(x) for x in self.cell_src[self.cell_ptr[c]:self.cell_ptr[c + 1]])
+                for c in range(self.num_cells)]
+
+    def __del__(self):
+        if self._h is not None and _lib is not None:
+            _lib.bpx_code_free(self._h)
+            self._h = None
+
+    # factories
+    @classmethod
+    def table1(cls):
+        return cls(TABLE1, 5, 2, 2)
+
+    @classmethod
+    def table3(cls):
+        return cls(TABLE3, 5, 3, 3)
+
+    @classmethod
+    def systematic(cls, k, e, b):
+        return cls(SYSTEMATIC, k + e, k, b)
+
+    @classmethod
+    def mojette_a(cls, n, k, b):
+        return cls(MOJETTE_A, n, k, b)
+
+    @classmethod
+    def mojette_b(cls, n, k, b, q_e):
+        return cls(MOJETTE_B, n, k, b, q_e=q_e)
+
+
+def workspace_bytes(code: Code, M, N, K, h, precision) -> int:
+    return int(lib().bpx_workspace_bytes(code.handle, M, N, K, h, precision))
+
+
+# ------------------------------------------------------------------ device calls
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+class Workspace:
+    """Device workspace bound to a code (bpx_workspace_init)."""
+
+    def __init__(self, code: Code, M, N, K, h, precision, device="cuda"):
+        torch = _torch()
+        self.nbytes = workspace_bytes(code, M, N, K, h, precision)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.t = self.buf[off:off + self.nbytes]
+        self.code = code
+        _check(lib().bpx_workspace_init(code.handle, _ptr(self.t), self.nbytes, _stream()))
+
+    @property
+    def ptr(self):
+        return _ptr(self.t)
+
+
+def schedule(code: Code, mask, ws: Workspace):
+    """a1: returns (peel_order int32[S,3], recovered uint8[S], info int32[16]) on device."""
+    torch = _torch()
+    S = code.num_sources
+    order = torch.empty((S, 3), dtype=torch.int32, device=mask.device)
+    rec = torch.empty(S, dtype=torch.uint8, device=mask.device)
+    info = torch.empty(INFO_LEN, dtype=torch.int32, device=mask.device)
+    _check(lib().bpx_schedule(code.handle, _ptr(mask), ws.ptr, ws.nbytes, _ptr(order), _ptr(rec),
+                              _ptr(info), _stream()))
+    return order, rec, info
+
+
+def encode(code: Code, A, h, ws: Workspace):
+    """a2 (materialized): coded rows of the surviving cells, FP32."""
+    torch = _torch()
+    out = torch.zeros((code.num_cells * h, A.shape[1]), dtype=torch.float32, device=A.device)
+    _check(lib().bpx_encode(code.handle, _ptr(A), A.shape[0], A.shape[1], h, ws.ptr, _ptr(out),
+                            _stream()))
+    return out
+
+
+def coded_products(code: Code, A, B, h, precision, ws: Workspace, products=None, C=None, opts=None):
+    """a3: products[c] = A_c B for surviving cells (num_cells*h x N);
+    depth-1 resolvers go to C when C is given."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[1]
+    if products is None:
+        products = torch.zeros((code.num_cells * h, N), dtype=torch.float32, device=A.device)
+    _check(lib().bpx_coded_products(code.handle, _ptr(A), _ptr(B), M, N, K, h, precision, ws.ptr,
+                                    ws.nbytes, _ptr(products), _ptr(C),
+                                    ct.byref(opts) if opts is not None else None, _stream()))
+    return products
+
+
+def peel_decode(code: Code, products, N, h, C, ws: Workspace, direct_written=False, opts=None):
+    """a4: numeric peel into C (S*h x N)."""
+    _check(lib().bpx_peel_decode(code.handle, _ptr(products), N, h, _ptr(C), int(direct_written),
+                                 ct.byref(opts) if opts is not None else None, ws.ptr, _stream()))
+    return C
+
+
+def alloc_C(code: Code, h, N, device="cuda"):
+    torch = _torch()
+    return torch.zeros((code.num_sources * h, N), dtype=torch.float32, device=device)
+
+
+def coded_matmul(code: Code, A, B, h, precision, mask, ws: Workspace, C=None, opts=None, info=None):
+    """Whole path; returns (C [S*h x N], info int32[16] on device)."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = alloc_C(code, h, N, A.device)
+    if info is None:
+        info = torch.zeros(INFO_LEN, dtype=torch.int32, device=A.device)
+    _check(lib().bpx_coded_matmul(code.handle, _ptr(A), _ptr(B), M, N, K, h, precision, _ptr(mask),
+                                  _ptr(C), ct.byref(opts) if opts is not None else None, ws.ptr,
+                                  ws.nbytes, _ptr(info), _stream()))
+    return C, info
+
+
+def coded_matmul_host(code: Code, hA, hB, h, precision, hmask, hC, dA, dB, dmask, dC,
+                      ws: Workspace, opts=None):
+    """End-to-end from host buffers (copies inside the call); returns
+    (status, info numpy int32[16])."""
+    M, K = hA.shape
+    N = hB.shape[1]
+    info = np.zeros(INFO_LEN, dtype=np.int32)
+    rc = lib().bpx_coded_matmul_host(
+        code.handle, _ptr(hA), _ptr(hB), M, N, K, h, precision, _ptr(hmask), _ptr(hC),
+        _ptr(dA), _ptr(dB), _ptr(dmask), _ptr(dC), ct.byref(opts) if opts is not None else None,
+        ws.ptr, ws.nbytes, info.ctypes.data_as(ct.c_void_p), _stream())
+    if rc not in (OK, ERR_UNDECODABLE):
+        raise BpxError(rc, lib().bpx_last_error().decode())
+    return rc, info

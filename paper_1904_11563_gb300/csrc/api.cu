@@ -1,0 +1,283 @@
+// C-ABI entry points of libbpx: argument checks, workspace views and the
+// launch sequence of the hot path.  Every step runs in the kernels of this
+// library; the host only validates, binds pointers and launches.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+
+using bpx::fail;
+
+namespace bpx {
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+}  // namespace bpx
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(BPX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_ws(const bpx_code* c, const void* ws, size_t ws_bytes, const bpx::WsLayout& L) {
+  if (!c) return fail(BPX_ERR_INVAL, "code is NULL");
+  if (!ws) return fail(BPX_ERR_INVAL, "workspace is NULL");
+  if (!aligned(ws, 256)) return fail(BPX_ERR_INVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < L.total)
+    return fail(BPX_ERR_NOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+  return BPX_OK;
+}
+
+int check_shapes(const bpx_code* c, int M, int N, int K, int h) {
+  if (M < 0 || N <= 0 || K <= 0 || h <= 0)
+    return fail(BPX_ERR_INVAL, "need M >= 0 and N, K, h > 0 (M=%d N=%d K=%d h=%d)", M, N, K, h);
+  if (N % 4 != 0) return fail(BPX_ERR_INVAL, "N = %d must be a multiple of 4", N);
+  if (K % 8 != 0) return fail(BPX_ERR_INVAL, "K = %d must be a multiple of 8", K);
+  if (static_cast<long long>(M) > static_cast<long long>(c->S) * h)
+    return fail(BPX_ERR_INVAL, "M = %d exceeds S h = %lld rows", M, 1LL * c->S * h);
+  if (static_cast<long long>(c->num_cells) * h > (1LL << 31) / 2)
+    return fail(BPX_ERR_INVAL, "too many coded rows");
+  return BPX_OK;
+}
+
+cudaStream_t S(bpx_stream s) { return static_cast<cudaStream_t>(s); }
+
+// Records the caller's timing event for the start (end = 0) or end (end = 1)
+// of a stage, when bpx_opts.stage_events asks for it.
+void stage_mark(const bpx_opts* o, int stage, int end, cudaStream_t st) {
+  if (!o || !o->stage_events) return;
+  void* ev = o->stage_events[2 * stage + end];
+  if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev), st);
+}
+
+}  // namespace
+
+extern "C" int bpx_workspace_init(const bpx_code* c, void* ws, size_t ws_bytes, bpx_stream stream) {
+  bpx::clear_error();
+  const bpx::WsLayout L = bpx::ws_layout(c ? c : nullptr, 0, 0, 0, 1, BPX_FP32);
+  if (!c) return fail(BPX_ERR_INVAL, "bpx_workspace_init: code is NULL");
+  if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  char* base = static_cast<char*>(ws);
+  std::vector<int32_t> hdr(bpx::HDR_LEN, 0);
+  hdr[bpx::HDR_MAGIC] = bpx::kWsMagic;
+  hdr[bpx::HDR_N] = c->n;
+  hdr[bpx::HDR_S] = c->S;
+  hdr[bpx::HDR_CELLS] = c->num_cells;
+  hdr[bpx::HDR_EDGES] = c->num_edges;
+  hdr[bpx::HDR_SIGMA] = c->sigma;
+  struct Part {
+    size_t off;
+    const void* src;
+    size_t bytes;
+  } parts[] = {
+      {L.g_hdr, hdr.data(), hdr.size() * 4},
+      {L.g_col_of_cell, c->col_of_cell.data(), c->col_of_cell.size() * 4},
+      {L.g_cell_ptr, c->cell_ptr.data(), c->cell_ptr.size() * 4},
+      {L.g_cell_src, c->cell_src.data(), c->cell_src.size() * 4},
+      {L.g_src_ptr, c->src_ptr.data(), c->src_ptr.size() * 4},
+      {L.g_src_cell, c->src_cell.data(), c->src_cell.size() * 4},
+  };
+  for (const Part& pt : parts) {
+    if (pt.bytes == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(base + pt.off, pt.src, pt.bytes, cudaMemcpyHostToDevice, S(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "bpx_workspace_init: copy");
+  }
+  cudaError_t e = cudaMemsetAsync(base + L.p_info, 0, L.plan_end - L.p_info, S(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_workspace_init: memset");
+  e = cudaStreamSynchronize(S(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_workspace_init: sync");
+  return BPX_OK;
+}
+
+extern "C" int bpx_schedule(const bpx_code* c, const uint8_t* d_mask, void* ws, size_t ws_bytes,
+                            int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info,
+                            bpx_stream stream) {
+  bpx::clear_error();
+  if (!c) return fail(BPX_ERR_INVAL, "bpx_schedule: code is NULL");
+  const bpx::WsLayout L = bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32);
+  if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  if (!d_mask) return fail(BPX_ERR_INVAL, "bpx_schedule: erasure mask is NULL");
+  const bpx::DevGraph g = bpx::make_graph(c, ws, L);
+  const bpx::DevPlan p = bpx::make_plan(ws, L);
+  cudaError_t e = bpx::launch_schedule(g, p, d_mask, d_peel_order, d_recovered, d_info, S(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_schedule: launch");
+  return BPX_OK;
+}
+
+extern "C" int bpx_encode(const bpx_code* c, const float* d_A, int M, int K, int h,
+                          const void* ws, float* d_A_coded, bpx_stream stream) {
+  bpx::clear_error();
+  if (!c || !d_A || !d_A_coded || !ws) return fail(BPX_ERR_INVAL, "bpx_encode: NULL argument");
+  if (int rc = check_shapes(c, M, 4, K, h)) return rc;
+  if (!aligned(d_A, 16) || !aligned(d_A_coded, 16))
+    return fail(BPX_ERR_INVAL, "bpx_encode: buffers must be 16-byte aligned");
+  const bpx::WsLayout L = bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32);
+  const bpx::DevGraph g = bpx::make_graph(c, ws, L);
+  const bpx::DevPlan p = bpx::make_plan(ws, L);
+  cudaError_t e = bpx::launch_encode_f32(g, p, d_A, M, K, h, d_A_coded, S(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_encode: launch");
+  return BPX_OK;
+}
+
+namespace {
+
+int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, int N, int K,
+                  int h, int precision, void* ws, size_t ws_bytes, float* d_products, float* d_C,
+                  const bpx_opts* opts, cudaStream_t st) {
+  if (!c || !d_A || !d_B || !ws || !d_products)
+    return fail(BPX_ERR_INVAL, "bpx_coded_products: NULL argument");
+  if (int rc = check_shapes(c, M, N, K, h)) return rc;
+  if (!aligned(d_A, 16) || !aligned(d_B, 16) || !aligned(d_products, 16) ||
+      (d_C && !aligned(d_C, 16)))
+    return fail(BPX_ERR_INVAL, "bpx_coded_products: buffers must be 16-byte aligned");
+  const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
+  if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  const bpx::DevGraph g = bpx::make_graph(c, ws, L);
+  const bpx::DevPlan p = bpx::make_plan(ws, L);
+  char* base = static_cast<char*>(ws);
+  const int config = opts ? opts->gemm_config : 0;
+  cudaError_t e = cudaSuccess;
+  switch (precision) {
+    case BPX_FP32:
+      stage_mark(opts, BPX_STAGE_GEMM, 0, st);
+      e = bpx::launch_gemm_f32(g, p, d_A, d_B, M, N, K, h, d_products, d_C, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 1, st);
+      break;
+    case BPX_BF16:
+    case BPX_BF16X3: {
+      const bool split = precision == BPX_BF16X3;
+      void* a_hi = base + L.a_hi;
+      void* a_lo = split ? base + L.a_lo : nullptr;
+      void* b_hi = base + L.b_hi;
+      void* b_lo = split ? base + L.b_lo : nullptr;
+      stage_mark(opts, BPX_STAGE_B_PREP, 0, st);
+      e = bpx::launch_b_split(d_B, K, N, b_hi, b_lo, st);
+      stage_mark(opts, BPX_STAGE_B_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
+      if (e == cudaSuccess) e = bpx::launch_encode_split(g, p, d_A, M, K, h, a_hi, a_lo, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 0, st);
+      if (e == cudaSuccess)
+        e = bpx::launch_gemm_tc(g, p, a_hi, a_lo, b_hi, b_lo, c->num_cells, N, K, h, split,
+                                d_products, d_C, config, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 1, st);
+      if (e == cudaErrorNotSupported)
+        return fail(BPX_ERR_UNSUPPORTED, "bf16 tensor-core path not available in this build");
+      break;
+    }
+    default:
+      return fail(BPX_ERR_UNSUPPORTED, "precision %d not supported", precision);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_coded_products: launch");
+  return BPX_OK;
+}
+
+int peel_impl(const bpx_code* c, const float* d_products, int N, int h, float* d_C,
+              int direct_written, const bpx_opts* opts, const void* ws, cudaStream_t st) {
+  if (!c || !d_products || !d_C || !ws) return fail(BPX_ERR_INVAL, "bpx_peel_decode: NULL argument");
+  if (N <= 0 || h <= 0 || N % 4 != 0) return fail(BPX_ERR_INVAL, "bpx_peel_decode: bad N or h");
+  if (!aligned(d_products, 16) || !aligned(d_C, 16))
+    return fail(BPX_ERR_INVAL, "bpx_peel_decode: buffers must be 16-byte aligned");
+  const bpx::WsLayout L = bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32);
+  const bpx::DevGraph g = bpx::make_graph(c, ws, L);
+  const bpx::DevPlan p = bpx::make_plan(ws, L);
+  const int comp = opts ? opts->compensate_depth : -1;
+  const int ctas = opts ? opts->peel_ctas : 0;
+  stage_mark(opts, BPX_STAGE_PEEL, 0, st);
+  cudaError_t e = bpx::launch_peel(g, p, d_products, d_C, N, h, direct_written ? 2 : 1, comp, ctas, st);
+  stage_mark(opts, BPX_STAGE_PEEL, 1, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_peel_decode: launch");
+  return BPX_OK;
+}
+
+}  // namespace
+
+extern "C" int bpx_coded_products(const bpx_code* c, const float* d_A, const float* d_B, int M,
+                                  int N, int K, int h, int precision, void* ws, size_t ws_bytes,
+                                  float* d_products, float* d_C, const bpx_opts* opts,
+                                  bpx_stream stream) {
+  bpx::clear_error();
+  return products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, d_products, d_C, opts,
+                       S(stream));
+}
+
+extern "C" int bpx_peel_decode(const bpx_code* c, const float* d_products, int N, int h, float* d_C,
+                               int direct_written, const bpx_opts* opts, const void* ws,
+                               bpx_stream stream) {
+  bpx::clear_error();
+  return peel_impl(c, d_products, N, h, d_C, direct_written, opts, ws, S(stream));
+}
+
+extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float* d_B, int M, int N,
+                                int K, int h, int precision, const uint8_t* d_mask, float* d_C,
+                                const bpx_opts* opts, void* ws, size_t ws_bytes, int32_t* d_info,
+                                bpx_stream stream) {
+  bpx::clear_error();
+  if (!c) return fail(BPX_ERR_INVAL, "bpx_coded_matmul: code is NULL");
+  if (!d_C) return fail(BPX_ERR_INVAL, "bpx_coded_matmul: C is NULL");
+  const bpx_opts o = opts ? *opts : bpx_default_opts();
+  const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
+  if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  stage_mark(&o, BPX_STAGE_SCHEDULE, 0, S(stream));
+  if (int rc = bpx_schedule(c, d_mask, ws, ws_bytes, nullptr, nullptr, d_info, stream)) return rc;
+  stage_mark(&o, BPX_STAGE_SCHEDULE, 1, S(stream));
+  float* products = reinterpret_cast<float*>(static_cast<char*>(ws) + L.products);
+  if (int rc = products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, products,
+                             o.direct_write ? d_C : nullptr, &o, S(stream)))
+    return rc;
+  return peel_impl(c, products, N, h, d_C, o.direct_write, &o, ws, S(stream));
+}
+
+extern "C" int bpx_coded_matmul_host(const bpx_code* c, const float* h_A, const float* h_B, int M,
+                                     int N, int K, int h, int precision, const uint8_t* h_mask,
+                                     float* h_C, float* d_A, float* d_B, uint8_t* d_mask,
+                                     float* d_C, const bpx_opts* opts, void* ws, size_t ws_bytes,
+                                     int32_t* h_info, bpx_stream stream) {
+  bpx::clear_error();
+  if (!c || !h_A || !h_B || !h_mask || !h_C || !d_A || !d_B || !d_mask || !d_C || !h_info)
+    return fail(BPX_ERR_INVAL, "bpx_coded_matmul_host: NULL argument");
+  if (int rc = check_shapes(c, M, N, K, h)) return rc;
+  cudaStream_t st = S(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_A, h_A, sizeof(float) * M * static_cast<size_t>(K),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "copy A");
+  if ((e = cudaMemcpyAsync(d_B, h_B, sizeof(float) * K * static_cast<size_t>(N),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "copy B");
+  if ((e = cudaMemcpyAsync(d_mask, h_mask, c->n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "copy mask");
+  const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
+  int32_t* d_info = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + L.p_info);
+  if (int rc = bpx_coded_matmul(c, d_A, d_B, M, N, K, h, precision, d_mask, d_C, opts, ws, ws_bytes,
+                                nullptr, stream))
+    return rc;
+  if ((e = cudaMemcpyAsync(h_C, d_C, sizeof(float) * M * static_cast<size_t>(N),
+                           cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "copy C");
+  if ((e = cudaMemcpyAsync(h_info, d_info, sizeof(int32_t) * BPX_INFO_LEN, cudaMemcpyDeviceToHost,
+                           st)) != cudaSuccess)
+    return cuda_fail(e, "copy info");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
+  if (h_info[BPX_INFO_DEVICE_ERR] != 0) return h_info[BPX_INFO_DEVICE_ERR];
+  return h_info[BPX_INFO_STATUS];
+}
+
+extern "C" const char* bpx_build_info(void) {
+  return "libbpx 0.1 (sm_103a; tcgen05/TMA tensor-core path, FP32 SIMT path)";
+}

@@ -1,0 +1,66 @@
+// Internal declarations shared by the host code and the CUDA translation
+// units of libbpx.  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bpx.h"
+
+// Host-side code graph (Section III): cells of each column, sources of each
+// cell, and the transposed source -> cells adjacency the scheduler walks.
+struct bpx_code {
+  int variant = 0, n = 0, k = 0, e = 0, b = 0, q_e = 0;
+  int S = 0, num_cells = 0, num_edges = 0, sigma = 0;
+  double eps = 0.0;
+  std::vector<int32_t> col_ptr, cell_ptr, cell_src, col_of_cell, heights, proj_p, proj_q;
+  std::vector<int32_t> src_ptr, src_cell;  // source -> cells (ascending cell id)
+};
+
+namespace bpx {
+
+// Thread-local error text; returns `code` for `return fail(...)`.
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Byte offsets of every array in the device workspace.  The graph section is
+// filled once by bpx_workspace_init; the plan section by bpx_schedule; the
+// product and staging sections by bpx_coded_products.
+struct WsLayout {
+  // graph (int32)
+  size_t g_hdr, g_col_of_cell, g_cell_ptr, g_cell_src, g_src_ptr, g_src_cell;
+  // plan (int32)
+  size_t p_info, p_ctr, p_cnt, p_surv, p_direct, p_front0, p_front1, p_cand;
+  size_t p_depth, p_resolver, p_order, p_newsrc, p_wave_ptr, p_cursor;
+  size_t plan_end;
+  // products (float, num_cells * h * N)
+  size_t products;
+  // staging for the tensor-core paths (bf16 / fp8 operands)
+  size_t a_hi, a_lo, b_hi, b_lo, a_scale, b_scale;
+  size_t total;
+};
+
+WsLayout ws_layout(const bpx_code* code, int M, int N, int K, int h, int precision);
+
+constexpr int32_t kWsMagic = 0x42505831;  // "BPX1"
+
+// Graph header layout (int32 words at g_hdr)
+enum { HDR_MAGIC = 0, HDR_N, HDR_S, HDR_CELLS, HDR_EDGES, HDR_SIGMA, HDR_LEN = 16 };
+
+// Plan counters at p_ctr (int32 words)
+enum {
+  CTR_NSURV = 0,  // surviving cells
+  CTR_NWAVES,     // rounds
+  CTR_NREC,       // recovered sources
+  CTR_NF,         // frontier size (scratch)
+  CTR_NNEXT,      // next frontier size (scratch)
+  CTR_NNEW,       // sources recovered this round (scratch)
+  CTR_ERR,        // device error code raised by a kernel self-check
+  CTR_LEN = 16
+};
+
+}  // namespace bpx

@@ -1,0 +1,331 @@
+// Code graphs of Section III, built on the host: the literal array codes of
+// Table I and Table III, the systematic Mojette array, and the projection
+// codes of Construction A (Cons33) and Construction B (cons35), each
+// projection's bins placed by Eq. (moj1).  Also the workspace layout and
+// the thread-local error text of the C ABI.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <new>
+
+#include "bpx_internal.h"
+
+namespace bpx {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+}  // namespace bpx
+
+using bpx::fail;
+
+namespace {
+
+constexpr int kMaxSources = 1 << 24;
+
+struct Builder {
+  bpx_code* c;
+  std::vector<std::vector<int32_t>> cells;  // support of each cell
+  explicit Builder(bpx_code* code) : c(code) {}
+
+  void begin_column(int height, int p, int q) {
+    c->col_ptr.push_back(static_cast<int32_t>(cells.size()));
+    c->heights.push_back(height);
+    c->proj_p.push_back(p);
+    c->proj_q.push_back(q);
+  }
+
+  void add_cell(std::vector<int32_t> supp) {
+    std::sort(supp.begin(), supp.end());
+    c->col_of_cell.push_back(static_cast<int32_t>(c->col_ptr.size()) - 1);
+    cells.push_back(std::move(supp));
+  }
+
+  // One projection (p, q) of the k x b grid as a code column.  Pixel (z, l)
+  // is source z k + l; its bin label is
+  //   (b-1) q u(q) + (k-1) p u(p) - z q - l p,  u(t) = [t > 0],
+  // which Eq. (moj1) keeps inside [0, b_i) with b_i = |p|(k-1) + |q|(b-1) + 1.
+  // Bins are emitted in ascending label order; empty bins are skipped.
+  void projection(int k, int b, int p, int q) {
+    const long long height = static_cast<long long>(std::abs(p)) * (k - 1) +
+                             static_cast<long long>(std::abs(q)) * (b - 1) + 1;
+    const long long offset = static_cast<long long>(b - 1) * q * (q > 0 ? 1 : 0) +
+                             static_cast<long long>(k - 1) * p * (p > 0 ? 1 : 0);
+    begin_column(static_cast<int>(height), p, q);
+    std::vector<std::vector<int32_t>> bins(static_cast<size_t>(height));
+    for (int z = 0; z < b; ++z)
+      for (int l = 0; l < k; ++l) {
+        const long long label = offset - static_cast<long long>(z) * q - static_cast<long long>(l) * p;
+        bins[static_cast<size_t>(label)].push_back(z * k + l);
+      }
+    for (auto& bin : bins)
+      if (!bin.empty()) add_cell(std::move(bin));
+  }
+
+  // A systematic data column: column l of the grid, one degree-one cell per
+  // pixel (z, l), z ascending.
+  void data_column(int k, int b, int l) {
+    begin_column(b, 0, 0);
+    for (int z = 0; z < b; ++z) add_cell({z * k + l});
+  }
+
+  // A literal column, sources given as the paper's 1-based v indices.
+  void literal_column(int height, std::initializer_list<std::initializer_list<int>> col) {
+    begin_column(height, 0, 0);
+    for (auto& cell : col) {
+      std::vector<int32_t> s;
+      for (int v : cell) s.push_back(v - 1);
+      add_cell(std::move(s));
+    }
+  }
+
+  void finish() {
+    c->col_ptr.push_back(static_cast<int32_t>(cells.size()));
+    c->num_cells = static_cast<int>(cells.size());
+    c->cell_ptr.assign(1, 0);
+    c->sigma = 0;
+    for (auto& s : cells) {
+      c->cell_src.insert(c->cell_src.end(), s.begin(), s.end());
+      c->cell_ptr.push_back(static_cast<int32_t>(c->cell_src.size()));
+      c->sigma = std::max(c->sigma, static_cast<int>(s.size()));
+    }
+    c->num_edges = static_cast<int>(c->cell_src.size());
+    // source -> cells, cells ascending
+    std::vector<int32_t> deg(c->S + 1, 0);
+    for (int32_t s : c->cell_src) ++deg[s + 1];
+    c->src_ptr.assign(c->S + 1, 0);
+    for (int s = 0; s < c->S; ++s) c->src_ptr[s + 1] = c->src_ptr[s] + deg[s + 1];
+    c->src_cell.assign(c->num_edges, 0);
+    std::vector<int32_t> fill(c->src_ptr.begin(), c->src_ptr.end() - 1);
+    for (int cell = 0; cell < c->num_cells; ++cell)
+      for (int i = c->cell_ptr[cell]; i < c->cell_ptr[cell + 1]; ++i)
+        c->src_cell[fill[c->cell_src[i]]++] = cell;
+    // Worst-case overhead (Section III-B): the tallest n - e columns, i.e.
+    // the tallest set of columns that still has to decode.
+    std::vector<int32_t> hs(c->heights);
+    std::sort(hs.begin(), hs.end(), [](int a, int b) { return a > b; });
+    long long tot = 0;
+    for (int j = 0; j < c->n - c->e; ++j) tot += hs[j];
+    c->eps = static_cast<double>(tot) / (static_cast<double>(c->k) * c->b) - 1.0;
+  }
+};
+
+int ceil_odd(int x) { return (x % 2 != 0) ? x : x + 1; }
+
+}  // namespace
+
+extern "C" int bpx_code_build(int variant, int n, int k, int e, int b, int q_e, bpx_code** out) {
+  bpx::clear_error();
+  if (!out) return fail(BPX_ERR_INVAL, "bpx_code_build: out is NULL");
+  *out = nullptr;
+  if (n < 1 || k < 1 || b < 1) return fail(BPX_ERR_INVAL, "bpx_code_build: n, k, b must be >= 1");
+  if (static_cast<long long>(k) * b > kMaxSources)
+    return fail(BPX_ERR_INVAL, "bpx_code_build: k*b = %lld sources exceeds 2^24", 1LL * k * b);
+  bpx_code* c = new (std::nothrow) bpx_code();
+  if (!c) return fail(BPX_ERR_NOMEM, "bpx_code_build: out of host memory");
+  c->variant = variant;
+  c->n = n;
+  c->k = k;
+  c->b = b;
+  c->q_e = q_e;
+  c->S = k * b;
+  Builder B(c);
+  int derived_e = -1;
+  switch (variant) {
+    case BPX_TABLE1:
+      // Table I, [5,2,2,2], sigma = 2 (Example 1).  Decodes from any two of
+      // its five columns, so it tolerates e = 3 column erasures.
+      if (n != 5 || k != 2 || b != 2) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "Table I code has (n,k,b) = (5,2,2)");
+      }
+      B.literal_column(2, {{1}, {2, 3}});
+      B.literal_column(2, {{2}, {1, 4}});
+      B.literal_column(2, {{3}, {2, 4}});
+      B.literal_column(2, {{4}, {1, 3}});
+      B.literal_column(2, {{1, 2}, {3, 4}});
+      derived_e = 3;
+      break;
+    case BPX_TABLE3:
+      // Table III, [5,3,2,3], sigma = 2 (Example 2): block MDS, e = 2.
+      if (n != 5 || k != 3 || b != 3) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "Table III code has (n,k,b) = (5,3,3)");
+      }
+      B.literal_column(3, {{1}, {3, 4}, {6, 7}});
+      B.literal_column(3, {{1, 2}, {4, 5}, {7, 8}});
+      B.literal_column(3, {{2, 3}, {5, 6}, {8, 9}});
+      B.literal_column(3, {{7}, {9, 1}, {4, 8}});
+      B.literal_column(3, {{3}, {2, 6}, {9, 5}});
+      derived_e = 2;
+      break;
+    case BPX_SYSTEMATIC: {
+      if (n <= k) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "systematic code needs n > k (n = k + e)");
+      }
+      for (int l = 0; l < k; ++l) B.data_column(k, b, l);
+      // parities q = 1, slopes 0, +1, -1, +2, -2, ...
+      for (int i = 0; i < n - k; ++i) {
+        const int m = (i + 1) / 2;
+        const int p = (i == 0) ? 0 : ((i % 2 == 1) ? m : -m);
+        B.projection(k, b, p, 1);
+      }
+      derived_e = n - k;
+      break;
+    }
+    case BPX_MOJETTE_A: {
+      // Construction A: q = 1, p = -floor((n-1)/2) .. ceil((n-1)/2).
+      if (n < k) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "Construction A needs n >= k");
+      }
+      const int lo = -((n - 1) / 2);
+      for (int i = 0; i < n; ++i) B.projection(k, b, lo + i, 1);
+      derived_e = n - k;
+      break;
+    }
+    case BPX_MOJETTE_B: {
+      // Construction B: q = 2^q_e, p = the n consecutive odd integers from
+      // ceil_odd(1 - n) (the smallest odd integer >= 1 - n).
+      if (q_e < 1 || q_e > 20) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "Construction B needs 1 <= q_e <= 20");
+      }
+      const int q = 1 << q_e;
+      const int need = (k + q - 1) / q;
+      if (n < need) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "Construction B needs n >= ceil(k / 2^q_e) = %d", need);
+      }
+      const int lo = ceil_odd(1 - n);
+      for (int i = 0; i < n; ++i) B.projection(k, b, lo + 2 * i, q);
+      derived_e = n - need;
+      break;
+    }
+    default:
+      delete c;
+      return fail(BPX_ERR_INVAL, "bpx_code_build: unknown variant %d", variant);
+  }
+  if (e >= 0 && e != derived_e) {
+    delete c;
+    return fail(BPX_ERR_INVAL, "bpx_code_build: e = %d but this code tolerates %d erasures", e, derived_e);
+  }
+  c->e = derived_e;
+  B.finish();
+  *out = c;
+  return BPX_OK;
+}
+
+extern "C" int bpx_code_info_get(const bpx_code* c, bpx_code_info* out) {
+  if (!c || !out) return fail(BPX_ERR_INVAL, "bpx_code_info_get: NULL argument");
+  out->variant = c->variant;
+  out->n = c->n;
+  out->k = c->k;
+  out->e = c->e;
+  out->b = c->b;
+  out->q_e = c->q_e;
+  out->num_sources = c->S;
+  out->num_cells = c->num_cells;
+  out->num_edges = c->num_edges;
+  out->sigma = c->sigma;
+  out->eps = c->eps;
+  out->col_ptr = c->col_ptr.data();
+  out->cell_ptr = c->cell_ptr.data();
+  out->cell_src = c->cell_src.data();
+  out->col_of_cell = c->col_of_cell.data();
+  out->heights = c->heights.data();
+  out->proj_p = c->proj_p.data();
+  out->proj_q = c->proj_q.data();
+  return BPX_OK;
+}
+
+extern "C" void bpx_code_free(bpx_code* c) { delete c; }
+
+extern "C" const char* bpx_last_error(void) { return bpx::g_last_error.c_str(); }
+
+extern "C" bpx_opts bpx_default_opts(void) {
+  bpx_opts o;
+  o.direct_write = 1;
+  o.compensate_depth = -1;
+  o.peel_ctas = 0;
+  o.gemm_config = 0;
+  o.stage_events = nullptr;
+  return o;
+}
+
+namespace bpx {
+
+WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision) {
+  (void)M;
+  WsLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  const size_t S = static_cast<size_t>(c->S), C = static_cast<size_t>(c->num_cells);
+  const size_t E = static_cast<size_t>(c->num_edges);
+  const size_t i32 = sizeof(int32_t);
+  L.g_hdr = take(HDR_LEN * i32);
+  L.g_col_of_cell = take(C * i32);
+  L.g_cell_ptr = take((C + 1) * i32);
+  L.g_cell_src = take(E * i32);
+  L.g_src_ptr = take((S + 1) * i32);
+  L.g_src_cell = take(E * i32);
+  L.p_info = take(BPX_INFO_LEN * i32);
+  L.p_ctr = take(CTR_LEN * i32);
+  L.p_cnt = take(C * i32);
+  L.p_surv = take(C * i32);
+  L.p_direct = take(C * i32);
+  L.p_front0 = take(C * i32);
+  L.p_front1 = take(C * i32);
+  L.p_cand = take(C * i32);
+  L.p_depth = take(S * i32);
+  L.p_resolver = take(S * i32);
+  L.p_order = take(S * i32);
+  L.p_newsrc = take(S * i32);
+  L.p_wave_ptr = take((S + 2) * i32);
+  L.p_cursor = take((S + 2) * i32);
+  L.plan_end = off;
+  const size_t hN = static_cast<size_t>(h > 0 ? h : 0) * static_cast<size_t>(N > 0 ? N : 0);
+  L.products = take(C * hN * sizeof(float));
+  const size_t rowsA = C * static_cast<size_t>(h > 0 ? h : 0);
+  const size_t Kp = static_cast<size_t>(K > 0 ? K : 0), Np = static_cast<size_t>(N > 0 ? N : 0);
+  L.a_hi = L.a_lo = L.b_hi = L.b_lo = L.a_scale = L.b_scale = off;
+  if (precision == BPX_BF16 || precision == BPX_BF16X3) {
+    L.a_hi = take(rowsA * Kp * 2);
+    L.b_hi = take(Np * Kp * 2);
+    if (precision == BPX_BF16X3) {
+      L.a_lo = take(rowsA * Kp * 2);
+      L.b_lo = take(Np * Kp * 2);
+    }
+  } else if (precision == BPX_MXFP8) {
+    L.a_hi = take(rowsA * Kp);
+    L.b_hi = take(Np * Kp);
+    L.a_scale = take(rowsA * ((Kp + 31) / 32) + 128 * 64);
+    L.b_scale = take(Np * ((Kp + 31) / 32) + 128 * 64);
+  }
+  L.total = off;
+  return L;
+}
+
+}  // namespace bpx
+
+extern "C" size_t bpx_workspace_bytes(const bpx_code* c, int M, int N, int K, int h, int precision) {
+  if (!c) return 0;
+  return bpx::ws_layout(c, M, N, K, h, precision).total;
+}

@@ -1,0 +1,99 @@
+// Device-side views of the workspace and helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bpx_internal.h"
+
+namespace bpx {
+
+// Code graph as uploaded into the workspace (CSR, int32).
+struct DevGraph {
+  const int32_t* col_of_cell;
+  const int32_t* cell_ptr;
+  const int32_t* cell_src;
+  const int32_t* src_ptr;
+  const int32_t* src_cell;
+  int n, S, num_cells, num_edges, sigma;
+};
+
+// Peel plan written by the schedule kernel.
+struct DevPlan {
+  int32_t* info;      // BPX_INFO_LEN
+  int32_t* ctr;       // CTR_LEN counters
+  int32_t* cnt;       // unknown sources per cell (-1: erased column)
+  int32_t* surv;      // surviving cells, ascending
+  int32_t* direct;    // per cell: the source it resolves at depth 1, or -1
+  int32_t* front0;    // frontier scratch
+  int32_t* front1;
+  int32_t* cand;      // per frontier entry: its unknown source
+  int32_t* depth;     // per source: round of recovery (0 = not recovered)
+  int32_t* resolver;  // per source: resolving cell (INT32_MAX = none)
+  int32_t* order;     // recovered sources sorted by (depth, source)
+  int32_t* newsrc;    // sources recovered in the current round
+  int32_t* wave_ptr;  // order[wave_ptr[d-1] .. wave_ptr[d]) = sources of depth d
+  int32_t* cursor;    // placement cursors (scratch)
+};
+
+inline DevGraph make_graph(const bpx_code* c, const void* ws, const WsLayout& L) {
+  auto base = static_cast<const char*>(ws);
+  DevGraph g;
+  g.col_of_cell = reinterpret_cast<const int32_t*>(base + L.g_col_of_cell);
+  g.cell_ptr = reinterpret_cast<const int32_t*>(base + L.g_cell_ptr);
+  g.cell_src = reinterpret_cast<const int32_t*>(base + L.g_cell_src);
+  g.src_ptr = reinterpret_cast<const int32_t*>(base + L.g_src_ptr);
+  g.src_cell = reinterpret_cast<const int32_t*>(base + L.g_src_cell);
+  g.n = c->n;
+  g.S = c->S;
+  g.num_cells = c->num_cells;
+  g.num_edges = c->num_edges;
+  g.sigma = c->sigma;
+  return g;
+}
+
+inline DevPlan make_plan(const void* ws, const WsLayout& L) {
+  char* base = const_cast<char*>(static_cast<const char*>(ws));
+  auto at = [&](size_t off) { return reinterpret_cast<int32_t*>(base + off); };
+  DevPlan p;
+  p.info = at(L.p_info);
+  p.ctr = at(L.p_ctr);
+  p.cnt = at(L.p_cnt);
+  p.surv = at(L.p_surv);
+  p.direct = at(L.p_direct);
+  p.front0 = at(L.p_front0);
+  p.front1 = at(L.p_front1);
+  p.cand = at(L.p_cand);
+  p.depth = at(L.p_depth);
+  p.resolver = at(L.p_resolver);
+  p.order = at(L.p_order);
+  p.newsrc = at(L.p_newsrc);
+  p.wave_ptr = at(L.p_wave_ptr);
+  p.cursor = at(L.p_cursor);
+  return p;
+}
+
+// Launchers (defined in the .cu files).  All return cudaError_t of the launch.
+cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
+                            int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
+                            cudaStream_t st);
+cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, float* C, int N, int h,
+                        int first_wave, int compensate_depth, int ctas, cudaStream_t st);
+cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* A, int M, int K,
+                              int h, float* out, cudaStream_t st);
+cudaError_t launch_encode_split(const DevGraph& g, const DevPlan& p, const float* A, int M, int K,
+                                int h, void* a_hi, void* a_lo, cudaStream_t st);
+cudaError_t launch_b_split(const float* B, int K, int N, void* b_hi, void* b_lo, cudaStream_t st);
+cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* A, const float* B,
+                            int M, int N, int K, int h, float* products, float* C_direct,
+                            cudaStream_t st);
+// Tensor-core coded GEMM over the staged bf16 operands (split or plain).
+cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
+                           const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
+                           bool split3, float* products, float* C_direct, int config,
+                           cudaStream_t st);
+
+int num_sms();
+
+}  // namespace bpx

@@ -1,0 +1,97 @@
+// a4: numeric peel.  C_s = P_r - sum_{t in supp(r), t != s} C_t along the
+// planned waves (Section I-A decoder, XOR read as subtraction).
+//
+// The subtraction is elementwise over the h x N block, so element i of C_s
+// depends only on element i of the blocks it reads.  Each CTA therefore owns
+// one contiguous slice of the block's float4 index range and walks the whole
+// schedule over that slice: a __syncthreads between waves is the only
+// synchronisation, with no grid barrier, flag or spin-wait.  Within a wave
+// the (source, float4) items of the slice are spread over the CTA's threads,
+// consecutive threads on consecutive float4s (128-bit coalesced accesses).
+#include <algorithm>
+
+#include "device_common.cuh"
+
+namespace bpx {
+namespace {
+
+constexpr int kPeelThreads = 256;
+
+__device__ __forceinline__ float4 ldg_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__global__ void __launch_bounds__(kPeelThreads)
+peel_kernel(DevGraph g, DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk,
+            int first_wave, int compensate_depth) {
+  const int nwaves = p.ctr[CTR_NWAVES];
+  const long long v0 = static_cast<long long>(blockIdx.x) * chunk;
+  if (v0 >= nv) return;
+  const int clen = static_cast<int>(min(static_cast<long long>(chunk), nv - v0));
+  const float4* P4 = reinterpret_cast<const float4*>(P);
+  float4* C4 = reinterpret_cast<float4*>(C);
+
+  for (int d = first_wave; d <= nwaves; ++d) {
+    const int o0 = p.wave_ptr[d - 1], o1 = p.wave_ptr[d];
+    const int items = (o1 - o0) * clen;
+    const bool comp = compensate_depth >= 0 && d > compensate_depth;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int j = it / clen;
+      const long long v = v0 + (it - j * clen);
+      const int s = p.order[o0 + j];
+      const int r = p.resolver[s];
+      const int e0 = g.cell_ptr[r], e1 = g.cell_ptr[r + 1];
+      const float4 pr = ldg_stream(P4 + static_cast<long long>(r) * nv + v);
+      if (!comp) {
+        float4 acc = pr;
+        for (int e = e0; e < e1; ++e) {
+          const int t = g.cell_src[e];
+          if (t == s) continue;
+          const float4 x = C4[static_cast<long long>(t) * nv + v];
+          acc.x -= x.x;
+          acc.y -= x.y;
+          acc.z -= x.z;
+          acc.w -= x.w;
+        }
+        C4[static_cast<long long>(s) * nv + v] = acc;
+      } else {
+        // Deep chains: subtract in FP64 and round once.
+        double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
+        for (int e = e0; e < e1; ++e) {
+          const int t = g.cell_src[e];
+          if (t == s) continue;
+          const float4 x = C4[static_cast<long long>(t) * nv + v];
+          ax -= x.x;
+          ay -= x.y;
+          az -= x.z;
+          aw -= x.w;
+        }
+        C4[static_cast<long long>(s) * nv + v] =
+            make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
+                        static_cast<float>(aw));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, float* C, int N, int h,
+                        int first_wave, int compensate_depth, int ctas, cudaStream_t st) {
+  const long long nv = static_cast<long long>(h) * N / 4;
+  if (nv <= 0) return cudaSuccess;
+  int target = ctas > 0 ? ctas : 4 * num_sms();
+  long long chunk = (nv + target - 1) / target;
+  chunk = std::max<long long>(32, (chunk + 31) / 32 * 32);
+  const long long grid = (nv + chunk - 1) / chunk;
+  peel_kernel<<<static_cast<unsigned>(grid), kPeelThreads, 0, st>>>(
+      g, p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);
+  return cudaGetLastError();
+}
+
+}  // namespace bpx

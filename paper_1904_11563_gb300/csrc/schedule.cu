@@ -1,0 +1,214 @@
+// a1: symbolic peel.  One CTA turns an erasure mask into the peel plan:
+// the surviving cells and, round by round, the sources that a surviving
+// cell with exactly one unknown source resolves (Section I-A decoder read as
+// parallel rounds).  Resolver = lowest such cell id; depth = the round; the
+// recovered sources are then listed in (depth, source) order.
+//
+// Each round only touches the cells whose unknown count just dropped to one
+// (a warp-parallel ready queue), so the cost is linear in the graph edges
+// plus one short barrier sequence per round.
+#include <climits>
+
+#include "device_common.cuh"
+
+namespace bpx {
+namespace {
+
+constexpr int kThreads = 1024;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = warp > 0 ? s_warp[warp - 1] : 0;
+  *total = s_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
+                uint8_t* recovered, int32_t* info_out) {
+  __shared__ int s_warp[32];
+  __shared__ int s_nf, s_nnew, s_nnext;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int c = tid; c < g.num_cells; c += nt) {
+    const bool alive = mask[g.col_of_cell[c]] == 0;
+    p.cnt[c] = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
+    p.direct[c] = -1;
+  }
+  for (int s = tid; s < g.S; s += nt) {
+    p.depth[s] = 0;
+    p.resolver[s] = INT_MAX;
+  }
+  if (tid == 0) {
+    s_nf = 0;
+    p.wave_ptr[0] = 0;
+  }
+  __syncthreads();
+
+  // Surviving cells in ascending id, and the first ready queue (degree one).
+  int nsurv = 0;
+  for (int base = 0; base < g.num_cells; base += nt) {
+    const int c = base + tid;
+    const int f = (c < g.num_cells && p.cnt[c] >= 0) ? 1 : 0;
+    int total;
+    const int ex = block_exclusive_scan(f, s_warp, &total);
+    if (f) {
+      p.surv[nsurv + ex] = c;
+      if (p.cnt[c] == 1) p.front0[atomicAdd(&s_nf, 1)] = c;
+    }
+    nsurv += total;
+  }
+  __syncthreads();
+
+  int32_t* fr = p.front0;
+  int32_t* nx = p.front1;
+  int round = 0, nrec = 0;
+  while (true) {
+    const int nf = s_nf;
+    if (nf == 0) break;
+    ++round;
+    // A: every ready cell names its one unknown source; lowest cell id wins.
+    for (int i = tid; i < nf; i += nt) {
+      const int c = fr[i];
+      int found = -1;
+      if (p.cnt[c] == 1) {
+        for (int e = g.cell_ptr[c]; e < g.cell_ptr[c + 1]; ++e) {
+          const int t = g.cell_src[e];
+          if (p.depth[t] == 0) {
+            found = t;
+            break;
+          }
+        }
+        if (found >= 0) atomicMin(&p.resolver[found], c);
+      }
+      p.cand[i] = found;
+    }
+    if (tid == 0) {
+      s_nnew = 0;
+      s_nnext = 0;
+    }
+    __syncthreads();
+    // B: mark the named sources recovered in this round (once each).
+    for (int i = tid; i < nf; i += nt) {
+      const int s = p.cand[i];
+      if (s >= 0 && atomicCAS(&p.depth[s], 0, round) == 0) p.newsrc[atomicAdd(&s_nnew, 1)] = s;
+    }
+    __syncthreads();
+    const int nnew = s_nnew;
+    if (nnew == 0) {
+      --round;
+      break;
+    }
+    nrec += nnew;
+    if (tid == 0) p.wave_ptr[round] = nrec;
+    // C: drop the recovered sources from their cells; a cell whose unknown
+    // count reaches one joins the next ready queue.
+    for (int j = tid; j < nnew; j += nt) {
+      const int s = p.newsrc[j];
+      for (int e = g.src_ptr[s]; e < g.src_ptr[s + 1]; ++e) {
+        const int c = g.src_cell[e];
+        if (p.cnt[c] >= 0) {
+          const int old = atomicSub(&p.cnt[c], 1);
+          if (old == 2) nx[atomicAdd(&s_nnext, 1)] = c;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s_nf = s_nnext;
+    int32_t* tmp = fr;
+    fr = nx;
+    nx = tmp;
+    __syncthreads();
+  }
+
+  // Place the recovered sources in (depth, source) order: one warp walks the
+  // sources in ascending id; lanes of equal depth share one cursor bump.
+  for (int d = 1 + tid; d <= round; d += nt) p.cursor[d] = p.wave_ptr[d - 1];
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    for (int base = 0; base < g.S; base += 32) {
+      const int s = base + lane;
+      const int d = s < g.S ? p.depth[s] : 0;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      int pos = 0;
+      if (lane == leader && d > 0) {
+        pos = p.cursor[d];
+        p.cursor[d] = pos + __popc(peers);
+      }
+      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (d > 0) p.order[pos + rank] = s;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int s = tid; s < g.S; s += nt) {
+    const int d = p.depth[s];
+    if (d == 1) p.direct[p.resolver[s]] = s;
+    if (recovered) recovered[s] = d > 0 ? 1 : 0;
+  }
+  if (peel_order) {
+    for (int i = tid; i < g.S; i += nt) {
+      if (i < nrec) {
+        const int s = p.order[i];
+        peel_order[3 * i + 0] = s;
+        peel_order[3 * i + 1] = p.resolver[s];
+        peel_order[3 * i + 2] = p.depth[s];
+      } else {
+        peel_order[3 * i + 0] = -1;
+        peel_order[3 * i + 1] = -1;
+        peel_order[3 * i + 2] = -1;
+      }
+    }
+  }
+  if (tid == 0) {
+    p.ctr[CTR_NSURV] = nsurv;
+    p.ctr[CTR_NWAVES] = round;
+    p.ctr[CTR_NREC] = nrec;
+    p.ctr[CTR_ERR] = 0;
+    int32_t inf[BPX_INFO_LEN];
+    for (int i = 0; i < BPX_INFO_LEN; ++i) inf[i] = 0;
+    inf[BPX_INFO_STATUS] = (nrec == g.S) ? BPX_OK : BPX_ERR_UNDECODABLE;
+    inf[BPX_INFO_RECOVERED] = nrec;
+    inf[BPX_INFO_WAVES] = round;
+    inf[BPX_INFO_SURVIVING] = nsurv;
+    inf[BPX_INFO_DIRECT] = round >= 1 ? p.wave_ptr[1] : 0;
+    for (int i = 0; i < BPX_INFO_LEN; ++i) {
+      p.info[i] = inf[i];
+      if (info_out) info_out[i] = inf[i];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
+                            int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
+                            cudaStream_t st) {
+  schedule_kernel<<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out);
+  return cudaGetLastError();
+}
+
+}  // namespace bpx

@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer and index work (surviving cells, peel order, resolvers, depths,
+recovered set) must match bit for bit; floating-point blocks of C must match
+the oracle's FP64 decode within the relative Frobenius tolerance per block
+(1e-5 for FP32 and split-BF16x3, 2e-2 for plain BF16).  Small-integer inputs
+keep every FP32 intermediate exact, so there the match is bit-exact too.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import bpx_oracle as o
+from paper_1904_11563_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-2}
+
+
+def _pair(bpx, name):
+    if name == "table1":
+        return bpx.Code.table1(), o.table1()
+    if name == "table3":
+        return bpx.Code.table3(), o.table3()
+    if name.startswith("sys"):
+        k, e, b = (int(x) for x in name[3:].split("_"))
+        return bpx.Code.systematic(k, e, b), o.systematic_mojette(k, e, b)
+    if name.startswith("A"):
+        n, k, b = (int(x) for x in name[1:].split("_"))
+        return bpx.Code.mojette_a(n, k, b), o.construction_a(n, k, b)
+    if name.startswith("B"):
+        n, k, b, q = (int(x) for x in name[1:].split("_"))
+        return bpx.Code.mojette_b(n, k, b, q), o.construction_b(n, k, b, q)
+    raise ValueError(name)
+
+
+def _masks(code_o, max_e, extra=()):
+    ms = [m for m in W.all_masks(code_o.n, max_e)]
+    for cols in extra:
+        ms.append(W.mask_from_columns(code_o.n, cols))
+    return ms
+
+
+def _oracle_decode(code_o, A, B, h, mask):
+    erased = list(np.nonzero(mask)[0])
+    return o.coded_matmul(code_o, A, B, h, erased)
+
+
+def _rel_block_err(C, R, h, S):
+    errs = []
+    for s in range(S):
+        r = R[s * h:(s + 1) * h]
+        c = C[s * h:(s + 1) * h]
+        nr = np.linalg.norm(r)
+        errs.append(np.linalg.norm(c - r) / nr if nr > 0 else np.linalg.norm(c))
+    return np.array(errs)
+
+
+# ---------------------------------------------------------------- a1: schedule
+
+SCHED_CODES = ["table1", "table3", "sys8_3_8", "sys6_5_5", "A7_4_10", "A11_8_12", "B6_8_4_2"]
+
+
+@pytest.mark.parametrize("name", SCHED_CODES)
+def test_schedule_bit_exact(libbpx, name):
+    bpx = libbpx
+    code, ref = _pair(bpx, name)
+    ws = bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32)
+    rng = np.random.default_rng(1)
+    masks = list(W.all_masks(code.n, min(code.e + 1, 3)))
+    masks += [(rng.random(code.n) < 0.5).astype(np.uint8) for _ in range(10)]
+    for m in masks:
+        dm = torch.from_numpy(m).cuda()
+        order, rec, info = bpx.schedule(code, dm, ws)
+        torch.cuda.synchronize()
+        sch = o.wave_schedule(ref, o.surviving_cells(ref, np.nonzero(m)[0]))
+        exp = np.full((code.num_sources, 3), -1, dtype=np.int32)
+        for i, (s, r, d) in enumerate(sch.order):
+            exp[i] = (s, r, d)
+        assert np.array_equal(order.cpu().numpy(), exp), m
+        assert list(rec.cpu().numpy()) == sch.recovered
+        inf = info.cpu().numpy()
+        assert inf[bpx.INFO_STATUS] == (bpx.OK if sch.ok else bpx.ERR_UNDECODABLE)
+        assert inf[bpx.INFO_RECOVERED] == sum(sch.recovered)
+        assert inf[bpx.INFO_WAVES] == sch.num_waves
+        assert inf[bpx.INFO_SURVIVING] == len(o.surviving_cells(ref, np.nonzero(m)[0]))
+
+
+def test_schedule_large_construction_a(libbpx):
+    """The full-size projection code (16392 sources, ~27.7k cells): bit-exact
+    plan for seeded 8-column erasures."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "A32_24_683")
+    ws = bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32)
+    for t in range(2):
+        m = W.erasure_mask(code.n, 8, 4000 + t)
+        order, rec, info = bpx.schedule(code, torch.from_numpy(m).cuda(), ws)
+        sch = o.wave_schedule(ref, o.surviving_cells(ref, np.nonzero(m)[0]))
+        got = order.cpu().numpy()
+        assert sch.ok
+        assert np.array_equal(got, np.array(sch.order, dtype=np.int32))
+        assert info.cpu().numpy()[bpx.INFO_WAVES] == sch.num_waves
+
+
+# ---------------------------------------------------------------- a2: encode
+
+@pytest.mark.parametrize("name,h", [("table3", 3), ("sys8_3_8", 2), ("A7_4_10", 1)])
+def test_encode_materialized(libbpx, name, h):
+    bpx = libbpx
+    code, ref = _pair(bpx, name)
+    M, K = code.num_sources * h - 1, 40
+    A = W.matrix((M, K), "uniform", 11)
+    ws = bpx.Workspace(code, M, 8, K, h, bpx.FP32)
+    m = W.erasure_mask(code.n, code.e, 5)
+    bpx.schedule(code, torch.from_numpy(m).cuda(), ws)
+    out = bpx.encode(code, torch.from_numpy(A).cuda(), h, ws).cpu().numpy()
+    cells = o.surviving_cells(ref, np.nonzero(m)[0])
+    for i, c in enumerate(cells):
+        exp = o.encode(ref, A, h, c)
+        np.testing.assert_allclose(out[i * h:(i + 1) * h], exp, rtol=1e-6, atol=1e-6)
+
+
+# ---------------------------------------------------------------- whole path
+
+def _run(bpx, code, A, B, h, prec, mask, opts=None):
+    M, K = A.shape
+    N = B.shape[1]
+    ws = bpx.Workspace(code, M, N, K, h, prec)
+    C, info = bpx.coded_matmul(code, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), h, prec,
+                               torch.from_numpy(mask).cuda(), ws, opts=opts)
+    torch.cuda.synchronize()
+    return C.cpu().numpy(), info.cpu().numpy()
+
+
+PRECS = [("fp32", 0)]
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_table1_all_masks_vs_oracle(libbpx, prec):
+    """Workload table1_512: every erasure pattern of <= 2 columns (and the
+    3-column ones the code also tolerates), every block within tolerance."""
+    bpx = libbpx
+    wl = W.WORKLOADS["table1_512"]
+    code, ref = _pair(bpx, "table1")
+    A, B = W.inputs(wl["M"], wl["K"], wl["N"], wl["dist"], wl["seed"])
+    P = bpx.PRECISIONS[prec]
+    for m in _masks(ref, 3):
+        C, info = _run(bpx, code, A, B, wl["h"], P, m)
+        R, sch = _oracle_decode(ref, A, B, wl["h"], m)
+        assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
+        err = _rel_block_err(C, R, wl["h"], ref.num_sources)
+        assert err.max() <= TOL[prec], (m, err)
+
+
+@pytest.mark.parametrize("name,h,M,K,N", [
+    ("table3", 3, 26, 136, 200),       # ragged: M < S h, K and N not tile multiples
+    ("sys8_3_8", 5, 320, 72, 36),
+    ("A7_4_10", 1, 40, 264, 132),      # one-row sources, depth > 1
+    ("B6_8_4_2", 2, 64, 32, 260),
+    ("table1", 130, 520, 64, 8),       # blocks taller than a tile
+])
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_integer_inputs_bit_exact(libbpx, name, h, M, K, N, prec):
+    """Small-integer inputs: every intermediate is an exact integer < 2^24,
+    so the decoded C equals the oracle (and A B) bit for bit."""
+    bpx = libbpx
+    code, ref = _pair(bpx, name)
+    A = W.matrix((M, K), "int", 21)
+    B = W.matrix((K, N), "int", 22)
+    ref_C = o.reference_product(A, B)
+    rng = np.random.default_rng(3)
+    for t in range(6):
+        m = W.erasure_mask(code.n, int(rng.integers(0, code.e + 1)), 100 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+        R, sch = _oracle_decode(ref, A, B, h, m)
+        assert info[bpx.INFO_STATUS] == (bpx.OK if sch.ok else bpx.ERR_UNDECODABLE)
+        assert np.array_equal(C[:M], ref_C), (name, m)
+        assert np.array_equal(C[:M], R[:M])
+
+
+def test_products_and_peel_separately(libbpx):
+    """a3 alone (no direct writes): every surviving cell's product within
+    tolerance of the oracle; then a4 alone fed with those products."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 4, 256, 96, 64
+    A, B = W.inputs(M, K, N, "normal", 31)
+    ws = bpx.Workspace(code, M, N, K, h, bpx.FP32)
+    m = W.erasure_mask(code.n, 3, 77)
+    bpx.schedule(code, torch.from_numpy(m).cuda(), ws)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    P = bpx.coded_products(code, dA, dB, h, bpx.FP32, ws)
+    Pn = P.cpu().numpy()
+    cells = o.surviving_cells(ref, np.nonzero(m)[0])
+    Po = o.coded_products(ref, A, B, h, cells)
+    for c in cells:
+        blk = Pn[c * h:(c + 1) * h]
+        assert np.linalg.norm(blk - Po[c]) / np.linalg.norm(Po[c]) <= 1e-5
+    C = bpx.alloc_C(code, h, N)
+    bpx.peel_decode(code, P, N, h, C, ws, direct_written=False)
+    R, sch = _oracle_decode(ref, A, B, h, m)
+    err = _rel_block_err(C.cpu().numpy(), R, h, ref.num_sources)
+    assert err.max() <= 1e-5
+
+
+def test_undecodable_partial(libbpx):
+    """Four erasures on Table I: status UNDECODABLE, recovered set as the
+    oracle's, recovered blocks correct, the rest untouched."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "table1")
+    h, M, K, N = 8, 32, 16, 12
+    A = W.matrix((M, K), "int", 41)
+    B = W.matrix((K, N), "int", 42)
+    for cols in itertools.combinations(range(5), 4):
+        m = W.mask_from_columns(5, cols)
+        C, info = _run(bpx, code, A, B, h, bpx.FP32, m)
+        sch = o.wave_schedule(ref, o.surviving_cells(ref, cols))
+        assert info[bpx.INFO_STATUS] == bpx.ERR_UNDECODABLE
+        assert info[bpx.INFO_RECOVERED] == sum(sch.recovered)
+        refC = o.reference_product(A, B)
+        for s in range(4):
+            blk = C[s * h:(s + 1) * h]
+            if sch.depth[s] > 0:
+                assert np.array_equal(blk, refC[s * h:(s + 1) * h])
+            else:
+                assert np.all(blk == 0)
+
+
+def test_compensated_peel(libbpx):
+    """compensate_depth = 0 forces the FP64 subtraction on every wave; the
+    result stays within tolerance and equals the plain path on integers."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "table3")
+    h, M, K, N = 6, 54, 48, 40
+    A, B = W.inputs(M, K, N, "loguniform", 51)
+    m = W.mask_from_columns(5, [0, 2])
+    opts = bpx.default_opts(compensate_depth=0)
+    C, info = _run(bpx, code, A, B, h, bpx.FP32, m, opts=opts)
+    R, sch = _oracle_decode(ref, A, B, h, m)
+    err = _rel_block_err(C, R, h, 9)
+    kap = _kappas(ref, A, B, h, m)
+    for s in range(9):
+        assert err[s] <= 1e-5 * max(1.0, kap[s]), (s, err[s], kap[s])
+
+
+def _kappas(ref, A, B, h, m):
+    cells = o.surviving_cells(ref, np.nonzero(m)[0])
+    sch = o.wave_schedule(ref, cells)
+    P = o.coded_products(ref, A, B, h, cells)
+    Cd = o.peel_decode(ref, P, sch, h, B.shape[1])
+    return o.amplification(ref, sch, P, Cd)
+
+
+def test_direct_write_off_matches_on(libbpx):
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 4, 256, 64, 48
+    A = W.matrix((M, K), "int", 61)
+    B = W.matrix((K, N), "int", 62)
+    m = W.erasure_mask(11, 3, 9)
+    C1, _ = _run(bpx, code, A, B, h, bpx.FP32, m)
+    C2, _ = _run(bpx, code, A, B, h, bpx.FP32, m, opts=bpx.default_opts(direct_write=0))
+    assert np.array_equal(C1, C2)
+
+
+def test_host_entry_point_matches_device(libbpx):
+    bpx = libbpx
+    code, ref = _pair(bpx, "table1")
+    h, M, K, N = 16, 64, 32, 24
+    A, B = W.inputs(M, K, N, "uniform", 71)
+    m = W.mask_from_columns(5, [1, 4])
+    C_dev, _ = _run(bpx, code, A, B, h, bpx.FP32, m)
+    ws = bpx.Workspace(code, M, N, K, h, bpx.FP32)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hm = torch.from_numpy(m).pin_memory()
+    hC = torch.zeros((M, N), dtype=torch.float32).pin_memory()
+    dA = torch.empty_like(hA, device="cuda")
+    dB = torch.empty_like(hB, device="cuda")
+    dm = torch.empty_like(hm, device="cuda")
+    dC = bpx.alloc_C(code, h, N)
+    rc, info = bpx.coded_matmul_host(code, hA, hB, h, bpx.FP32, hm, hC, dA, dB, dm, dC, ws)
+    assert rc == bpx.OK and info[bpx.INFO_STATUS] == bpx.OK
+    assert np.array_equal(hC.numpy(), C_dev[:M])

@@ -1,0 +1,88 @@
+"""Host-side checks of libbpx (no GPU needed): the library loads, exports
+every entry point include/bpx.h declares, and builds code graphs identical
+to the oracle's (bit-exact integer work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import bpx_oracle as o
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "bpx.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bpx_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(libbpx):
+    names = _declared()
+    assert len(names) >= 14
+    L = ctypes.CDLL(libbpx.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+CASES = [
+    ("table1", lambda b: b.Code.table1(), lambda: o.table1()),
+    ("table3", lambda b: b.Code.table3(), lambda: o.table3()),
+    ("sys8_3_8", lambda b: b.Code.systematic(8, 3, 8), lambda: o.systematic_mojette(8, 3, 8)),
+    ("sys12_6_4", lambda b: b.Code.systematic(12, 4, 6), lambda: o.systematic_mojette(12, 4, 6)),
+    ("sys6_5_5", lambda b: b.Code.systematic(6, 5, 5), lambda: o.systematic_mojette(6, 5, 5)),
+    ("A5_3_4", lambda b: b.Code.mojette_a(5, 3, 4), lambda: o.construction_a(5, 3, 4)),
+    ("A8_6_6", lambda b: b.Code.mojette_a(8, 6, 6), lambda: o.construction_a(8, 6, 6)),
+    ("A11_8_12", lambda b: b.Code.mojette_a(11, 8, 12), lambda: o.construction_a(11, 8, 12)),
+    ("A9_3_2", lambda b: b.Code.mojette_a(9, 3, 2), lambda: o.construction_a(9, 3, 2)),
+    ("A32_24_683", lambda b: b.Code.mojette_a(32, 24, 683), lambda: o.construction_a(32, 24, 683)),
+    ("B5_6_5_1", lambda b: b.Code.mojette_b(5, 6, 5, 1), lambda: o.construction_b(5, 6, 5, 1)),
+    ("B6_8_4_2", lambda b: b.Code.mojette_b(6, 8, 4, 2), lambda: o.construction_b(6, 8, 4, 2)),
+    ("B12_20_50_2", lambda b: b.Code.mojette_b(12, 20, 50, 2), lambda: o.construction_b(12, 20, 50, 2)),
+]
+
+
+@pytest.mark.parametrize("name,mk_lib,mk_orc", CASES, ids=[c[0] for c in CASES])
+def test_code_graph_matches_oracle(libbpx, name, mk_lib, mk_orc):
+    c = mk_lib(libbpx)
+    r = mk_orc()
+    assert (c.n, c.k, c.b, c.e) == (r.n, r.k, r.b, r.e)
+    assert c.num_sources == r.num_sources
+    assert c.num_cells == r.num_cells
+    assert c.cells == [tuple(x) for x in r.cells]
+    assert list(c.col_of_cell) == list(r.col_of_cell)
+    assert list(c.heights) == list(r.heights)
+    assert c.sigma == r.sigma
+    assert c.eps == pytest.approx(r.eps(), rel=1e-12, abs=1e-15)
+    for j, pq in enumerate(r.proj):
+        if pq is not None:
+            assert (c.proj_p[j], c.proj_q[j]) == pq
+
+
+def test_invalid_parameters_raise(libbpx):
+    with pytest.raises(libbpx.BpxError) as ei:
+        libbpx.Code(libbpx.TABLE1, 5, 3, 2)
+    assert ei.value.code == libbpx.ERR_INVAL and "Table I" in str(ei.value)
+    with pytest.raises(libbpx.BpxError):
+        libbpx.Code(libbpx.MOJETTE_A, 3, 4, 5)       # n < k
+    with pytest.raises(libbpx.BpxError):
+        libbpx.Code(libbpx.SYSTEMATIC, 8, 8, 4)       # no parity
+    with pytest.raises(libbpx.BpxError):
+        libbpx.Code(libbpx.MOJETTE_A, 5, 3, 4, e=1)   # wrong e
+    with pytest.raises(libbpx.BpxError):
+        libbpx.Code(99, 5, 3, 4)
+
+
+def test_workspace_bytes_grow_with_shapes(libbpx):
+    c = libbpx.Code.systematic(8, 3, 8)
+    w0 = libbpx.workspace_bytes(c, 0, 0, 0, 1, libbpx.FP32)
+    w1 = libbpx.workspace_bytes(c, 1024, 256, 256, 128, libbpx.FP32)
+    w2 = libbpx.workspace_bytes(c, 1024, 256, 256, 128, libbpx.BF16X3)
+    assert 0 < w0 < w1 < w2
+    # products: num_cells * h * N floats
+    assert w1 - w0 >= c.num_cells * 128 * 256 * 4
+
+
+def test_build_info(libbpx):
+    assert b"sm_103a" in libbpx.lib().bpx_build_info()

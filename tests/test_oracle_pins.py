@@ -449,3 +449,56 @@ def test_expansion_reproduces_products():
     for s, e in o.expansion(code, sch).items():
         tot = sum(v * P[c] for c, v in e.items())
         assert np.array_equal(tot, Cd[s])
+
+
+@pytest.mark.parametrize("n,k,b,q_e", [(5, 6, 5, 1), (6, 8, 4, 2), (7, 6, 9, 1), (9, 10, 30, 1), (12, 20, 50, 2)])
+def test_eps_construction_b_closed_form(n, k, b, q_e):
+    """Construction B overhead: heights-based eps equals the Lemma B.1 closed
+    form and brute force over every decoding set of columns."""
+    code = o.construction_b(n, k, b, q_e)
+    t = n - code.e
+    assert t == -(-k // 2 ** q_e)
+    closed = o.eps_construction_b_closed_form(n, k, b, q_e)
+    brute = max(sum(code.heights[j] for j in sub)
+                for sub in itertools.combinations(range(n), t)) / (k * b) - 1
+    assert code.eps() == pytest.approx(closed, rel=1e-12)
+    assert brute == pytest.approx(closed, rel=1e-12)
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """A sign error in the bin label of Eq. (moj1) or a dropped term in the
+    peel subtraction must fail the pins above."""
+    good_bins = o.mojette_bins
+
+    def bad_bins(k, b, p, q):
+        offset = (b - 1) * q * o._u(q) + (k - 1) * p * o._u(p)
+        bins = {}
+        for z in range(b):
+            for l in range(k):
+                bins.setdefault(offset - z * q + l * p, []).append(z * k + l)
+        return {lab: sorted(v) for lab, v in bins.items()}
+
+    monkeypatch.setattr(o, "mojette_bins", bad_bins)
+    got = sorted(tuple(v) for v in o.mojette_bins(4, 3, 1, 1).values())
+    assert got != _brute_lines(4, 3, 1, 1)
+    monkeypatch.setattr(o, "mojette_bins", good_bins)
+
+    def bad_peel(code, products, sched, h, N):
+        C = {}
+        for s, r, _d in sched.order:
+            acc = products[r].copy()
+            others = [t for t in code.cells[r] if t != s]
+            for t in others[:-1]:          # drops the last term
+                acc -= C[t]
+            C[s] = acc
+        return C
+
+    code = o.table1()
+    rng = np.random.default_rng(1)
+    A, B = _int_inputs(rng, 8, 6, 5)
+    cells = o.surviving_cells(code, [0, 1])
+    sch = o.wave_schedule(code, cells)
+    P = o.coded_products(code, A, B, 2, cells)
+    Cd = bad_peel(code, P, sch, 2, 5)
+    ref = o.reference_product(A, B)
+    assert any(not np.array_equal(Cd[s], ref[2 * s:2 * s + 2]) for s in Cd)
