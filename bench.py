@@ -132,10 +132,16 @@ class StageEvents:
         return ct.cast(self.arrays[i], ct.POINTER(ct.c_void_p))
 
     def stage_ms(self, i, stage):
+        """Milliseconds between the stage's two events, or None when the path
+        did not record them (the error is cleared so that it does not
+        surface in a later CUDA call)."""
         a = self.arrays[i]
         ms = ct.c_float()
         rc = self.rt.cudaEventElapsedTime(ct.byref(ms), a[2 * stage], a[2 * stage + 1])
-        return ms.value if rc == 0 else None
+        if rc != 0:
+            self.rt.cudaGetLastError()
+            return None
+        return ms.value
 
 
 # ------------------------------------------------------------------ CPU oracle legs
@@ -292,7 +298,10 @@ def run_ours(args, wl):
         inf = info.cpu().numpy()
         assert inf[bpx.INFO_STATUS] == bpx.OK, inf
         stage = {}
+        recorded = ["schedule", "gemm", "peel"] + (["b_prep", "a_prep"] if prec != "fp32" else [])
         for si, nm in enumerate(bpx.STAGE_NAMES):
+            if nm not in recorded:
+                continue
             vals = [sev.stage_ms(i, si) for i in range(steps)]
             vals = [v for v in vals if v is not None and v > 0]
             stage[nm] = sum(vals) / len(vals) if vals else 0.0

@@ -138,7 +138,7 @@ namespace {
 
 int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, int N, int K,
                   int h, int precision, void* ws, size_t ws_bytes, float* d_products, float* d_C,
-                  const bpx_opts* opts, cudaStream_t st) {
+                  const bpx_opts* opts, int32_t* d_info, cudaStream_t st) {
   if (!c || !d_A || !d_B || !ws || !d_products)
     return fail(BPX_ERR_INVAL, "bpx_coded_products: NULL argument");
   if (int rc = check_shapes(c, M, N, K, h)) return rc;
@@ -174,7 +174,7 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
       stage_mark(opts, BPX_STAGE_GEMM, 0, st);
       if (e == cudaSuccess)
         e = bpx::launch_gemm_tc(g, p, a_hi, a_lo, b_hi, b_lo, c->num_cells, N, K, h, split,
-                                d_products, d_C, config, st);
+                                d_products, d_C, config, d_info, st);
       stage_mark(opts, BPX_STAGE_GEMM, 1, st);
       if (e == cudaErrorNotSupported)
         return fail(BPX_ERR_UNSUPPORTED, "bf16 tensor-core path not available in this build");
@@ -213,7 +213,7 @@ extern "C" int bpx_coded_products(const bpx_code* c, const float* d_A, const flo
                                   bpx_stream stream) {
   bpx::clear_error();
   return products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, d_products, d_C, opts,
-                       S(stream));
+                       nullptr, S(stream));
 }
 
 extern "C" int bpx_peel_decode(const bpx_code* c, const float* d_products, int N, int h, float* d_C,
@@ -238,7 +238,7 @@ extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float
   stage_mark(&o, BPX_STAGE_SCHEDULE, 1, S(stream));
   float* products = reinterpret_cast<float*>(static_cast<char*>(ws) + L.products);
   if (int rc = products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, products,
-                             o.direct_write ? d_C : nullptr, &o, S(stream)))
+                             o.direct_write ? d_C : nullptr, &o, d_info, S(stream)))
     return rc;
   return peel_impl(c, products, N, h, d_C, o.direct_write, &o, ws, S(stream));
 }

@@ -92,7 +92,7 @@ cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* A,
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
                            const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
                            bool split3, float* products, float* C_direct, int config,
-                           cudaStream_t st);
+                           int32_t* info_out, cudaStream_t st);
 
 int num_sms();
 

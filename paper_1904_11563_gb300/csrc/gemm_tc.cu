@@ -1,12 +1,427 @@
-// a3 on the tensor cores (placeholder until the tcgen05 kernel lands).
+// a3 on the 5th-generation tensor cores (tcgen05 + TMA + TMEM), sm_103a.
+//
+// Coded products P = A_coded * B over the staged bf16 operands:
+//   A_coded (rows = h * surviving cells, K-major) written by the encode+split
+//   kernel, B^T (N x K, K-major) written by the B split kernel.
+// Split-BF16x3 accumulates hi*hi + hi*lo + lo*hi into one FP32 TMEM
+// accumulator (the lo*lo term is below FP32 rounding); plain BF16 issues the
+// hi*hi MMA only.
+//
+// Persistent warp-specialised kernel, one 128 x 256 output tile at a time:
+//   warp 0     TMA producer: 128B-swizzled 64-wide k-slices of A (hi, lo)
+//              and B (hi, lo) into a ring of shared-memory stages
+//   warp 1     TMEM owner + MMA issuer (one thread): tcgen05.mma kind::f16,
+//              M=128 N=256 K=16, commit -> "stage empty" / "accumulator full"
+//   warps 2-5  epilogue: tcgen05.ld 32x32b from one of two TMEM accumulators
+//              (double buffered so the next tile's MMAs overlap the drain),
+//              rows scattered to the cell's product slot or straight into
+//              the source block of C for depth-1 resolvers.
+// Every mbarrier wait is bounded (clock64 budget); a wait that runs out
+// raises BPX_ERR_TIMEOUT in the plan's info words, tells the other warps to
+// stop, and the CTA still frees its TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
 #include "device_common.cuh"
 
 namespace bpx {
+namespace {
 
-cudaError_t launch_gemm_tc(const DevGraph&, const DevPlan&, const void*, const void*, const void*,
-                           const void*, int, int, int, int, bool, float*, float*, int,
-                           cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;  // bf16 elements = 128 bytes per row: one 128B swizzle atom row
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 512;  // two 256-column FP32 accumulators
+constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the canonical 128-byte
+// swizzled layout (8-row x 128 B atoms, 1024 B between 8-row groups).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFF) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                // leading byte offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;        // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                // descriptor version (tcgen05)
+  d |= static_cast<uint64_t>(2) << 61;                // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            (static_cast<uint32_t>(BN >> 3) << 17) |
+                            (static_cast<uint32_t>(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcParams {
+  DevGraph g;
+  DevPlan p;
+  float* products;
+  float* C_direct;
+  int32_t* info_out;
+  int N, K, h;
+  int group;  // m-tiles per rasterisation band
+};
+
+template <bool kSplit>
+struct Stage {
+  static constexpr uint32_t kA = BM * BK * 2;  // 16 KB
+  static constexpr uint32_t kB = BN * BK * 2;  // 32 KB
+  static constexpr uint32_t kBytes = kSplit ? 2 * (kA + kB) : (kA + kB);
+  // offsets inside a stage
+  static constexpr uint32_t kAhi = 0;
+  static constexpr uint32_t kAlo = kA;
+  static constexpr uint32_t kBhi = kSplit ? 2 * kA : kA;
+  static constexpr uint32_t kBlo = kBhi + kB;
+};
+
+__device__ __forceinline__ void raise_error(const TcParams& P, int code, volatile int* abort_flag) {
+  *abort_flag = 1;
+  atomicExch(&P.p.ctr[CTR_ERR], code);
+  atomicExch(&P.p.info[BPX_INFO_DEVICE_ERR], code);
+  atomicExch(&P.p.info[BPX_INFO_STATUS], code);
+  if (P.info_out) {
+    atomicExch(&P.info_out[BPX_INFO_DEVICE_ERR], code);
+    atomicExch(&P.info_out[BPX_INFO_STATUS], code);
+  }
+}
+
+template <bool kSplit, int kStages>
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
+               const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
+               TcParams P) {
+  using St = Stage<kSplit>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nsurv = P.p.ctr[CTR_NSURV];
+  const int Mc = nsurv * P.h;
+  const int m_tiles = (Mc + BM - 1) / BM;
+  const int n_tiles = (P.N + BN - 1) / BN;
+  const int num_tiles = m_tiles * n_tiles;
+  const int k_blocks = (P.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tfull_bar[a]), 1);
+      mbar_init(smem_u32(&tempty_bar[a]), 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+
+  // tile -> (m, n): bands of `group` m-tiles; inside a band n-major so that
+  // CTAs resident together share a few A row tiles and B column tiles in L2.
+  auto tile_mn = [&](int t, int& m, int& n) {
+    const int band_tiles = P.group * n_tiles;
+    const int band = t / band_tiles;
+    const int r = t - band * band_tiles;
+    const int rows_in_band = min(P.group, m_tiles - band * P.group);
+    m = band * P.group + r % rows_in_band;
+    n = r / rows_in_band;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int kb_all = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        int mt, nt;
+        tile_mn(t, mt, nt);
+        for (int kb = 0; kb < k_blocks; ++kb, ++kb_all) {
+          const int s = kb_all % kStages;
+          const uint32_t ph = static_cast<uint32_t>((kb_all / kStages) & 1) ^ 1u;
+          if (!mbar_wait(smem_u32(&empty_bar[s]), ph, &abort_flag)) {
+            if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+            ok = false;
+            break;
+          }
+          const uint32_t base = smem_u32(smem + s * St::kBytes);
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          mbar_expect_tx(fb, St::kBytes);
+          tma_load_2d(base + St::kAhi, &map_ahi, fb, kb * BK, mt * BM);
+          if (kSplit) tma_load_2d(base + St::kAlo, &map_alo, fb, kb * BK, mt * BM);
+          tma_load_2d(base + St::kBhi, &map_bhi, fb, kb * BK, nt * BN);
+          if (kSplit) tma_load_2d(base + St::kBlo, &map_blo, fb, kb * BK, nt * BN);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int kb_all = 0, it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), static_cast<uint32_t>((it >> 1) & 1) ^ 1u,
+                       &abort_flag)) {
+          if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+          break;
+        }
+        fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+        for (int kb = 0; kb < k_blocks; ++kb, ++kb_all) {
+          const int s = kb_all % kStages;
+          if (!mbar_wait(smem_u32(&full_bar[s]), static_cast<uint32_t>((kb_all / kStages) & 1),
+                         &abort_flag)) {
+            if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t base = smem_u32(smem + s * St::kBytes);
+          const uint64_t ahi = sdesc_sw128(base + St::kAhi);
+          const uint64_t bhi = sdesc_sw128(base + St::kBhi);
+          const uint64_t alo = sdesc_sw128(base + St::kAlo);
+          const uint64_t blo = sdesc_sw128(base + St::kBlo);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            umma_bf16(d_tmem, ahi + adv, bhi + adv, first);
+            if (kSplit) {
+              umma_bf16(d_tmem, ahi + adv, blo + adv, 1u);
+              umma_bf16(d_tmem, alo + adv, bhi + adv, 1u);
+            }
+          }
+          umma_commit(smem_u32(&empty_bar[s]));
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int it = 0;
+    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++it) {
+      const int acc = it & 1;
+      if (!mbar_wait(smem_u32(&tfull_bar[acc]), static_cast<uint32_t>((it >> 1) & 1), &abort_flag)) {
+        if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+        break;
+      }
+      fence_after();
+      int mt, nt;
+      tile_mn(t, mt, nt);
+      const int r = mt * BM + row;
+      float* dst = nullptr;
+      if (r < Mc) {
+        const int ci = r / P.h;
+        const int j = r - ci * P.h;
+        const int cell = P.p.surv[ci];
+        const int ds = P.C_direct ? P.p.direct[cell] : -1;
+        dst = ds >= 0 ? P.C_direct + (static_cast<long long>(ds) * P.h + j) * P.N
+                      : P.products + (static_cast<long long>(cell) * P.h + j) * P.N;
+      }
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                             static_cast<uint32_t>(acc * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(taddr + c * 32, v);
+        if (dst) {
+          const int n0 = nt * BN + c * 32;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int n = n0 + 4 * q;
+            if (n < P.N)
+              *reinterpret_cast<float4*>(dst + n) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D K-major bf16 tensor map: rows x K, box = box_rows x 64 with 128 B swizzle.
+bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box_rows) {
+  auto enc = get_encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <bool kSplit, int kStages>
+cudaError_t launch_impl(const TcParams& P, const void* a_hi, const void* a_lo, const void* b_hi,
+                        const void* b_lo, int num_cells, cudaStream_t st) {
+  CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
+  const long long rows = static_cast<long long>(num_cells) * P.h;
+  if (!make_map(&m_ahi, a_hi, rows, P.K, BM) || !make_map(&m_bhi, b_hi, P.N, P.K, BN))
+    return cudaErrorInvalidValue;
+  if (kSplit) {
+    if (!make_map(&m_alo, a_lo, rows, P.K, BM) || !make_map(&m_blo, b_lo, P.N, P.K, BN))
+      return cudaErrorInvalidValue;
+  } else {
+    m_alo = m_ahi;
+    m_blo = m_bhi;
+  }
+  const size_t smem = static_cast<size_t>(kStages) * Stage<kSplit>::kBytes + 1024;
+  auto kern = gemm_tc_kernel<kSplit, kStages>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const long long m_tiles_max = (rows + BM - 1) / BM;
+  const long long tiles_max = m_tiles_max * ((P.N + BN - 1) / BN);
+  const int grid = static_cast<int>(std::min<long long>(tiles_max, num_sms()));
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, kThreads, smem, st>>>(m_ahi, m_alo, m_bhi, m_blo, P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
+                           const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
+                           bool split3, float* products, float* C_direct, int config,
+                           int32_t* info_out, cudaStream_t st) {
+  TcParams P;
+  P.g = g;
+  P.p = p;
+  P.products = products;
+  P.C_direct = C_direct;
+  P.info_out = info_out;
+  P.N = N;
+  P.K = K;
+  P.h = h;
+  P.group = 16;
+  if (config >= 100) P.group = config - 100;  // rasterisation band override
+  if (P.group < 1) P.group = 1;
+  if (split3) return launch_impl<true, 2>(P, a_hi, a_lo, b_hi, b_lo, num_cells, st);
+  return launch_impl<false, 4>(P, a_hi, a_lo, b_hi, b_lo, num_cells, st);
 }
 
 }  // namespace bpx

@@ -139,7 +139,7 @@ def _run(bpx, code, A, B, h, prec, mask, opts=None):
 PRECS = [("fp32", 0)]
 
 
-@pytest.mark.parametrize("prec", ["fp32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
 def test_table1_all_masks_vs_oracle(libbpx, prec):
     """Workload table1_512: every erasure pattern of <= 2 columns (and the
     3-column ones the code also tolerates), every block within tolerance."""
@@ -163,7 +163,7 @@ def test_table1_all_masks_vs_oracle(libbpx, prec):
     ("B6_8_4_2", 2, 64, 32, 260),
     ("table1", 130, 520, 64, 8),       # blocks taller than a tile
 ])
-@pytest.mark.parametrize("prec", ["fp32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
 def test_integer_inputs_bit_exact(libbpx, name, h, M, K, N, prec):
     """Small-integer inputs: every intermediate is an exact integer < 2^24,
     so the decoded C equals the oracle (and A B) bit for bit."""
@@ -286,3 +286,48 @@ def test_host_entry_point_matches_device(libbpx):
     rc, info = bpx.coded_matmul_host(code, hA, hB, h, bpx.FP32, hm, hC, dA, dB, dm, dC, ws)
     assert rc == bpx.OK and info[bpx.INFO_STATUS] == bpx.OK
     assert np.array_equal(hC.numpy(), C_dev[:M])
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32"])
+def test_many_tiles_per_cta(libbpx, prec):
+    """Bench-shaped code and block height at reduced N, K: ~600 output tiles
+    of 128 x 256, so every persistent CTA runs several tiles and both TMEM
+    accumulators and every barrier phase are exercised."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 128, 8192, 256, 2048
+    A, B = W.inputs(M, K, N, "normal", 81)
+    for t in range(2):
+        m = W.erasure_mask(11, 3, 2000 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        R, sch = _oracle_decode(ref, A, B, h, m)
+        err = _rel_block_err(C, R, h, ref.num_sources)
+        assert err.max() <= TOL[prec], (prec, err.max())
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_full_size_sysmoj_8192_sampled(libbpx, prec):
+    """The benchmark workload at full size (A, B 8192 x 8192 N(0,1), h = 128,
+    3 erased columns) in the benchmark's launch configuration; blocks of C
+    checked against FP64 A_s B for the deepest sources and a direct one."""
+    bpx = libbpx
+    wl = W.WORKLOADS["sysmoj_8192"]
+    code, ref = _pair(bpx, "sys8_3_8")
+    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+    A, B = W.device_inputs(M, K, N, "normal", 2)
+    m = W.erasure_mask(11, 3, wl["mask_seed_base"] + 7)
+    ws = bpx.Workspace(code, M, N, K, h, bpx.PRECISIONS[prec])
+    C, info = bpx.coded_matmul(code, A, B, h, bpx.PRECISIONS[prec], torch.from_numpy(m).cuda(), ws)
+    torch.cuda.synchronize()
+    assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+    sch = o.wave_schedule(ref, o.surviving_cells(ref, list(np.nonzero(m)[0])))
+    deep = sorted(range(64), key=lambda s: -sch.depth[s])[:2]
+    direct = [s for s in range(64) if sch.depth[s] == 1][:1]
+    Ah = A.cpu().numpy()
+    Bh = B.cpu().numpy().astype(np.float64)
+    for s in deep + direct:
+        r = o.row_block(Ah, s, h) @ Bh
+        c = C[s * h:(s + 1) * h].cpu().numpy()
+        err = np.linalg.norm(c - r) / np.linalg.norm(r)
+        assert err <= TOL[prec], (prec, s, sch.depth[s], err)
