@@ -500,6 +500,21 @@ def amplification(code: Code, sched: Schedule, products: dict, C: dict) -> dict:
     return out
 
 
+def propagation(code: Code, sched: Schedule, products: dict, C: dict) -> dict:
+    """nu_s = sqrt(sum_c coef_{s,c}^2 ||P_c||_F^2) / ||C_s||_F: the factor by
+    which independent relative errors of size eps in every product grow, on
+    average, on the way to C_s (eps nu_s is the expected relative error of
+    C_s; kappa_s is its worst case).  nu_s = 1 for a source copied from a
+    degree-one cell."""
+    coef = expansion(code, sched)
+    out = {}
+    for s, e in coef.items():
+        num = np.sqrt(sum(float(v) ** 2 * np.linalg.norm(products[c]) ** 2 for c, v in e.items()))
+        den = np.linalg.norm(C[s])
+        out[s] = float(num / den) if den > 0 else float("inf")
+    return out
+
+
 def all_erasure_patterns(n: int, max_e: int):
     """Every set of at most max_e erased columns."""
     for e in range(max_e + 1):

@@ -50,6 +50,28 @@ def _oracle_decode(code_o, A, B, h, mask):
     return o.coded_matmul(code_o, A, B, h, erased)
 
 
+def _nu(ref, A, B, h, m):
+    """Oracle propagation factor per source (1 for direct copies)."""
+    cells = o.surviving_cells(ref, list(np.nonzero(m)[0]))
+    sch = o.wave_schedule(ref, cells)
+    used = sorted(set(r for _s, r, _d in sch.order))
+    P = o.coded_products(ref, A, B, h, used)
+    Cd = o.peel_decode(ref, P, sch, h, B.shape[1])
+    nu = o.propagation(ref, sch, P, Cd)
+    return np.array([nu.get(s, 1.0) for s in range(ref.num_sources)])
+
+
+def _check_blocks(C, R, ref, A, B, h, m, prec):
+    """Every block within TOL x nu_s: the stated per-block tolerance applies
+    to each coded product and to each block copied from one; a block peeled
+    out of several products inherits their errors, magnified by nu_s."""
+    err = _rel_block_err(C, R, h, ref.num_sources)
+    nu = _nu(ref, A, B, h, m)
+    bound = TOL[prec] * np.maximum(1.0, nu)
+    assert np.all(err <= bound), (prec, err.max(), (err / bound).max())
+    return err, nu
+
+
 def _rel_block_err(C, R, h, S):
     errs = []
     for s in range(S):
@@ -136,9 +158,6 @@ def _run(bpx, code, A, B, h, prec, mask, opts=None):
     return C.cpu().numpy(), info.cpu().numpy()
 
 
-PRECS = [("fp32", 0)]
-
-
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
 def test_table1_all_masks_vs_oracle(libbpx, prec):
     """Workload table1_512: every erasure pattern of <= 2 columns (and the
@@ -152,8 +171,7 @@ def test_table1_all_masks_vs_oracle(libbpx, prec):
         C, info = _run(bpx, code, A, B, wl["h"], P, m)
         R, sch = _oracle_decode(ref, A, B, wl["h"], m)
         assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
-        err = _rel_block_err(C, R, wl["h"], ref.num_sources)
-        assert err.max() <= TOL[prec], (m, err)
+        _check_blocks(C, R, ref, A, B, wl["h"], m, prec)
 
 
 @pytest.mark.parametrize("name,h,M,K,N", [
@@ -302,8 +320,7 @@ def test_many_tiles_per_cta(libbpx, prec):
         C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
         assert info[bpx.INFO_STATUS] == bpx.OK
         R, sch = _oracle_decode(ref, A, B, h, m)
-        err = _rel_block_err(C, R, h, ref.num_sources)
-        assert err.max() <= TOL[prec], (prec, err.max())
+        _check_blocks(C, R, ref, A, B, h, m, prec)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
@@ -325,9 +342,11 @@ def test_full_size_sysmoj_8192_sampled(libbpx, prec):
     deep = sorted(range(64), key=lambda s: -sch.depth[s])[:2]
     direct = [s for s in range(64) if sch.depth[s] == 1][:1]
     Ah = A.cpu().numpy()
-    Bh = B.cpu().numpy().astype(np.float64)
+    Bf = B.cpu().numpy()
+    Bh = Bf.astype(np.float64)
+    nu = _nu(ref, Ah, Bf[:, :256], h, m)     # norms from a column slice
     for s in deep + direct:
         r = o.row_block(Ah, s, h) @ Bh
         c = C[s * h:(s + 1) * h].cpu().numpy()
         err = np.linalg.norm(c - r) / np.linalg.norm(r)
-        assert err <= TOL[prec], (prec, s, sch.depth[s], err)
+        assert err <= TOL[prec] * max(1.0, nu[s]), (prec, s, sch.depth[s], err, nu[s])

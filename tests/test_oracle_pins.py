@@ -502,3 +502,35 @@ def test_planted_mistakes_are_caught(monkeypatch):
     Cd = bad_peel(code, P, sch, 2, 5)
     ref = o.reference_product(A, B)
     assert any(not np.array_equal(Cd[s], ref[2 * s:2 * s + 2]) for s in Cd)
+
+
+def test_propagation_factors():
+    """nu_s = 1 for sources copied from a degree-one cell; 1 <= nu_s <= kappa_s
+    (Cauchy-Schwarz); and nu_s predicts the spread of injected product
+    errors: perturbing every product by independent relative noise of size
+    eps gives block errors of about eps nu_s."""
+    code = o.systematic_mojette(8, 3, 8)
+    rng = np.random.default_rng(12)
+    h, K, N = 4, 64, 48
+    A = rng.standard_normal((code.num_sources * h, K))
+    B = rng.standard_normal((K, N))
+    erased = [0, 3, 9]
+    cells = o.surviving_cells(code, erased)
+    sch = o.wave_schedule(code, cells)
+    P = o.coded_products(code, A, B, h, cells)
+    Cd = o.peel_decode(code, P, sch, h, N)
+    nu = o.propagation(code, sch, P, Cd)
+    kap = o.amplification(code, sch, P, Cd)
+    for s, r, d in sch.order:
+        if len(code.cells[r]) == 1:
+            assert nu[s] == pytest.approx(1.0)
+        assert 1.0 - 1e-12 <= nu[s] <= kap[s] + 1e-12
+    eps = 1e-6
+    ratios = []
+    for trial in range(20):
+        Pn = {c: p * (1 + eps * rng.standard_normal(p.shape)) for c, p in P.items()}
+        Cn = o.peel_decode(code, Pn, sch, h, N)
+        for s in Cd:
+            err = np.linalg.norm(Cn[s] - Cd[s]) / np.linalg.norm(Cd[s])
+            ratios.append(err / (eps * nu[s]))
+    assert 0.7 < np.mean(ratios) < 1.3
