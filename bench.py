@@ -42,6 +42,10 @@ def _parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemm-config", type=int, default=0)
+    ap.add_argument("--precisions", default="",
+                    help="comma list overriding the timed precisions (e.g. 'bf16x3' for profiling)")
+    ap.add_argument("--shape", default="",
+                    help="M,N,K override of the workload (profiling of reduced cases only)")
     return ap.parse_args()
 
 
@@ -237,7 +241,9 @@ def run_ours(args, wl):
 
     # the headline precision
     precs = []
-    if args.precision == "auto":
+    if args.precisions:
+        precs = [x for x in args.precisions.split(",") if x]
+    elif args.precision == "auto":
         precs = ["bf16x3", "fp32"]
     else:
         precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
@@ -328,14 +334,23 @@ def run_ours(args, wl):
         direct = [s for s in range(64) if sch.depth[s] == 1]
         samples = sorted(set(deep[:3] + direct[:1]))
         refs = {s: o.row_block(Ah, s, h) @ Bh for s in samples}
+        # propagation factors from the oracle on a 256-column slice of B
+        cells = o.surviving_cells(ref, list(np.nonzero(last_mask)[0]))
+        used = sorted(set(r_ for _s, r_, _d in sch.order))
+        Bs = Bm[:, :256].cpu().numpy()
+        Po = o.coded_products(ref, Ah, Bs, h, used)
+        nu = o.propagation(ref, sch, Po, o.peel_decode(ref, Po, sch, h, Bs.shape[1]))
         for prec, r in results.items():
             Cn = r["C"]
             errs = []
             for s in samples:
                 blk = Cn[s * h:(s + 1) * h].double().cpu().numpy()
                 errs.append(float(np.linalg.norm(blk - refs[s]) / np.linalg.norm(refs[s])))
-            rel[prec] = {"max": max(errs), "sources": samples,
-                         "depths": [sch.depth[s] for s in samples]}
+            direct_err = [e for e, s in zip(errs, samples) if sch.depth[s] == 1]
+            rel[prec] = {"max": max(errs), "max_direct": max(direct_err) if direct_err else None,
+                         "max_err_over_nu": max(e / max(1.0, nu[s]) for e, s in zip(errs, samples)),
+                         "sources": samples, "depths": [sch.depth[s] for s in samples],
+                         "nu": [round(nu[s], 3) for s in samples], "errs": errs}
 
     # roofline of the dominant kernel (the coded GEMM)
     import json as _j
@@ -422,7 +437,9 @@ def run_ours(args, wl):
 def main():
     args = _parse()
     from paper_1904_11563_gb300 import workloads as W
-    wl = W.WORKLOADS[WORKLOAD]
+    wl = dict(W.WORKLOADS[WORKLOAD])
+    if args.shape:
+        wl["M"], wl["N"], wl["K"] = (int(x) for x in args.shape.split(","))
     if args.impl == "reference":
         run_reference(args, wl)
     else:
