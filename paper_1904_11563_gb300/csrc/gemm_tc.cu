@@ -11,11 +11,18 @@
 //   warp 0     TMA producer: 128B-swizzled 64-wide k-slices of A (hi, lo)
 //              and B (hi, lo) into a ring of shared-memory stages
 //   warp 1     TMEM owner + MMA issuer (one thread): tcgen05.mma kind::f16,
-//              M=128 N=256 K=16, commit -> "stage empty" / "accumulator full"
-//   warps 2-5  epilogue: tcgen05.ld 32x32b from one of two TMEM accumulators
-//              (double buffered so the next tile's MMAs overlap the drain),
-//              rows scattered to the cell's product slot or straight into
-//              the source block of C for depth-1 resolvers.
+//              M=128 N=256 K=16, commit -> "stage empty" / "segment full"
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, 128 columns each.
+//
+// The tensor core adds each MMA's products into its FP32 accumulator with
+// truncation, so the error of a long K sum grows with K.  The K range of a
+// tile is therefore cut into segments of `seg_kb` k-blocks: the MMA warp
+// accumulates a segment into one of two TMEM buffers (starting from zero),
+// and the epilogue warps drain the finished buffer into FP32 registers with
+// round-to-nearest adds while the next segment accumulates in the other
+// buffer.  After a tile's last segment the registers are written out: rows
+// scattered to the cell's product slot, or straight into the source block
+// of C for depth-1 resolvers.
 // Every mbarrier wait is bounded (clock64 budget); a wait that runs out
 // raises BPX_ERR_TIMEOUT in the plan's info words, tells the other warps to
 // stop, and the CTA still frees its TMEM and exits.
@@ -32,8 +39,8 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;  // bf16 elements = 128 bytes per row: one 128B swizzle atom row
-constexpr int kThreads = 192;
-constexpr int kTmemCols = 512;  // two 256-column FP32 accumulators
+constexpr int kThreads = 320;  // producer, MMA, 8 epilogue warps
+constexpr int kTmemCols = 512;  // two 256-column FP32 segment accumulators
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -142,7 +149,8 @@ struct TcParams {
   float* C_direct;
   int32_t* info_out;
   int N, K, h;
-  int group;  // m-tiles per rasterisation band
+  int group;   // m-tiles per rasterisation band
+  int seg_kb;  // k-blocks per TMEM accumulation segment
 };
 
 template <bool kSplit>
@@ -177,7 +185,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
-  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ __align__(8) uint64_t sfull_bar[2], sempty_bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
@@ -188,6 +196,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
   const int n_tiles = (P.N + BN - 1) / BN;
   const int num_tiles = m_tiles * n_tiles;
   const int k_blocks = (P.K + BK - 1) / BK;
+  const int seg_kb = P.seg_kb;
+  const int n_segs = (k_blocks + seg_kb - 1) / seg_kb;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -196,8 +206,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
-      mbar_init(smem_u32(&tfull_bar[a]), 1);
-      mbar_init(smem_u32(&tempty_bar[a]), 4);
+      mbar_init(smem_u32(&sfull_bar[a]), 1);
+      mbar_init(smem_u32(&sempty_bar[a]), 8);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -252,90 +262,104 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      int kb_all = 0, it = 0;
+      int kb_all = 0, g = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++it) {
-        const int acc = it & 1;
-        if (!mbar_wait(smem_u32(&tempty_bar[acc]), static_cast<uint32_t>((it >> 1) & 1) ^ 1u,
-                       &abort_flag)) {
-          if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
-          break;
-        }
-        fence_after();
-        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
-        for (int kb = 0; kb < k_blocks; ++kb, ++kb_all) {
-          const int s = kb_all % kStages;
-          if (!mbar_wait(smem_u32(&full_bar[s]), static_cast<uint32_t>((kb_all / kStages) & 1),
+      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
+          const int buf = g & 1;
+          if (!mbar_wait(smem_u32(&sempty_bar[buf]), static_cast<uint32_t>((g >> 1) & 1) ^ 1u,
                          &abort_flag)) {
             if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t base = smem_u32(smem + s * St::kBytes);
-          const uint64_t ahi = sdesc_sw128(base + St::kAhi);
-          const uint64_t bhi = sdesc_sw128(base + St::kBhi);
-          const uint64_t alo = sdesc_sw128(base + St::kAlo);
-          const uint64_t blo = sdesc_sw128(base + St::kBlo);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
-            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            umma_bf16(d_tmem, ahi + adv, bhi + adv, first);
-            if (kSplit) {
-              umma_bf16(d_tmem, ahi + adv, blo + adv, 1u);
-              umma_bf16(d_tmem, alo + adv, bhi + adv, 1u);
+          const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(buf * BN);
+          const int kb0 = sg * seg_kb, kb1 = min(k_blocks, kb0 + seg_kb);
+          for (int kb = kb0; kb < kb1; ++kb, ++kb_all) {
+            const int s = kb_all % kStages;
+            if (!mbar_wait(smem_u32(&full_bar[s]), static_cast<uint32_t>((kb_all / kStages) & 1),
+                           &abort_flag)) {
+              if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+              ok = false;
+              break;
             }
+            fence_after();
+            const uint32_t base = smem_u32(smem + s * St::kBytes);
+            const uint64_t ahi = sdesc_sw128(base + St::kAhi);
+            const uint64_t bhi = sdesc_sw128(base + St::kBhi);
+            const uint64_t alo = sdesc_sw128(base + St::kAlo);
+            const uint64_t blo = sdesc_sw128(base + St::kBlo);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
+              const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
+              umma_bf16(d_tmem, ahi + adv, bhi + adv, first);
+              if (kSplit) {
+                umma_bf16(d_tmem, ahi + adv, blo + adv, 1u);
+                umma_bf16(d_tmem, alo + adv, bhi + adv, 1u);
+              }
+            }
+            umma_commit(smem_u32(&empty_bar[s]));
           }
-          umma_commit(smem_u32(&empty_bar[s]));
+          if (!ok) break;
+          umma_commit(smem_u32(&sfull_bar[buf]));
         }
-        if (!ok) break;
-        umma_commit(smem_u32(&tfull_bar[acc]));
       }
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half by warp
+    const int e = warp - 2;
     const int quarter = warp & 3;
+    const int half = e >> 2;
     const int row = quarter * 32 + lane;
-    int it = 0;
-    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++it) {
-      const int acc = it & 1;
-      if (!mbar_wait(smem_u32(&tfull_bar[acc]), static_cast<uint32_t>((it >> 1) & 1), &abort_flag)) {
-        if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
-        break;
+    int g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+      float accum[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) accum[i] = 0.f;
+      for (int sg = 0; sg < n_segs; ++sg, ++g) {
+        const int buf = g & 1;
+        if (!mbar_wait(smem_u32(&sfull_bar[buf]), static_cast<uint32_t>((g >> 1) & 1), &abort_flag)) {
+          if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                               static_cast<uint32_t>(buf * BN + half * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float v[32];
+          tmem_ld32(taddr + c * 32, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) accum[c * 32 + i] = __fadd_rn(accum[c * 32 + i], v[i]);
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sempty_bar[buf]));
       }
-      fence_after();
+      if (!ok) break;
       int mt, nt;
       tile_mn(t, mt, nt);
       const int r = mt * BM + row;
-      float* dst = nullptr;
       if (r < Mc) {
         const int ci = r / P.h;
         const int j = r - ci * P.h;
         const int cell = P.p.surv[ci];
         const int ds = P.C_direct ? P.p.direct[cell] : -1;
-        dst = ds >= 0 ? P.C_direct + (static_cast<long long>(ds) * P.h + j) * P.N
-                      : P.products + (static_cast<long long>(cell) * P.h + j) * P.N;
-      }
-      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                             static_cast<uint32_t>(acc * BN);
-#pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        float v[32];
-        tmem_ld32(taddr + c * 32, v);
-        if (dst) {
-          const int n0 = nt * BN + c * 32;
+        float* dst = ds >= 0 ? P.C_direct + (static_cast<long long>(ds) * P.h + j) * P.N
+                             : P.products + (static_cast<long long>(cell) * P.h + j) * P.N;
+        const int n0 = nt * BN + half * 128;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int n = n0 + 4 * q;
-            if (n < P.N)
-              *reinterpret_cast<float4*>(dst + n) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          }
+        for (int q = 0; q < 32; ++q) {
+          const int n = n0 + 4 * q;
+          if (n < P.N)
+            *reinterpret_cast<float4*>(dst + n) =
+                make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
         }
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
     }
   }
 
@@ -418,8 +442,14 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
   P.K = K;
   P.h = h;
   P.group = 16;
-  if (config >= 100) P.group = config - 100;  // rasterisation band override
-  if (P.group < 1) P.group = 1;
+  P.seg_kb = 4;
+  // config: 0 = defaults; otherwise group * 100 + seg_kb (autotuner space)
+  if (config > 0) {
+    P.group = config / 100;
+    P.seg_kb = config % 100;
+  }
+  if (P.group < 1) P.group = 16;
+  if (P.seg_kb < 1) P.seg_kb = 4;
   if (split3) return launch_impl<true, 2>(P, a_hi, a_lo, b_hi, b_lo, num_cells, st);
   return launch_impl<false, 4>(P, a_hi, a_lo, b_hi, b_lo, num_cells, st);
 }
