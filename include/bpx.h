@@ -226,6 +226,26 @@ int bpx_coded_matmul_host(const bpx_code* code, const float* h_A, const float* h
                           float* d_A, float* d_B, uint8_t* d_mask, float* d_C, const bpx_opts* opts,
                           void* d_ws, size_t ws_bytes, int32_t* h_info, bpx_stream stream);
 
+/* a1 without any device allocation by the caller or the library (the paper has
+ * no counterpart: this is a deployment convenience).  Same computation and
+ * outputs as bpx_schedule, but the graph copy and the peel plan live in one
+ * fixed 8 MiB array inside the library instead of a caller workspace.  Meant
+ * for callers that cannot allocate device memory -- e.g. code embedded in a
+ * runtime that owns the device pool, or latency-critical paths that cannot
+ * take the synchronisation of cudaMalloc/cudaFree.  The caller still passes
+ * the mask (input) and the outputs; NULL outputs are skipped.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Codes whose scratch exceeds 8 MiB are rejected with BPX_ERR_INVAL
+ *     (roughly 2 num_edges + 8 num_cells + 6 num_sources int32 words).
+ *   - Every call uploads its code's graph into the shared array and reuses
+ *     it, so calls that overlap on the GPU (other streams, other threads)
+ *     race on it: serialise them.  The plan stays in the array until the next
+ *     call; it is not usable by the workspace-based calls. */
+int bpx_schedule_noalloc(const bpx_code* code, const uint8_t* d_erasure_mask,
+                         int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info,
+                         bpx_stream stream);
+
 /* Default options (direct_write = 1, compensate_depth = -1, autos). */
 bpx_opts bpx_default_opts(void);
 

@@ -84,6 +84,7 @@ def lib():
                                  vp, sz, vp, vp]),
         "bpx_coded_matmul_host": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
                                       f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
+        "bpx_schedule_noalloc": (i, [vp, vp, vp, vp, vp, vp]),
         "bpx_default_opts": (Opts, []),
         "bpx_build_info": (ct.c_char_p, []),
     }

@@ -8,6 +8,7 @@
 // (a warp-parallel ready queue), so the cost is linear in the graph edges
 // plus one short barrier sequence per round.
 #include <climits>
+#include <mutex>
 
 #include "device_common.cuh"
 
@@ -212,3 +213,86 @@ cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* 
 }
 
 }  // namespace bpx
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot allocate device memory themselves: code that runs inside
+// a host runtime which owns the whole device pool (a raw cudaMalloc would
+// bypass its accounting or fail against its cap), or latency-critical callers
+// that cannot afford the device-wide synchronisation cudaMalloc / cudaFree
+// imply.  For them bpx_schedule_noalloc runs the same schedule kernel with its
+// scratch (graph copy + peel plan) in the fixed array below instead of a
+// caller workspace.  Every GPU that loads this library keeps the array until
+// the process exits.
+namespace bpx {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(8) << 20;  // 8 MiB
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocBytes / sizeof(int32_t)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+}  // namespace bpx
+
+extern "C" int bpx_schedule_noalloc(const bpx_code* c, const uint8_t* d_mask, int32_t* d_peel_order,
+                                    uint8_t* d_recovered, int32_t* d_info, bpx_stream stream) {
+  using bpx::fail;
+  bpx::clear_error();
+  if (!c) return fail(BPX_ERR_INVAL, "bpx_schedule_noalloc: code is NULL");
+  if (!d_mask) return fail(BPX_ERR_INVAL, "bpx_schedule_noalloc: erasure mask is NULL");
+  const bpx::WsLayout L = bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32);
+  if (L.total > bpx::kNoAllocBytes)
+    return fail(BPX_ERR_INVAL,
+                "bpx_schedule_noalloc: this code needs %zu bytes of scratch, more than the fixed "
+                "%zu-byte array; use bpx_schedule with a workspace",
+                L.total, bpx::kNoAllocBytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(BPX_ERR_CUDA, "bpx_schedule_noalloc: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= bpx::kMaxDevices) return fail(BPX_ERR_UNSUPPORTED, "device id %d too large", dev);
+  void* base = nullptr;
+  {
+    // First call on a device: look up the array's device address with that
+    // device current (the array's name is only a host-side stand-in).
+    std::lock_guard<std::mutex> lk(bpx::g_noalloc_mu);
+    if (!bpx::g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, bpx::g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(BPX_ERR_CUDA, "bpx_schedule_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      bpx::g_noalloc_ptr[dev] = p;
+    }
+    base = bpx::g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* b = static_cast<char*>(base);
+  struct Part {
+    size_t off;
+    const void* src;
+    size_t bytes;
+  } parts[] = {
+      {L.g_col_of_cell, c->col_of_cell.data(), c->col_of_cell.size() * 4},
+      {L.g_cell_ptr, c->cell_ptr.data(), c->cell_ptr.size() * 4},
+      {L.g_cell_src, c->cell_src.data(), c->cell_src.size() * 4},
+      {L.g_src_ptr, c->src_ptr.data(), c->src_ptr.size() * 4},
+      {L.g_src_cell, c->src_cell.data(), c->src_cell.size() * 4},
+  };
+  // The graph of this call's code replaces whatever the previous call left;
+  // the kernel initialises every plan array it reads.
+  for (const Part& pt : parts) {
+    if (pt.bytes == 0) continue;
+    e = cudaMemcpyAsync(b + pt.off, pt.src, pt.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(BPX_ERR_CUDA, "bpx_schedule_noalloc: copy: %s", cudaGetErrorString(e));
+  }
+  const bpx::DevGraph g = bpx::make_graph(c, base, L);
+  const bpx::DevPlan p = bpx::make_plan(base, L);
+  e = bpx::launch_schedule(g, p, d_mask, d_peel_order, d_recovered, d_info, st);
+  if (e != cudaSuccess) return fail(BPX_ERR_CUDA, "bpx_schedule_noalloc: launch: %s", cudaGetErrorString(e));
+  return BPX_OK;
+}
+
