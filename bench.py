@@ -31,6 +31,34 @@ sys.path.insert(0, ROOT)
 METRIC = "useful TFLOP/s of coded A·B w/ e erasures, BF16x3 vs FP32; rel. error"
 WORKLOAD = "sysmoj_8192"
 
+CODE_TEXT = {
+    "sysmoj_8192": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, slopes 0,+1,-1)",
+    "mojA_16384": "Mojette Construction A n=32 (k=24 x b=683 grid, q=1, p=-15..16), e=8",
+}
+
+
+def _lib_code(bpx, wl):
+    kind, *args = wl["code"]
+    return {"systematic": lambda: bpx.Code.systematic(*args),
+            "mojette_a": lambda: bpx.Code.mojette_a(*args),
+            "table1": bpx.Code.table1, "table3": bpx.Code.table3}[kind]()
+
+
+def _oracle_code(o, wl):
+    kind, *args = wl["code"]
+    return {"systematic": lambda: o.systematic_mojette(*args),
+            "mojette_a": lambda: o.construction_a(*args),
+            "table1": o.table1, "table3": o.table3}[kind]()
+
+
+def _n_cols(wl):
+    kind, *args = wl["code"]
+    return {"systematic": lambda: args[0] + args[1], "mojette_a": lambda: args[0]}.get(kind, lambda: 5)()
+
+
+def _mask(W, wl, t):
+    return W.erasure_mask(_n_cols(wl), wl["e"], wl["mask_seed_base"] + (t % wl.get("trials", 100)))
+
 
 def _parse():
     ap = argparse.ArgumentParser()
@@ -44,6 +72,7 @@ def _parse():
     ap.add_argument("--gemm-config", type=int, default=0)
     ap.add_argument("--precisions", default="",
                     help="comma list overriding the timed precisions (e.g. 'bf16x3' for profiling)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(CODE_TEXT))
     ap.add_argument("--shape", default="",
                     help="M,N,K override of the workload (profiling of reduced cases only)")
     return ap.parse_args()
@@ -52,12 +81,13 @@ def _parse():
 # ------------------------------------------------------------------ helpers
 
 def _config(wl):
-    return {"workload": WORKLOAD,
-            "code": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, slopes 0,+1,-1)",
+    mb = 4 * wl["M"] * wl["K"] / 1e6
+    return {"workload": wl["name"], "code": CODE_TEXT[wl["name"]],
             "M": wl["M"], "N": wl["N"], "K": wl["K"], "h": wl["h"], "erasures": wl["e"],
-            "trials": wl["trials"], "mask_seeds": f"{wl['mask_seed_base']}+t, t=step mod {wl['trials']}",
-            "inputs": "A, B iid N(0,1) FP32, seeded",
-            "l2": "inputs larger than L2 (A, B 256 MB each; no flush)"}
+            "trials": wl.get("trials", 100),
+            "mask_seeds": f"{wl['mask_seed_base']}+t, t=step mod {wl.get('trials', 100)}",
+            "inputs": f"A, B iid {'N(0,1)' if wl['dist'] == 'normal' else 'U(-1,1)'} FP32, seeded",
+            "l2": f"inputs larger than L2 (A {mb:.0f} MB; no flush)"}
 
 
 class ClockSampler:
@@ -150,11 +180,11 @@ class StageEvents:
 
 # ------------------------------------------------------------------ CPU oracle legs
 
-def _oracle_sample(A, B, h, mask, ncols):
+def _oracle_sample(A, B, h, mask, ncols, wl):
     """Runs the FP64 oracle's whole coded path on the first ncols columns of
     B (the path is columnwise separable); returns seconds."""
     from oracle import bpx_oracle as o
-    code = o.systematic_mojette(8, 3, 8)
+    code = _oracle_code(o, wl)
     t0 = time.perf_counter()
     C, sch = o.coded_matmul(code, A, B[:, :ncols], h, list(np.nonzero(mask)[0]))
     dt = time.perf_counter() - t0
@@ -173,12 +203,12 @@ def cpu_baseline(A, B, wl, budget_s=12.0):
     """The oracle as it stands on a bounded column sample of the workload."""
     M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
     from paper_1904_11563_gb300 import workloads as W
-    mask = W.erasure_mask(11, 3, wl["mask_seed_base"])
+    mask = _mask(W, wl, 0)
     cols = 256
-    t = _oracle_sample(A, B, h, mask, cols)
+    t = _oracle_sample(A, B, h, mask, cols, wl)
     total_t, total_cols = t, cols
     while total_t < budget_s and total_cols + cols <= N:
-        total_t += _oracle_sample(A, B, h, mask, cols)
+        total_t += _oracle_sample(A, B, h, mask, cols, wl)
         total_cols += cols
     useful = 2.0 * M * K * total_cols
     return {"value": useful / total_t / 1e12, "unit": "TFLOP/s", "cores": _cores(), "kind": "oracle",
@@ -192,14 +222,14 @@ def run_reference(args, wl):
         return
     from paper_1904_11563_gb300 import workloads as W
     M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
-    A = W.matrix((M, K), "normal", 2)
-    B = W.matrix((K, N), "normal", 3)
+    A = W.matrix((M, K), wl["dist"], wl["seed"])
+    B = W.matrix((K, N), wl["dist"], wl["seed"] + 1)
     cols = 128
     warm = max(args.warmup, 3)
     times = []
     for i in range(warm + args.steps):
-        mask = W.erasure_mask(11, 3, wl["mask_seed_base"] + (i % wl["trials"]))
-        dt = _oracle_sample(A, B, h, mask, cols)
+        mask = _mask(W, wl, i)
+        dt = _oracle_sample(A, B, h, mask, cols, wl)
         if i >= warm:
             times.append(dt)
     tot = sum(times)
@@ -232,10 +262,11 @@ def run_ours(args, wl):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
-    code = bpx.Code.systematic(8, 3, 8)
-    A, Bm = W.device_inputs(M, K, N, "normal", 2, device=dev)
-    masks = torch.from_numpy(np.stack([W.erasure_mask(11, 3, wl["mask_seed_base"] + t)
-                                       for t in range(wl["trials"])])).to(dev)
+    code = _lib_code(bpx, wl)
+    A, Bm = W.device_inputs(M, K, N, wl["dist"], wl["seed"], device=dev)
+    trials = wl.get("trials", 100)
+    wl["trials"] = trials
+    masks = torch.from_numpy(np.stack([_mask(W, wl, t) for t in range(trials)])).to(dev)
     warm = max(args.warmup, 3)
     steps = args.steps
 
@@ -255,10 +286,10 @@ def run_ours(args, wl):
         gpu_index = int(cvd.split(",")[local].strip())
 
     surv_rows = []
-    for t in range(wl["trials"]):
-        m = W.erasure_mask(11, 3, wl["mask_seed_base"] + t)
-        surv = sum(int(h_) for j, h_ in enumerate([8] * 8 + [8, 15, 15]) if not m[j])
-        surv_rows.append(surv * h)
+    col_cells = np.diff(code.col_ptr)
+    for t in range(trials):
+        m = _mask(W, wl, t)
+        surv_rows.append(int(sum(int(col_cells[j]) for j in range(code.n) if not m[j])) * h)
 
     for prec in precs:
         P = bpx.PRECISIONS[prec]
@@ -324,7 +355,7 @@ def run_ours(args, wl):
     # relative error per block on sampled sources vs FP64 A_s B (numpy), the
     # depths taken from the library's own plan for the last timed mask
     rel = {}
-    last_mask = torch.from_numpy(W.erasure_mask(11, 3, wl["mask_seed_base"] + ((warm + steps - 1) % wl["trials"]))).to(dev)
+    last_mask = torch.from_numpy(_mask(W, wl, warm + steps - 1)).to(dev)
     ws_s = bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32, device=dev)
     order, _rec, _inf = bpx.schedule(code, last_mask, ws_s)
     order = order.cpu().numpy()
@@ -334,7 +365,7 @@ def run_ours(args, wl):
         Bh = Bm.cpu().numpy().astype(np.float64)
         deep = sorted(depth, key=lambda s_: -depth[s_])[:3]
         direct = [s_ for s_ in sorted(depth) if depth[s_] == 1][:1]
-        samples = sorted(set(deep + direct))
+        samples = [s_ for s_ in sorted(set(deep + direct)) if (s_ + 1) * h <= M]
         refs = {s_: Ah[s_ * h:(s_ + 1) * h].astype(np.float64) @ Bh for s_ in samples}
         for prec, r in results.items():
             Cn = r["C"]
@@ -352,7 +383,7 @@ def run_ours(args, wl):
     peel_bytes = []
     deg = np.diff(code.cell_ptr)
     for i in range(steps):
-        mk = torch.from_numpy(W.erasure_mask(11, 3, wl["mask_seed_base"] + ((warm + i) % wl["trials"]))).to(dev)
+        mk = torch.from_numpy(_mask(W, wl, warm + i)).to(dev)
         od, _r2, _i2 = bpx.schedule(code, mk, ws_s)
         od = od.cpu().numpy()
         peel_bytes.append(sum(int(deg[r_] + 1) * h * N * 4 for s_, r_, d_ in od if s_ >= 0 and d_ >= 2))
@@ -417,8 +448,8 @@ def run_ours(args, wl):
         hC = torch.empty((M, N), dtype=torch.float32).pin_memory()
         dA = torch.empty_like(A)
         dB = torch.empty_like(Bm)
-        dmask = torch.empty(11, dtype=torch.uint8, device=dev)
-        hmasks = [torch.from_numpy(W.erasure_mask(11, 3, wl["mask_seed_base"] + t)).pin_memory()
+        dmask = torch.empty(code.n, dtype=torch.uint8, device=dev)
+        hmasks = [torch.from_numpy(_mask(W, wl, t)).pin_memory()
                   for t in range(wl["trials"])]
         ws = R["ws"]
         dC = R["C"]
@@ -432,7 +463,7 @@ def run_ours(args, wl):
             assert rc == bpx.OK
         dt = (time.perf_counter() - t_s) / e2e_steps
         line["e2e"] = {"value": useful / dt / 1e12, "unit": "TFLOP/s",
-                       "h2d_bytes_per_step": 4 * (M * K + K * N) + 11,
+                       "h2d_bytes_per_step": 4 * (M * K + K * N) + code.n,
                        "d2h_bytes_per_step": 4 * M * N + 4 * bpx.INFO_LEN,
                        "ms_per_step": dt * 1e3, "api": "bpx_coded_matmul_host"}
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -448,7 +479,8 @@ def run_ours(args, wl):
 def main():
     args = _parse()
     from paper_1904_11563_gb300 import workloads as W
-    wl = dict(W.WORKLOADS[WORKLOAD])
+    wl = dict(W.WORKLOADS[args.workload])
+    wl["name"] = args.workload
     if args.shape:
         wl["M"], wl["N"], wl["K"] = (int(x) for x in args.shape.split(","))
     if args.impl == "reference":

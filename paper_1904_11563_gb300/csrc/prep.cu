@@ -16,8 +16,9 @@ namespace bpx {
 namespace {
 
 constexpr int kEncThreads = 256;
+constexpr int kEncVec = 8;  // consecutive K elements per thread (two float4 loads per source)
 
-// One CTA per (coded row, 1024-column chunk); blockIdx.x walks the coded rows
+// One CTA per (coded row, 2048-column chunk); blockIdx.x walks the coded rows
 // fastest so that CTAs resident together read the same K-chunk of A (L2 reuse
 // of a source block across the cells that contain it).
 template <int kMode>  // 0: FP32 out, 1: bf16 hi only, 2: bf16 hi + lo
@@ -30,67 +31,86 @@ encode_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, 
   const int ci = row / h, j = row - ci * h;
   const int cell = p.surv[ci];
   const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
-  const int k4 = (blockIdx.y * kEncThreads + threadIdx.x) * 4;
-  if (k4 >= K) return;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int k8 = (blockIdx.y * kEncThreads + threadIdx.x) * kEncVec;
+  if (k8 >= K) return;
+  const bool full = k8 + kEncVec <= K;  // K % 8 == 0, so a chunk is full or absent
+  float acc[kEncVec];
+#pragma unroll
+  for (int i = 0; i < kEncVec; ++i) acc[i] = 0.f;
   for (int e = e0; e < e1; ++e) {
-    const long long arow = static_cast<long long>(g.cell_src[e]) * h + j;
-    if (arow >= M) continue;
-    const float4 x = __ldg(reinterpret_cast<const float4*>(A + arow * K + k4));
-    acc.x += x.x;
-    acc.y += x.y;
-    acc.z += x.z;
-    acc.w += x.w;
+    const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+    if (arow >= M || !full) continue;
+    const float4* src = reinterpret_cast<const float4*>(A + arow * K + k8);
+    const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+    acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
+    acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
   }
-  const long long o = static_cast<long long>(row) * K + k4;
+  if (!full) return;
+  const long long o = static_cast<long long>(row) * K + k8;
   if (kMode == 0) {
-    *reinterpret_cast<float4*>(out_f32 + o) = acc;
+    float4* d = reinterpret_cast<float4*>(out_f32 + o);
+    d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    d[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
   } else {
-    const __nv_bfloat162 h01 = __floats2bfloat162_rn(acc.x, acc.y);
-    const __nv_bfloat162 h23 = __floats2bfloat162_rn(acc.z, acc.w);
-    uint2 hv;
-    hv.x = *reinterpret_cast<const uint32_t*>(&h01);
-    hv.y = *reinterpret_cast<const uint32_t*>(&h23);
-    *reinterpret_cast<uint2*>(out_hi + o) = hv;
-    if (kMode == 2) {
-      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-      const __nv_bfloat162 l01 = __floats2bfloat162_rn(acc.x - f01.x, acc.y - f01.y);
-      const __nv_bfloat162 l23 = __floats2bfloat162_rn(acc.z - f23.x, acc.w - f23.y);
-      uint2 lv;
-      lv.x = *reinterpret_cast<const uint32_t*>(&l01);
-      lv.y = *reinterpret_cast<const uint32_t*>(&l23);
-      *reinterpret_cast<uint2*>(out_lo + o) = lv;
+    uint32_t hv[4], lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(acc[2 * q], acc[2 * q + 1]);
+      hv[q] = *reinterpret_cast<const uint32_t*>(&hh);
+      if (kMode == 2) {
+        const float2 f = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(acc[2 * q] - f.x, acc[2 * q + 1] - f.y);
+        lv[q] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
     }
+    *reinterpret_cast<uint4*>(out_hi + o) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    if (kMode == 2) *reinterpret_cast<uint4*>(out_lo + o) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
   }
 }
 
 // B (K x N row-major FP32) -> Bt (N x K row-major bf16) through a 64 x 64
-// shared-memory tile: coalesced FP32 reads along N, bf16x2 writes along K.
+// shared-memory tile: float4 reads along N, 16-byte bf16 writes along K.
 constexpr int kTile = 64;
 __global__ void __launch_bounds__(256)
 b_split_kernel(const float* __restrict__ B, int K, int N, __nv_bfloat16* bt_hi,
                __nv_bfloat16* bt_lo) {
   __shared__ float tile[kTile][kTile + 1];
   const int n0 = blockIdx.x * kTile, k0 = blockIdx.y * kTile;
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
-  for (int r = ty; r < kTile; r += 4) {
-    const int k = k0 + r, n = n0 + tx;
-    tile[r][tx] = (k < K && n < N) ? __ldg(B + static_cast<long long>(k) * N + n) : 0.f;
+  {
+    // 64 rows (k) x 16 float4 (n): 4 float4 per thread
+    const int c4 = threadIdx.x & 15, r0 = threadIdx.x >> 4;  // 16 x 16
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + 16 * i, k = k0 + r, n = n0 + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < K && n < N) v = __ldg(reinterpret_cast<const float4*>(B + static_cast<long long>(k) * N + n));
+      tile[r][4 * c4 + 0] = v.x;
+      tile[r][4 * c4 + 1] = v.y;
+      tile[r][4 * c4 + 2] = v.z;
+      tile[r][4 * c4 + 3] = v.w;
+    }
   }
   __syncthreads();
-  // write: thread handles (n = n0 + row, k = k0 + 2*c .. +1)
-  const int c = threadIdx.x & 31, rr = threadIdx.x >> 5;  // 32 x 8
-  for (int r = rr; r < kTile; r += 8) {
-    const int n = n0 + r, k = k0 + 2 * c;
+  // 64 n-rows x 8 chunks of 8 k: thread -> (n = t / 8, chunk = t % 8), two rounds
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int t = threadIdx.x + 256 * i;
+    const int r = t >> 3, kc = t & 7;
+    const int n = n0 + r, k = k0 + 8 * kc;
     if (n >= N || k >= K) continue;
-    const float x0 = tile[2 * c][r], x1 = tile[2 * c + 1][r];
-    const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
-    const long long o = static_cast<long long>(n) * K + k;
-    *reinterpret_cast<__nv_bfloat162*>(bt_hi + o) = hv;
-    if (bt_lo) {
-      const float2 f = __bfloat1622float2(hv);
-      *reinterpret_cast<__nv_bfloat162*>(bt_lo + o) = __floats2bfloat162_rn(x0 - f.x, x1 - f.y);
+    uint32_t hv[4], lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x0 = tile[8 * kc + 2 * q][r], x1 = tile[8 * kc + 2 * q + 1][r];
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
+      hv[q] = *reinterpret_cast<const uint32_t*>(&hh);
+      const float2 f = __bfloat1622float2(hh);
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - f.x, x1 - f.y);
+      lv[q] = *reinterpret_cast<const uint32_t*>(&ll);
     }
+    const long long o = static_cast<long long>(n) * K + k;
+    *reinterpret_cast<uint4*>(bt_hi + o) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    if (bt_lo) *reinterpret_cast<uint4*>(bt_lo + o) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
   }
 }
 
@@ -100,7 +120,7 @@ cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* 
                               int h, float* out, cudaStream_t st) {
   const long long rows = static_cast<long long>(g.num_cells) * h;
   if (rows == 0 || K == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(rows), (K / 4 + kEncThreads - 1) / kEncThreads);
+  dim3 grid(static_cast<unsigned>(rows), (K / kEncVec + kEncThreads - 1) / kEncThreads);
   encode_kernel<0><<<grid, kEncThreads, 0, st>>>(g, p, A, M, K, h, out, nullptr, nullptr);
   return cudaGetLastError();
 }
@@ -109,7 +129,7 @@ cudaError_t launch_encode_split(const DevGraph& g, const DevPlan& p, const float
                                 int h, void* a_hi, void* a_lo, cudaStream_t st) {
   const long long rows = static_cast<long long>(g.num_cells) * h;
   if (rows == 0 || K == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(rows), (K / 4 + kEncThreads - 1) / kEncThreads);
+  dim3 grid(static_cast<unsigned>(rows), (K / kEncVec + kEncThreads - 1) / kEncThreads);
   auto hi = static_cast<__nv_bfloat16*>(a_hi);
   auto lo = static_cast<__nv_bfloat16*>(a_lo);
   if (lo)

@@ -100,6 +100,9 @@ def device_inputs(M: int, K: int, N: int, dist: str, seed: int, device="cuda"):
     elif dist == "uniform":
         A = torch.rand((M, K), generator=g, device=device, dtype=torch.float32).mul_(2).sub_(1)
         B = torch.rand((K, N), generator=g, device=device, dtype=torch.float32).mul_(2).sub_(1)
+    elif dist == "int":
+        A = torch.randint(-2, 3, (M, K), generator=g, device=device).to(torch.float32)
+        B = torch.randint(-2, 3, (K, N), generator=g, device=device).to(torch.float32)
     else:
         raise ValueError(dist)
     return A, B

@@ -350,3 +350,35 @@ def test_full_size_sysmoj_8192_sampled(libbpx, prec):
         c = C[s * h:(s + 1) * h].cpu().numpy()
         err = np.linalg.norm(c - r) / np.linalg.norm(r)
         assert err <= TOL[prec] * max(1.0, nu[s]), (prec, s, sch.depth[s], err, nu[s])
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32"])
+def test_construction_a_full_size_integer_bit_exact(libbpx, prec):
+    """Workload mojA_16384 at full size (Construction A n=32, k=24, b=683,
+    h=1: 16392 one-row sources, ~20.9k coded rows, A 16384 x 16384,
+    B 16384 x 8192, 8 erased columns, hundreds of peel waves) with integer
+    inputs in [-2, 2]: every product and every peeled row is an exact
+    integer below 2^24, so the decoded rows must equal A B bit for bit --
+    checked on the deepest rows, direct rows and random rows."""
+    bpx = libbpx
+    wl = W.WORKLOADS["mojA_16384"]
+    code = bpx.Code.mojette_a(32, 24, 683)
+    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+    A, B = W.device_inputs(M, K, N, "int", 40)
+    m = torch.from_numpy(W.erasure_mask(32, 8, wl["mask_seed_base"])).cuda()
+    ws = bpx.Workspace(code, M, N, K, h, bpx.PRECISIONS[prec])
+    C, info = bpx.coded_matmul(code, A, B, h, bpx.PRECISIONS[prec], m, ws)
+    torch.cuda.synchronize()
+    inf = info.cpu().numpy()
+    assert inf[bpx.INFO_STATUS] == bpx.OK
+    assert inf[bpx.INFO_WAVES] > 100
+    order, _rec, _i = bpx.schedule(code, m, bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32))
+    order = order.cpu().numpy()
+    rows = [int(s) for s, _r, d in order[::-1][:6] if s < M]          # deepest
+    rows += [int(s) for s, _r, d in order if d == 1][:3]               # direct
+    rows += list(np.random.default_rng(0).choice(M, 6, replace=False))
+    Bh = B.cpu().numpy().astype(np.float64)
+    Cn = C[rows].cpu().numpy()
+    An = A[rows].cpu().numpy().astype(np.float64)
+    ref = An @ Bh
+    assert np.array_equal(Cn, ref), (prec, np.abs(Cn - ref).max())
