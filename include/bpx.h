@@ -237,7 +237,7 @@ int bpx_coded_matmul_host(const bpx_code* code, const float* h_A, const float* h
  *   - The first call on each device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
  *   - Codes whose scratch exceeds 8 MiB are rejected with BPX_ERR_INVAL
- *     (roughly 2 num_edges + 8 num_cells + 6 num_sources int32 words).
+ *     (roughly 3 num_edges + 8 num_cells + 9 num_sources int32 words).
  *   - Every call uploads its code's graph into the shared array and reuses
  *     it, so calls that overlap on the GPU (other streams, other threads)
  *     race on it: serialise them.  The plan stays in the array until the next

@@ -36,6 +36,7 @@ struct WsLayout {
   // plan (int32)
   size_t p_info, p_ctr, p_cnt, p_surv, p_direct, p_front0, p_front1, p_cand;
   size_t p_depth, p_resolver, p_order, p_newsrc, p_wave_ptr, p_cursor;
+  size_t p_pl_res, p_pl_ptr, p_pl_list;  // peel list: resolver and subtrahends per order entry
   size_t plan_end;
   // products (float, num_cells * h * N)
   size_t products;

@@ -300,6 +300,9 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
   L.p_newsrc = take(S * i32);
   L.p_wave_ptr = take((S + 2) * i32);
   L.p_cursor = take((S + 2) * i32);
+  L.p_pl_res = take(S * i32);
+  L.p_pl_ptr = take((S + 1) * i32);
+  L.p_pl_list = take(E * i32);
   L.plan_end = off;
   const size_t hN = static_cast<size_t>(h > 0 ? h : 0) * static_cast<size_t>(N > 0 ? N : 0);
   L.products = take(C * hN * sizeof(float));

@@ -35,6 +35,12 @@ struct DevPlan {
   int32_t* newsrc;    // sources recovered in the current round
   int32_t* wave_ptr;  // order[wave_ptr[d-1] .. wave_ptr[d]) = sources of depth d
   int32_t* cursor;    // placement cursors (scratch)
+  // Peel list, one entry per position i of `order`: the resolver of order[i]
+  // and, in pl_list[pl_ptr[i] .. pl_ptr[i+1]), the other sources of that
+  // resolver in ascending id (the blocks subtracted from its product).
+  int32_t* pl_res;
+  int32_t* pl_ptr;
+  int32_t* pl_list;
 };
 
 inline DevGraph make_graph(const bpx_code* c, const void* ws, const WsLayout& L) {
@@ -71,6 +77,9 @@ inline DevPlan make_plan(const void* ws, const WsLayout& L) {
   p.newsrc = at(L.p_newsrc);
   p.wave_ptr = at(L.p_wave_ptr);
   p.cursor = at(L.p_cursor);
+  p.pl_res = at(L.p_pl_res);
+  p.pl_ptr = at(L.p_pl_ptr);
+  p.pl_list = at(L.p_pl_list);
   return p;
 }
 

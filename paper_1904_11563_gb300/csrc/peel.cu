@@ -25,8 +25,59 @@ __device__ __forceinline__ float4 ldg_stream(const float4* p) {
   return v;
 }
 
+__device__ __forceinline__ void sub4(float4& a, const float4& x) {
+  a.x -= x.x;
+  a.y -= x.y;
+  a.z -= x.z;
+  a.w -= x.w;
+}
+
+// One (source, float4) item: C_s[v] = P_r[v] - sum of the listed blocks,
+// subtracted in ascending source id.
+template <bool kF64>
+__device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, float4* C4, long long nv,
+                                          int i, long long v) {
+  const int s = p.order[i];
+  const int r = p.pl_res[i];
+  int e = p.pl_ptr[i];
+  const int e1 = p.pl_ptr[i + 1];
+  const float4 pr = ldg_stream(P4 + static_cast<long long>(r) * nv + v);
+  if (!kF64) {
+    // 16 list entries, then 16 independent block loads, then the ascending
+    // subtractions: two round trips per 16 subtrahends.
+    constexpr int kB = 16;
+    float4 acc = pr;
+    for (; e < e1; e += kB) {
+      int t[kB];
+      float4 x[kB];
+#pragma unroll
+      for (int q = 0; q < kB; ++q) t[q] = (e + q < e1) ? p.pl_list[e + q] : -1;
+#pragma unroll
+      for (int q = 0; q < kB; ++q)
+        x[q] = t[q] >= 0 ? C4[static_cast<long long>(t[q]) * nv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < kB; ++q)
+        if (t[q] >= 0) sub4(acc, x[q]);
+    }
+    C4[static_cast<long long>(s) * nv + v] = acc;
+  } else {
+    // Deep chains: subtract in FP64 and round once.
+    double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
+    for (; e < e1; ++e) {
+      const float4 x = C4[p.pl_list[e] * nv + v];
+      ax -= x.x;
+      ay -= x.y;
+      az -= x.z;
+      aw -= x.w;
+    }
+    C4[static_cast<long long>(s) * nv + v] =
+        make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
+                    static_cast<float>(aw));
+  }
+}
+
 __global__ void __launch_bounds__(kPeelThreads)
-peel_kernel(DevGraph g, DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk,
+peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk,
             int first_wave, int compensate_depth) {
   const int nwaves = p.ctr[CTR_NWAVES];
   const long long v0 = static_cast<long long>(blockIdx.x) * chunk;
@@ -42,38 +93,10 @@ peel_kernel(DevGraph g, DevPlan p, const float* __restrict__ P, float* C, long l
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int j = it / clen;
       const long long v = v0 + (it - j * clen);
-      const int s = p.order[o0 + j];
-      const int r = p.resolver[s];
-      const int e0 = g.cell_ptr[r], e1 = g.cell_ptr[r + 1];
-      const float4 pr = ldg_stream(P4 + static_cast<long long>(r) * nv + v);
-      if (!comp) {
-        float4 acc = pr;
-        for (int e = e0; e < e1; ++e) {
-          const int t = g.cell_src[e];
-          if (t == s) continue;
-          const float4 x = C4[static_cast<long long>(t) * nv + v];
-          acc.x -= x.x;
-          acc.y -= x.y;
-          acc.z -= x.z;
-          acc.w -= x.w;
-        }
-        C4[static_cast<long long>(s) * nv + v] = acc;
-      } else {
-        // Deep chains: subtract in FP64 and round once.
-        double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
-        for (int e = e0; e < e1; ++e) {
-          const int t = g.cell_src[e];
-          if (t == s) continue;
-          const float4 x = C4[static_cast<long long>(t) * nv + v];
-          ax -= x.x;
-          ay -= x.y;
-          az -= x.z;
-          aw -= x.w;
-        }
-        C4[static_cast<long long>(s) * nv + v] =
-            make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
-                        static_cast<float>(aw));
-      }
+      if (comp)
+        peel_item<true>(p, P4, C4, nv, o0 + j, v);
+      else
+        peel_item<false>(p, P4, C4, nv, o0 + j, v);
     }
     __syncthreads();
   }
@@ -87,10 +110,10 @@ cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, flo
   if (nv <= 0) return cudaSuccess;
   int target = ctas > 0 ? ctas : 4 * num_sms();
   long long chunk = (nv + target - 1) / target;
-  chunk = std::max<long long>(32, (chunk + 31) / 32 * 32);
+  chunk = std::max<long long>(8, (chunk + 7) / 8 * 8);
   const long long grid = (nv + chunk - 1) / chunk;
   peel_kernel<<<static_cast<unsigned>(grid), kPeelThreads, 0, st>>>(
-      g, p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);
+      p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);
   return cudaGetLastError();
 }
 

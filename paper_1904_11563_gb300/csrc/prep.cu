@@ -15,10 +15,10 @@
 namespace bpx {
 namespace {
 
-constexpr int kEncThreads = 256;
+constexpr int kEncThreads = 128;  // 1024 columns per CTA: one K-chunk of A stays L2-resident
 constexpr int kEncVec = 8;  // consecutive K elements per thread (two float4 loads per source)
 
-// One CTA per (coded row, 2048-column chunk); blockIdx.x walks the coded rows
+// One CTA per (coded row, 1024-column chunk); blockIdx.x walks the coded rows
 // fastest so that CTAs resident together read the same K-chunk of A (L2 reuse
 // of a source block across the cells that contain it).
 template <int kMode>  // 0: FP32 out, 1: bf16 hi only, 2: bf16 hi + lo

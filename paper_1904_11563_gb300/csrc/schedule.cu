@@ -5,8 +5,11 @@
 // recovered sources are then listed in (depth, source) order.
 //
 // Each round only touches the cells whose unknown count just dropped to one
-// (a warp-parallel ready queue), so the cost is linear in the graph edges
-// plus one short barrier sequence per round.
+// (a warp-parallel ready queue: one warp per ready cell, one warp per newly
+// recovered source), so the cost is linear in the graph edges plus one short
+// barrier sequence per round.  The plan also carries a flat "peel list" (per
+// recovered source: its resolver and the blocks to subtract) for the numeric
+// peel.
 #include <climits>
 #include <mutex>
 
@@ -16,6 +19,7 @@ namespace bpx {
 namespace {
 
 constexpr int kThreads = 1024;
+constexpr size_t kSmemStateMax = 200 * 1024;  // bytes of per-cell + per-source state kept on chip
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -44,20 +48,28 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
   return before + x - v;
 }
 
+// kSmem: the per-cell unknown counts and per-source depths (the state every
+// round reads and updates) live in shared memory when they fit, else in the
+// plan's global arrays.
+template <bool kSmem>
 __global__ void __launch_bounds__(kThreads, 1)
 schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
                 uint8_t* recovered, int32_t* info_out) {
+  extern __shared__ int32_t dyn_smem[];
   __shared__ int s_warp[32];
   __shared__ int s_nf, s_nnew, s_nnext;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  int32_t* cnt = kSmem ? dyn_smem : p.cnt;
+  int32_t* depth = kSmem ? dyn_smem + g.num_cells : p.depth;
 
   for (int c = tid; c < g.num_cells; c += nt) {
     const bool alive = mask[g.col_of_cell[c]] == 0;
-    p.cnt[c] = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
+    cnt[c] = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
     p.direct[c] = -1;
   }
   for (int s = tid; s < g.S; s += nt) {
-    p.depth[s] = 0;
+    depth[s] = 0;
     p.resolver[s] = INT_MAX;
   }
   if (tid == 0) {
@@ -70,12 +82,12 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
   int nsurv = 0;
   for (int base = 0; base < g.num_cells; base += nt) {
     const int c = base + tid;
-    const int f = (c < g.num_cells && p.cnt[c] >= 0) ? 1 : 0;
+    const int f = (c < g.num_cells && cnt[c] >= 0) ? 1 : 0;
     int total;
     const int ex = block_exclusive_scan(f, s_warp, &total);
     if (f) {
       p.surv[nsurv + ex] = c;
-      if (p.cnt[c] == 1) p.front0[atomicAdd(&s_nf, 1)] = c;
+      if (cnt[c] == 1) p.front0[atomicAdd(&s_nf, 1)] = c;
     }
     nsurv += total;
   }
@@ -88,21 +100,27 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
     const int nf = s_nf;
     if (nf == 0) break;
     ++round;
-    // A: every ready cell names its one unknown source; lowest cell id wins.
-    for (int i = tid; i < nf; i += nt) {
+    // A: one warp per ready cell: the lanes scan its support together and
+    // the single unknown source is named; the lowest cell id wins it.
+    for (int i = warp; i < nf; i += nwarps) {
       const int c = fr[i];
       int found = -1;
-      if (p.cnt[c] == 1) {
-        for (int e = g.cell_ptr[c]; e < g.cell_ptr[c + 1]; ++e) {
-          const int t = g.cell_src[e];
-          if (p.depth[t] == 0) {
-            found = t;
+      if (cnt[c] == 1) {
+        const int e0 = g.cell_ptr[c], e1 = g.cell_ptr[c + 1];
+        for (int base = e0; base < e1; base += 32) {
+          const int e = base + lane;
+          const int t = e < e1 ? g.cell_src[e] : -1;
+          const unsigned m = __ballot_sync(0xffffffffu, t >= 0 && depth[t] == 0);
+          if (m) {
+            found = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
             break;
           }
         }
-        if (found >= 0) atomicMin(&p.resolver[found], c);
       }
-      p.cand[i] = found;
+      if (lane == 0) {
+        if (found >= 0) atomicMin(&p.resolver[found], c);
+        p.cand[i] = found;
+      }
     }
     if (tid == 0) {
       s_nnew = 0;
@@ -112,7 +130,7 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
     // B: mark the named sources recovered in this round (once each).
     for (int i = tid; i < nf; i += nt) {
       const int s = p.cand[i];
-      if (s >= 0 && atomicCAS(&p.depth[s], 0, round) == 0) p.newsrc[atomicAdd(&s_nnew, 1)] = s;
+      if (s >= 0 && atomicCAS(&depth[s], 0, round) == 0) p.newsrc[atomicAdd(&s_nnew, 1)] = s;
     }
     __syncthreads();
     const int nnew = s_nnew;
@@ -122,14 +140,15 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
     }
     nrec += nnew;
     if (tid == 0) p.wave_ptr[round] = nrec;
-    // C: drop the recovered sources from their cells; a cell whose unknown
-    // count reaches one joins the next ready queue.
-    for (int j = tid; j < nnew; j += nt) {
+    // C: one warp per recovered source drops it from its cells; a cell whose
+    // unknown count reaches one joins the next ready queue.
+    for (int j = warp; j < nnew; j += nwarps) {
       const int s = p.newsrc[j];
-      for (int e = g.src_ptr[s]; e < g.src_ptr[s + 1]; ++e) {
+      const int e1 = g.src_ptr[s + 1];
+      for (int e = g.src_ptr[s] + lane; e < e1; e += 32) {
         const int c = g.src_cell[e];
-        if (p.cnt[c] >= 0) {
-          const int old = atomicSub(&p.cnt[c], 1);
+        if (cnt[c] >= 0) {
+          const int old = atomicSub(&cnt[c], 1);
           if (old == 2) nx[atomicAdd(&s_nnext, 1)] = c;
         }
       }
@@ -147,10 +166,9 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
   for (int d = 1 + tid; d <= round; d += nt) p.cursor[d] = p.wave_ptr[d - 1];
   __syncthreads();
   if (tid < 32) {
-    const int lane = tid;
     for (int base = 0; base < g.S; base += 32) {
       const int s = base + lane;
-      const int d = s < g.S ? p.depth[s] : 0;
+      const int d = s < g.S ? depth[s] : 0;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
       const int leader = __ffs(peers) - 1;
       const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -166,9 +184,38 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
   }
   __syncthreads();
   for (int s = tid; s < g.S; s += nt) {
-    const int d = p.depth[s];
+    const int d = depth[s];
+    if (kSmem) p.depth[s] = d;
     if (d == 1) p.direct[p.resolver[s]] = s;
     if (recovered) recovered[s] = d > 0 ? 1 : 0;
+  }
+  // Peel list: for order position i, the resolver and the other sources of
+  // its support (ascending), so the numeric peel reads flat descriptors.
+  int lbase = 0;
+  for (int base = 0; base < nrec; base += nt) {
+    const int i = base + tid;
+    int len = 0, r = 0;
+    if (i < nrec) {
+      r = p.resolver[p.order[i]];
+      len = g.cell_ptr[r + 1] - g.cell_ptr[r] - 1;
+    }
+    int total;
+    const int ex = block_exclusive_scan(len, s_warp, &total);
+    if (i < nrec) {
+      p.pl_res[i] = r;
+      p.pl_ptr[i] = lbase + ex;
+    }
+    lbase += total;
+  }
+  if (tid == 0) p.pl_ptr[nrec] = lbase;
+  __syncthreads();
+  for (int i = warp; i < nrec; i += nwarps) {
+    const int s = p.order[i], r = p.pl_res[i], o = p.pl_ptr[i];
+    const int e0 = g.cell_ptr[r], e1 = g.cell_ptr[r + 1];
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const int t = g.cell_src[e];
+      if (t != s) p.pl_list[o + (e - e0) - (t > s ? 1 : 0)] = t;
+    }
   }
   if (peel_order) {
     for (int i = tid; i < g.S; i += nt) {
@@ -176,7 +223,7 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
         const int s = p.order[i];
         peel_order[3 * i + 0] = s;
         peel_order[3 * i + 1] = p.resolver[s];
-        peel_order[3 * i + 2] = p.depth[s];
+        peel_order[3 * i + 2] = depth[s];
       } else {
         peel_order[3 * i + 0] = -1;
         peel_order[3 * i + 1] = -1;
@@ -208,7 +255,15 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
                             cudaStream_t st) {
-  schedule_kernel<<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out);
+  const size_t smem = (static_cast<size_t>(g.num_cells) + g.S) * sizeof(int32_t);
+  if (smem <= kSmemStateMax) {
+    cudaError_t e = cudaFuncSetAttribute(schedule_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemStateMax));
+    if (e != cudaSuccess) return e;
+    schedule_kernel<true><<<1, kThreads, smem, st>>>(g, p, mask, peel_order, recovered, info_out);
+  } else {
+    schedule_kernel<false><<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out);
+  }
   return cudaGetLastError();
 }
 
