@@ -116,7 +116,7 @@ typedef struct {
   int compensate_depth; /* sources deeper than this are peeled in FP64 before one rounding;
                            < 0 (default -1): never */
   int peel_ctas;        /* 0 = auto (a multiple of the SM count) */
-  int gemm_config;      /* 0 = auto; otherwise a tile configuration id of the tensor-core GEMM */
+  int gemm_config;      /* 0 = defaults; otherwise band * 1000 + seg_kb * 10 + tile (bpx_autotune) */
   void* const* stage_events; /* NULL, or cudaEvent_t[2 * BPX_NUM_STAGES] created by the caller:
                                 events 2i / 2i+1 are recorded on the stream right before / after
                                 stage i (enum bpx_stage).  Used to time kernels in place. */
@@ -225,6 +225,68 @@ int bpx_coded_matmul_host(const bpx_code* code, const float* h_A, const float* h
                           int K, int h, int precision, const uint8_t* h_erasure_mask, float* h_C,
                           float* d_A, float* d_B, uint8_t* d_mask, float* d_C, const bpx_opts* opts,
                           void* d_ws, size_t ws_bytes, int32_t* h_info, bpx_stream stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent coded multiplications run together.  Each job is a whole
+ * instance of the problem above (its own code, shapes, erasure mask and
+ * buffers); the paper's scheme applies per job.  All device pointers are the
+ * caller's and must stay valid while the group is used. */
+typedef struct bpx_group bpx_group; /* opaque, host-side */
+
+typedef struct {
+  const bpx_code* code;        /* host handle; must outlive the group */
+  const float* A;              /* device, M x K */
+  const float* B;              /* device, K x N */
+  float* C;                    /* device, S h x N (depth-1 blocks are written by the GEMM) */
+  const uint8_t* erasure_mask; /* device, n bytes; read at every run */
+  int32_t* info;               /* device int32[BPX_INFO_LEN] per job, or NULL */
+  int M, N, K, h;
+} bpx_job;
+
+/* Plans a batch (host only): each job's workspace region, the per-stage grids
+ * and the device job tables.  precision: BPX_BF16 or BPX_BF16X3. */
+int bpx_group_create(const bpx_job* jobs, int njobs, int precision, bpx_group** out);
+
+/* Device bytes the group needs (all jobs' workspaces + job tables). */
+size_t bpx_group_workspace_bytes(const bpx_group* group);
+
+/* Binds the workspace: uploads every job's code graph and the job tables,
+ * encodes the TMA descriptors; synchronizes `stream`. */
+int bpx_group_init(bpx_group* group, void* d_ws, size_t ws_bytes, bpx_stream stream);
+
+/* Runs every job: one launch per stage over all jobs (a1 schedule, B split,
+ * a2 encode + split, one persistent grouped tcgen05 GEMM over all jobs' tiles,
+ * a4 peel).  No host synchronization or allocation inside: the call can be
+ * captured in a CUDA graph.  Each job's outcome lands in its info words.
+ * opts->gemm_config must keep the planned tile width (0 = the planned one). */
+int bpx_grouped_run(bpx_group* group, const bpx_opts* opts, bpx_stream stream);
+
+/* Captures bpx_grouped_run into a CUDA graph owned by the group on the first
+ * call (or when the options change) and replays it; `stream` must not be the
+ * legacy default stream. */
+int bpx_group_graph_launch(bpx_group* group, const bpx_opts* opts, bpx_stream stream);
+
+/* Selects the grouped GEMM's tile configuration (see bpx_autotune) and
+ * re-plans the GEMM table if the tile width changes (synchronizes). */
+int bpx_group_set_config(bpx_group* group, int gemm_config, bpx_stream stream);
+
+/* Tile autotuner for the grouped GEMM: times each candidate configuration
+ * (NULL / 0 = a built-in list) on the group's own jobs and keeps the fastest.
+ * Synchronizes; not capturable. */
+int bpx_group_autotune(bpx_group* group, const int* configs, int nconfigs, bpx_stream stream,
+                       int* best_config, float* best_ms);
+
+/* Tile autotuner for one coded multiplication on the tensor cores: runs the
+ * whole path once, then times the GEMM under each candidate configuration.
+ * gemm_config = band * 1000 + seg_kb * 10 + tile, tile 1 = 128x256 and
+ * 2 = 128x128 output tiles, seg_kb = k-blocks of 64 per TMEM accumulation
+ * segment, band = m-tiles per rasterisation band.  Synchronizes. */
+int bpx_autotune(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
+                 int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
+                 const int* configs, int nconfigs, bpx_stream stream, int* best_config, float* best_ms);
+
+void bpx_group_free(bpx_group* group);
 
 /* a1 without any device allocation by the caller or the library (the paper has
  * no counterpart: this is a deployment convenience).  Same computation and

@@ -55,6 +55,12 @@ NUM_STAGES = 5
 STAGE_NAMES = ["schedule", "b_prep", "a_prep", "gemm", "peel"]
 
 
+class Job(ct.Structure):
+    _fields_ = [("code", ct.c_void_p), ("A", ct.c_void_p), ("B", ct.c_void_p), ("C", ct.c_void_p),
+                ("erasure_mask", ct.c_void_p), ("info", ct.c_void_p),
+                ("M", ct.c_int), ("N", ct.c_int), ("K", ct.c_int), ("h", ct.c_int)]
+
+
 _lib = None
 
 
@@ -85,6 +91,17 @@ def lib():
         "bpx_coded_matmul_host": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
                                       f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_schedule_noalloc": (i, [vp, vp, vp, vp, vp, vp]),
+        "bpx_group_create": (i, [ct.POINTER(Job), i, i, ct.POINTER(vp)]),
+        "bpx_group_workspace_bytes": (sz, [vp]),
+        "bpx_group_init": (i, [vp, vp, sz, vp]),
+        "bpx_grouped_run": (i, [vp, ct.POINTER(Opts), vp]),
+        "bpx_group_graph_launch": (i, [vp, ct.POINTER(Opts), vp]),
+        "bpx_group_set_config": (i, [vp, i, vp]),
+        "bpx_group_autotune": (i, [vp, ct.POINTER(ct.c_int), i, vp, ct.POINTER(ct.c_int),
+                                   ct.POINTER(ct.c_float)]),
+        "bpx_autotune": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, vp, sz, ct.POINTER(ct.c_int), i, vp,
+                             ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
+        "bpx_group_free": (None, [vp]),
         "bpx_default_opts": (Opts, []),
         "bpx_build_info": (ct.c_char_p, []),
     }
@@ -284,3 +301,65 @@ def coded_matmul_host(code: Code, hA, hB, h, precision, hmask, hC, dA, dB, dmask
     if rc not in (OK, ERR_UNDECODABLE):
         raise BpxError(rc, lib().bpx_last_error().decode())
     return rc, info
+
+
+def autotune(code: Code, A, B, h, precision, mask, ws: Workspace, C=None, configs=None):
+    """Tile autotuner of the tensor-core GEMM for one job; returns (config, ms)."""
+    M, K = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = alloc_C(code, h, N, A.device)
+    best, ms = ct.c_int(), ct.c_float()
+    arr = (ct.c_int * len(configs))(*configs) if configs else None
+    _check(lib().bpx_autotune(code.handle, _ptr(A), _ptr(B), M, N, K, h, precision, _ptr(mask), _ptr(C),
+                              ws.ptr, ws.nbytes, arr, len(configs) if configs else 0, _stream(),
+                              ct.byref(best), ct.byref(ms)))
+    return best.value, ms.value
+
+
+class Group:
+    """A batch of coded multiplications run together (bpx_group_*).
+
+    jobs: list of dicts with keys code, A, B, C, mask, h (torch tensors on
+    the device; C with S*h rows) and optionally info (int32[16] tensor)."""
+
+    def __init__(self, jobs, precision=BF16X3, device="cuda"):
+        torch = _torch()
+        self._h = None
+        self.jobs = jobs
+        arr = (Job * len(jobs))()
+        for i, j in enumerate(jobs):
+            A, B = j["A"], j["B"]
+            arr[i] = Job(j["code"].handle, A.data_ptr(), B.data_ptr(), j["C"].data_ptr(),
+                         j["mask"].data_ptr(), j["info"].data_ptr() if j.get("info") is not None else None,
+                         A.shape[0], B.shape[1], A.shape[1], j["h"])
+        self._arr = arr
+        h = ct.c_void_p()
+        _check(lib().bpx_group_create(arr, len(jobs), precision, ct.byref(h)))
+        self._h = h
+        self.nbytes = int(lib().bpx_group_workspace_bytes(h))
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ws = self.buf[off:off + self.nbytes]
+        _check(lib().bpx_group_init(h, _ptr(self.ws), self.nbytes, _stream()))
+
+    def run(self, opts=None):
+        _check(lib().bpx_grouped_run(self._h, ct.byref(opts) if opts is not None else None, _stream()))
+
+    def graph_launch(self, opts=None):
+        _check(lib().bpx_group_graph_launch(self._h, ct.byref(opts) if opts is not None else None, _stream()))
+
+    def set_config(self, config):
+        _check(lib().bpx_group_set_config(self._h, config, _stream()))
+
+    def autotune(self, configs=None):
+        best, ms = ct.c_int(), ct.c_float()
+        arr = (ct.c_int * len(configs))(*configs) if configs else None
+        _check(lib().bpx_group_autotune(self._h, arr, len(configs) if configs else 0, _stream(),
+                                        ct.byref(best), ct.byref(ms)))
+        return best.value, ms.value
+
+    def __del__(self):
+        if self._h is not None and _lib is not None:
+            _lib.bpx_group_free(self._h)
+            self._h = None

@@ -83,7 +83,69 @@ inline DevPlan make_plan(const void* ws, const WsLayout& L) {
   return p;
 }
 
+// One job of a grouped launch (bpx_grouped_run): a whole coded
+// multiplication with its own code, shapes, mask, workspace region and
+// buffers.  *_base fields give the first CTA of the job in each multi-job
+// kernel's grid (CTAs are looked up by binary search over these).
+struct GJob {
+  DevGraph g;
+  DevPlan p;
+  const float* A;
+  const float* B;
+  float* C;
+  float* products;
+  const uint8_t* mask;
+  int32_t* info_out;
+  void* a_hi;
+  void* a_lo;
+  void* b_hi;
+  void* b_lo;
+  int M, N, K, h;
+  long long bsplit_base, enc_base, peel_base;
+  int peel_chunk;
+};
+
+// Index of the last job whose base (selected by `field`) is <= x.
+template <typename F>
+__device__ __forceinline__ int find_job(const GJob* jobs, int njobs, long long x, F field) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (field(jobs[mid]) <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Grid sizes of the multi-job kernels for one job.
+inline long long bsplit_ctas(int N, int K) { return static_cast<long long>((N + 63) / 64) * ((K + 63) / 64); }
+inline long long encode_ctas(long long rows, int K) { return rows * ((K / 8 + 127) / 128); }
+int peel_chunk_for(long long nv, int ctas_hint);
+
 // Launchers (defined in the .cu files).  All return cudaError_t of the launch.
+cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, cudaStream_t st);
+cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st);
+cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st);
+cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
+                              int compensate_depth, cudaStream_t st);
+cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
+                                   int config, cudaStream_t st);
+size_t tc_job_bytes();
+
+// Inputs of one job's entry in the grouped tensor-core GEMM table.
+struct TcSpec {
+  DevPlan p;
+  const void* a_hi;
+  const void* a_lo;
+  const void* b_hi;
+  const void* b_lo;
+  int num_cells, N, K, h;
+  float* products;
+  float* C_direct;
+  int32_t* info_out;
+};
+cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
+                           long long* total_tiles, cudaStream_t st);
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
                             cudaStream_t st);

@@ -30,6 +30,9 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "device_common.cuh"
 
@@ -37,10 +40,8 @@ namespace bpx {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 256;
 constexpr int BK = 64;  // bf16 elements = 128 bytes per row: one 128B swizzle atom row
 constexpr int kThreads = 320;  // producer, MMA, 8 epilogue warps
-constexpr int kTmemCols = 512;  // two 256-column FP32 segment accumulators
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -99,17 +100,29 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            (static_cast<uint32_t>(BN >> 3) << 17) |
-                            (static_cast<uint32_t>(BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// M = 128, N = kBN.
+template <int kBN>
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kBN >> 3) << 17) |
+         (static_cast<uint32_t>(BM >> 4) << 24);
+}
 
+template <int kBN>
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc_bf16<kBN>()), "r"(acc));
+}
+
+// A tensor map held in global memory (the job table of a grouped launch) is
+// made visible to the TMA unit's proxy before first use.
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -142,46 +155,85 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-struct TcParams {
-  DevGraph g;
-  DevPlan p;
+// One coded GEMM: its tensor maps and where its plan and outputs live.
+// A grouped launch keeps an array of these in global memory; a single launch
+// passes one as a __grid_constant__ parameter.
+struct __align__(64) TcJob {
+  CUtensorMap map_ahi, map_alo, map_bhi, map_blo;
+  const int32_t* ctr;     // plan counters (surviving-cell count)
+  const int32_t* surv;    // surviving cells, ascending
+  const int32_t* direct;  // per cell: the source it resolves at depth 1, or -1
+  int32_t* info;          // plan info words (device error reporting)
+  int32_t* info_out;      // caller's info words, or null
   float* products;
   float* C_direct;
-  int32_t* info_out;
   int N, K, h;
-  int group;   // m-tiles per rasterisation band
-  int seg_kb;  // k-blocks per TMEM accumulation segment
+  int m_tiles_max, n_tiles;
+  long long tile_base;    // first tile of this job in the launch's tile space
 };
 
-template <bool kSplit>
+template <bool kSplit, int kBN>
 struct Stage {
-  static constexpr uint32_t kA = BM * BK * 2;  // 16 KB
-  static constexpr uint32_t kB = BN * BK * 2;  // 32 KB
+  static constexpr uint32_t kA = BM * BK * 2;   // 16 KB
+  static constexpr uint32_t kB = kBN * BK * 2;  // 32 or 16 KB
   static constexpr uint32_t kBytes = kSplit ? 2 * (kA + kB) : (kA + kB);
-  // offsets inside a stage
   static constexpr uint32_t kAhi = 0;
   static constexpr uint32_t kAlo = kA;
   static constexpr uint32_t kBhi = kSplit ? 2 * kA : kA;
   static constexpr uint32_t kBlo = kBhi + kB;
 };
 
-__device__ __forceinline__ void raise_error(const TcParams& P, int code, volatile int* abort_flag) {
+__device__ __forceinline__ void raise_error(const TcJob& J, int code, volatile int* abort_flag) {
   *abort_flag = 1;
-  atomicExch(&P.p.ctr[CTR_ERR], code);
-  atomicExch(&P.p.info[BPX_INFO_DEVICE_ERR], code);
-  atomicExch(&P.p.info[BPX_INFO_STATUS], code);
-  if (P.info_out) {
-    atomicExch(&P.info_out[BPX_INFO_DEVICE_ERR], code);
-    atomicExch(&P.info_out[BPX_INFO_STATUS], code);
+  atomicExch(&J.info[BPX_INFO_DEVICE_ERR], code);
+  atomicExch(&J.info[BPX_INFO_STATUS], code);
+  if (J.info_out) {
+    atomicExch(&J.info_out[BPX_INFO_DEVICE_ERR], code);
+    atomicExch(&J.info_out[BPX_INFO_STATUS], code);
   }
 }
 
-template <bool kSplit, int kStages>
+// Where a tile of the launch's tile space lands: its job, its (m, n) tile of
+// that job (bands of `group` m-tiles, n-major inside a band so that CTAs
+// resident together share a few A row tiles and B column tiles in L2), and
+// whether it covers surviving rows at all (tiles past the job's surviving
+// rows are skipped by every role alike).
+struct TileRef {
+  const TcJob* J;
+  int m, n, Mc, k_blocks;
+  bool live;
+};
+
+__device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {  // last job with tile_base <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_base <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  TileRef R;
+  R.J = &jobs[lo];
+  const TcJob& J = *R.J;
+  const int lt = static_cast<int>(t - J.tile_base);
+  const int band_tiles = group * J.n_tiles;
+  const int band = lt / band_tiles;
+  const int r = lt - band * band_tiles;
+  const int rows_in_band = min(group, J.m_tiles_max - band * group);
+  R.m = band * group + r % rows_in_band;
+  R.n = r / rows_in_band;
+  R.Mc = J.ctr[CTR_NSURV] * J.h;
+  R.k_blocks = (J.K + BK - 1) / BK;
+  R.live = R.m * BM < R.Mc;
+  return R;
+}
+
+template <bool kSplit, int kStages, int kBN>
 __global__ void __launch_bounds__(kThreads, 1)
-gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
-               const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
-               TcParams P) {
-  using St = Stage<kSplit>;
+gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ table, int njobs,
+               long long total_tiles, int group, int seg_kb) {
+  using St = Stage<kSplit, kBN>;
+  constexpr int kTmemCols = 2 * kBN;  // two FP32 segment accumulators
+  constexpr int kCols = kBN / 2;      // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
@@ -189,15 +241,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
+  const TcJob* jobs = table ? table : &single;
+  const bool grouped = table != nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nsurv = P.p.ctr[CTR_NSURV];
-  const int Mc = nsurv * P.h;
-  const int m_tiles = (Mc + BM - 1) / BM;
-  const int n_tiles = (P.N + BN - 1) / BN;
-  const int num_tiles = m_tiles * n_tiles;
-  const int k_blocks = (P.K + BK - 1) / BK;
-  const int seg_kb = P.seg_kb;
-  const int n_segs = (k_blocks + seg_kb - 1) / seg_kb;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -224,39 +270,38 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
   fence_after();
   const uint32_t tmem_base = tmem_base_sh;
 
-  // tile -> (m, n): bands of `group` m-tiles; inside a band n-major so that
-  // CTAs resident together share a few A row tiles and B column tiles in L2.
-  auto tile_mn = [&](int t, int& m, int& n) {
-    const int band_tiles = P.group * n_tiles;
-    const int band = t / band_tiles;
-    const int r = t - band * band_tiles;
-    const int rows_in_band = min(P.group, m_tiles - band * P.group);
-    m = band * P.group + r % rows_in_band;
-    n = r / rows_in_band;
-  };
-
   if (warp == 0) {
     if (lane == 0) {
       int kb_all = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-        int mt, nt;
-        tile_mn(t, mt, nt);
-        for (int kb = 0; kb < k_blocks; ++kb, ++kb_all) {
+      const TcJob* fenced = nullptr;
+      for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        const TileRef T = locate(jobs, njobs, t, group);
+        if (!T.live) continue;
+        if (grouped && T.J != fenced) {
+          tensormap_acquire(&T.J->map_ahi);
+          tensormap_acquire(&T.J->map_bhi);
+          if (kSplit) {
+            tensormap_acquire(&T.J->map_alo);
+            tensormap_acquire(&T.J->map_blo);
+          }
+          fenced = T.J;
+        }
+        for (int kb = 0; kb < T.k_blocks; ++kb, ++kb_all) {
           const int s = kb_all % kStages;
           const uint32_t ph = static_cast<uint32_t>((kb_all / kStages) & 1) ^ 1u;
           if (!mbar_wait(smem_u32(&empty_bar[s]), ph, &abort_flag)) {
-            if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+            if (!abort_flag) raise_error(*T.J, BPX_ERR_TIMEOUT, &abort_flag);
             ok = false;
             break;
           }
           const uint32_t base = smem_u32(smem + s * St::kBytes);
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, St::kBytes);
-          tma_load_2d(base + St::kAhi, &map_ahi, fb, kb * BK, mt * BM);
-          if (kSplit) tma_load_2d(base + St::kAlo, &map_alo, fb, kb * BK, mt * BM);
-          tma_load_2d(base + St::kBhi, &map_bhi, fb, kb * BK, nt * BN);
-          if (kSplit) tma_load_2d(base + St::kBlo, &map_blo, fb, kb * BK, nt * BN);
+          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, kb * BK, T.m * BM);
+          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, kb * BK, T.m * BM);
+          tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, kb * BK, T.n * kBN);
+          if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * BK, T.n * kBN);
         }
       }
     }
@@ -264,23 +309,26 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
     if (lane == 0) {
       int kb_all = 0, g = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+      for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+        const TileRef T = locate(jobs, njobs, t, group);
+        if (!T.live) continue;
+        const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
           const int buf = g & 1;
           if (!mbar_wait(smem_u32(&sempty_bar[buf]), static_cast<uint32_t>((g >> 1) & 1) ^ 1u,
                          &abort_flag)) {
-            if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+            if (!abort_flag) raise_error(*T.J, BPX_ERR_TIMEOUT, &abort_flag);
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(buf * BN);
-          const int kb0 = sg * seg_kb, kb1 = min(k_blocks, kb0 + seg_kb);
+          const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(buf * kBN);
+          const int kb0 = sg * seg_kb, kb1 = min(T.k_blocks, kb0 + seg_kb);
           for (int kb = kb0; kb < kb1; ++kb, ++kb_all) {
             const int s = kb_all % kStages;
             if (!mbar_wait(smem_u32(&full_bar[s]), static_cast<uint32_t>((kb_all / kStages) & 1),
                            &abort_flag)) {
-              if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+              if (!abort_flag) raise_error(*T.J, BPX_ERR_TIMEOUT, &abort_flag);
               ok = false;
               break;
             }
@@ -294,10 +342,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
             for (int kk = 0; kk < BK / 16; ++kk) {
               const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
-              umma_bf16(d_tmem, ahi + adv, bhi + adv, first);
+              umma_bf16<kBN>(d_tmem, ahi + adv, bhi + adv, first);
               if (kSplit) {
-                umma_bf16(d_tmem, ahi + adv, blo + adv, 1u);
-                umma_bf16(d_tmem, alo + adv, bhi + adv, 1u);
+                umma_bf16<kBN>(d_tmem, ahi + adv, blo + adv, 1u);
+                umma_bf16<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
               }
             }
             umma_commit(smem_u32(&empty_bar[s]));
@@ -315,22 +363,25 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
     const int row = quarter * 32 + lane;
     int g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-      float accum[128];
+    for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+      const TileRef T = locate(jobs, njobs, t, group);
+      if (!T.live) continue;
+      const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
+      float accum[kCols];
 #pragma unroll
-      for (int i = 0; i < 128; ++i) accum[i] = 0.f;
+      for (int i = 0; i < kCols; ++i) accum[i] = 0.f;
       for (int sg = 0; sg < n_segs; ++sg, ++g) {
         const int buf = g & 1;
         if (!mbar_wait(smem_u32(&sfull_bar[buf]), static_cast<uint32_t>((g >> 1) & 1), &abort_flag)) {
-          if (!abort_flag) raise_error(P, BPX_ERR_TIMEOUT, &abort_flag);
+          if (!abort_flag) raise_error(*T.J, BPX_ERR_TIMEOUT, &abort_flag);
           ok = false;
           break;
         }
         fence_after();
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                               static_cast<uint32_t>(buf * BN + half * 128);
+                               static_cast<uint32_t>(buf * kBN + half * kCols);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < kCols / 32; ++c) {
           float v[32];
           tmem_ld32(taddr + c * 32, v);
 #pragma unroll
@@ -341,21 +392,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constan
         if (lane == 0) mbar_arrive(smem_u32(&sempty_bar[buf]));
       }
       if (!ok) break;
-      int mt, nt;
-      tile_mn(t, mt, nt);
-      const int r = mt * BM + row;
-      if (r < Mc) {
-        const int ci = r / P.h;
-        const int j = r - ci * P.h;
-        const int cell = P.p.surv[ci];
-        const int ds = P.C_direct ? P.p.direct[cell] : -1;
-        float* dst = ds >= 0 ? P.C_direct + (static_cast<long long>(ds) * P.h + j) * P.N
-                             : P.products + (static_cast<long long>(cell) * P.h + j) * P.N;
-        const int n0 = nt * BN + half * 128;
+      const TcJob& J = *T.J;
+      const int r = T.m * BM + row;
+      if (r < T.Mc) {
+        const int ci = r / J.h;
+        const int j = r - ci * J.h;
+        const int cell = J.surv[ci];
+        const int ds = J.C_direct ? J.direct[cell] : -1;
+        float* dst = ds >= 0 ? J.C_direct + (static_cast<long long>(ds) * J.h + j) * J.N
+                             : J.products + (static_cast<long long>(cell) * J.h + j) * J.N;
+        const int n0 = T.n * kBN + half * kCols;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < kCols / 4; ++q) {
           const int n = n0 + 4 * q;
-          if (n < P.N)
+          if (n < J.N)
             *reinterpret_cast<float4*>(dst + n) =
                 make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
         }
@@ -400,58 +450,131 @@ bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box
   return r == CUDA_SUCCESS;
 }
 
-template <bool kSplit, int kStages>
-cudaError_t launch_impl(const TcParams& P, const void* a_hi, const void* a_lo, const void* b_hi,
-                        const void* b_lo, int num_cells, cudaStream_t st) {
-  CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
-  const long long rows = static_cast<long long>(num_cells) * P.h;
-  if (!make_map(&m_ahi, a_hi, rows, P.K, BM) || !make_map(&m_bhi, b_hi, P.N, P.K, BN))
-    return cudaErrorInvalidValue;
-  if (kSplit) {
-    if (!make_map(&m_alo, a_lo, rows, P.K, BM) || !make_map(&m_blo, b_lo, P.N, P.K, BN))
-      return cudaErrorInvalidValue;
-  } else {
-    m_alo = m_ahi;
-    m_blo = m_bhi;
-  }
-  const size_t smem = static_cast<size_t>(kStages) * Stage<kSplit>::kBytes + 1024;
-  auto kern = gemm_tc_kernel<kSplit, kStages>;
+// Tile configurations the autotuner chooses among (gemm_config % 10).
+int tile_bn(int config) { return (config % 10) == 2 ? 128 : 256; }
+
+template <bool kSplit, int kStages, int kBN>
+cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, long long total_tiles,
+                           int group, int seg_kb, cudaStream_t st) {
+  const size_t smem = static_cast<size_t>(kStages) * Stage<kSplit, kBN>::kBytes + 1024;
+  auto kern = gemm_tc_kernel<kSplit, kStages, kBN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  const long long m_tiles_max = (rows + BM - 1) / BM;
-  const long long tiles_max = m_tiles_max * ((P.N + BN - 1) / BN);
-  const int grid = static_cast<int>(std::min<long long>(tiles_max, num_sms()));
+  const int grid = static_cast<int>(std::min<long long>(total_tiles, num_sms()));
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, kThreads, smem, st>>>(m_ahi, m_alo, m_bhi, m_blo, P);
+  kern<<<grid, kThreads, smem, st>>>(single, table, njobs, total_tiles, group, seg_kb);
   return cudaGetLastError();
 }
 
+cudaError_t dispatch(bool split3, int bn, const TcJob& single, const TcJob* table, int njobs,
+                     long long total_tiles, int group, int seg_kb, cudaStream_t st) {
+  if (split3) {
+    if (bn == 128) return launch_variant<true, 3, 128>(single, table, njobs, total_tiles, group, seg_kb, st);
+    return launch_variant<true, 2, 256>(single, table, njobs, total_tiles, group, seg_kb, st);
+  }
+  if (bn == 128) return launch_variant<false, 6, 128>(single, table, njobs, total_tiles, group, seg_kb, st);
+  return launch_variant<false, 4, 256>(single, table, njobs, total_tiles, group, seg_kb, st);
+}
+
+// gemm_config: 0 = defaults (BN 256, band 16, segment 4 k-blocks), else
+// band * 1000 + seg_kb * 10 + tile (tile 1 = 128x256, 2 = 128x128).
+void decode_config(int config, int* group, int* seg_kb, int* bn) {
+  *group = 16;
+  *seg_kb = 4;
+  *bn = 256;
+  if (config > 0) {
+    *bn = tile_bn(config);
+    if ((config / 10) % 100 > 0) *seg_kb = (config / 10) % 100;
+    if (config / 1000 > 0) *group = config / 1000;
+  }
+}
+
 }  // namespace
+
+namespace {
+
+bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
+                 const void* b_lo, int num_cells, int N, int K, int h, int bn, float* products,
+                 float* C_direct, int32_t* info_out) {
+  memset(J, 0, sizeof *J);
+  const long long rows = static_cast<long long>(num_cells) * h;
+  if (!make_map(&J->map_ahi, a_hi, rows, K, BM) || !make_map(&J->map_bhi, b_hi, N, K, bn)) return false;
+  if (a_lo) {
+    if (!make_map(&J->map_alo, a_lo, rows, K, BM) || !make_map(&J->map_blo, b_lo, N, K, bn)) return false;
+  } else {
+    J->map_alo = J->map_ahi;
+    J->map_blo = J->map_bhi;
+  }
+  J->ctr = p.ctr;
+  J->surv = p.surv;
+  J->direct = p.direct;
+  J->info = p.info;
+  J->info_out = info_out;
+  J->products = products;
+  J->C_direct = C_direct;
+  J->N = N;
+  J->K = K;
+  J->h = h;
+  J->m_tiles_max = static_cast<int>((rows + BM - 1) / BM);
+  J->n_tiles = (N + bn - 1) / bn;
+  J->tile_base = 0;
+  return true;
+}
+
+}  // namespace
+
+// Builds the device job table of a grouped GEMM for the given tile config:
+// jobs ordered by decreasing K (longest tiles first, so the static striding
+// of persistent CTAs over the tile space balances), tile_base prefix sums.
+// Copies the table to d_table (n * tc_job_bytes() bytes) and synchronises.
+cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
+                           long long* total_tiles, cudaStream_t st) {
+  int group, seg_kb, bn;
+  decode_config(config, &group, &seg_kb, &bn);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return specs[a].K > specs[b].K; });
+  std::vector<TcJob> tab(n);
+  long long base = 0;
+  for (int r = 0; r < n; ++r) {
+    const TcSpec& S = specs[idx[r]];
+    if (!tc_fill_job(&tab[r], S.p, S.a_hi, split3 ? S.a_lo : nullptr, S.b_hi, split3 ? S.b_lo : nullptr,
+                     S.num_cells, S.N, S.K, S.h, bn, S.products, S.C_direct, S.info_out))
+      return cudaErrorInvalidValue;
+    tab[r].tile_base = base;
+    base += static_cast<long long>(tab[r].m_tiles_max) * tab[r].n_tiles;
+  }
+  *total_tiles = base;
+  cudaError_t e = cudaMemcpyAsync(d_table, tab.data(), sizeof(TcJob) * n, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+size_t tc_job_bytes() { return sizeof(TcJob); }
 
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
                            const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
                            bool split3, float* products, float* C_direct, int config,
                            int32_t* info_out, cudaStream_t st) {
-  TcParams P;
-  P.g = g;
-  P.p = p;
-  P.products = products;
-  P.C_direct = C_direct;
-  P.info_out = info_out;
-  P.N = N;
-  P.K = K;
-  P.h = h;
-  P.group = 16;
-  P.seg_kb = 4;
-  // config: 0 = defaults; otherwise group * 100 + seg_kb (autotuner space)
-  if (config > 0) {
-    P.group = config / 100;
-    P.seg_kb = config % 100;
-  }
-  if (P.group < 1) P.group = 16;
-  if (P.seg_kb < 1) P.seg_kb = 4;
-  if (split3) return launch_impl<true, 2>(P, a_hi, a_lo, b_hi, b_lo, num_cells, st);
-  return launch_impl<false, 4>(P, a_hi, a_lo, b_hi, b_lo, num_cells, st);
+  (void)g;
+  int group, seg_kb, bn;
+  decode_config(config, &group, &seg_kb, &bn);
+  TcJob J;
+  if (!tc_fill_job(&J, p, a_hi, split3 ? a_lo : nullptr, b_hi, split3 ? b_lo : nullptr, num_cells, N, K, h,
+                   bn, products, C_direct, info_out))
+    return cudaErrorInvalidValue;
+  const long long tiles = static_cast<long long>(J.m_tiles_max) * J.n_tiles;
+  return dispatch(split3, bn, J, nullptr, 1, tiles, group, seg_kb, st);
+}
+
+// Grouped launch over a device table of jobs (tile_base set, maps encoded).
+cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
+                                   int config, cudaStream_t st) {
+  int group, seg_kb, bn;
+  decode_config(config, &group, &seg_kb, &bn);
+  TcJob dummy;
+  memset(&dummy, 0, sizeof dummy);
+  return dispatch(split3, bn, dummy, static_cast<const TcJob*>(d_jobs), njobs, total_tiles, group, seg_kb, st);
 }
 
 }  // namespace bpx

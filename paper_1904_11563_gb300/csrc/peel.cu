@@ -76,11 +76,11 @@ __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, fl
   }
 }
 
-__global__ void __launch_bounds__(kPeelThreads)
-peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk,
-            int first_wave, int compensate_depth) {
+__device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restrict__ P, float* C,
+                                          long long nv, int chunk, int first_wave,
+                                          int compensate_depth, long long cta) {
   const int nwaves = p.ctr[CTR_NWAVES];
-  const long long v0 = static_cast<long long>(blockIdx.x) * chunk;
+  const long long v0 = cta * chunk;
   if (v0 >= nv) return;
   const int clen = static_cast<int>(min(static_cast<long long>(chunk), nv - v0));
   const float4* P4 = reinterpret_cast<const float4*>(P);
@@ -102,15 +102,42 @@ peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int 
   }
 }
 
+__global__ void __launch_bounds__(kPeelThreads)
+peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk, int first_wave,
+            int compensate_depth) {
+  peel_body(p, P, C, nv, chunk, first_wave, compensate_depth, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kPeelThreads)
+peel_group_kernel(const GJob* __restrict__ jobs, int njobs, int first_wave, int compensate_depth) {
+  const long long b = blockIdx.x;
+  const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.peel_base; });
+  const GJob& J = jobs[j];
+  const long long nv = static_cast<long long>(J.h) * J.N / 4;
+  peel_body(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - J.peel_base);
+}
+
 }  // namespace
+
+int peel_chunk_for(long long nv, int ctas_hint) {
+  const int target = ctas_hint > 0 ? ctas_hint : 4 * num_sms();
+  long long chunk = (nv + target - 1) / target;
+  return static_cast<int>(std::max<long long>(8, (chunk + 7) / 8 * 8));
+}
+
+cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
+                              int compensate_depth, cudaStream_t st) {
+  if (total_ctas <= 0) return cudaSuccess;
+  peel_group_kernel<<<static_cast<unsigned>(total_ctas), kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave,
+                                                                                compensate_depth);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, float* C, int N, int h,
                         int first_wave, int compensate_depth, int ctas, cudaStream_t st) {
   const long long nv = static_cast<long long>(h) * N / 4;
   if (nv <= 0) return cudaSuccess;
-  int target = ctas > 0 ? ctas : 4 * num_sms();
-  long long chunk = (nv + target - 1) / target;
-  chunk = std::max<long long>(8, (chunk + 7) / 8 * 8);
+  const long long chunk = peel_chunk_for(nv, ctas);
   const long long grid = (nv + chunk - 1) / chunk;
   peel_kernel<<<static_cast<unsigned>(grid), kPeelThreads, 0, st>>>(
       p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);

@@ -22,16 +22,16 @@ constexpr int kEncVec = 8;  // consecutive K elements per thread (two float4 loa
 // fastest so that CTAs resident together read the same K-chunk of A (L2 reuse
 // of a source block across the cells that contain it).
 template <int kMode>  // 0: FP32 out, 1: bf16 hi only, 2: bf16 hi + lo
-__global__ void __launch_bounds__(kEncThreads)
-encode_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, int h,
-              float* out_f32, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo) {
+__device__ __forceinline__ void encode_body(const DevGraph& g, const DevPlan& p,
+                                            const float* __restrict__ A, int M, int K, int h,
+                                            float* out_f32, __nv_bfloat16* out_hi,
+                                            __nv_bfloat16* out_lo, int row, int kchunk) {
   const int nsurv = p.ctr[CTR_NSURV];
-  const int row = blockIdx.x;  // coded row in the compacted order
-  if (row >= nsurv * h) return;
+  if (row >= nsurv * h) return;  // row: coded row in the compacted order
   const int ci = row / h, j = row - ci * h;
   const int cell = p.surv[ci];
   const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
-  const int k8 = (blockIdx.y * kEncThreads + threadIdx.x) * kEncVec;
+  const int k8 = (kchunk * kEncThreads + threadIdx.x) * kEncVec;
   if (k8 >= K) return;
   const bool full = k8 + kEncVec <= K;  // K % 8 == 0, so a chunk is full or absent
   float acc[kEncVec];
@@ -68,14 +68,21 @@ encode_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, 
   }
 }
 
+template <int kMode>
+__global__ void __launch_bounds__(kEncThreads)
+encode_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, int h,
+              float* out_f32, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo) {
+  encode_body<kMode>(g, p, A, M, K, h, out_f32, out_hi, out_lo, blockIdx.x, blockIdx.y);
+}
+
 // B (K x N row-major FP32) -> Bt (N x K row-major bf16) through a 64 x 64
 // shared-memory tile: float4 reads along N, 16-byte bf16 writes along K.
 constexpr int kTile = 64;
-__global__ void __launch_bounds__(256)
-b_split_kernel(const float* __restrict__ B, int K, int N, __nv_bfloat16* bt_hi,
-               __nv_bfloat16* bt_lo) {
+__device__ __forceinline__ void b_split_body(const float* __restrict__ B, int K, int N,
+                                             __nv_bfloat16* bt_hi, __nv_bfloat16* bt_lo, int bx,
+                                             int by) {
   __shared__ float tile[kTile][kTile + 1];
-  const int n0 = blockIdx.x * kTile, k0 = blockIdx.y * kTile;
+  const int n0 = bx * kTile, k0 = by * kTile;
   {
     // 64 rows (k) x 16 float4 (n): 4 float4 per thread
     const int c4 = threadIdx.x & 15, r0 = threadIdx.x >> 4;  // 16 x 16
@@ -114,6 +121,35 @@ b_split_kernel(const float* __restrict__ B, int K, int N, __nv_bfloat16* bt_hi,
   }
 }
 
+__global__ void __launch_bounds__(256)
+b_split_kernel(const float* __restrict__ B, int K, int N, __nv_bfloat16* bt_hi, __nv_bfloat16* bt_lo) {
+  b_split_body(B, K, N, bt_hi, bt_lo, blockIdx.x, blockIdx.y);
+}
+
+// Grouped launches: a flat grid over every job's CTAs; each CTA finds its job
+// and its local (x, y) block, x fastest as in the single-job grids.
+__global__ void __launch_bounds__(256) b_split_group_kernel(const GJob* __restrict__ jobs, int njobs) {
+  const long long b = blockIdx.x;
+  const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.bsplit_base; });
+  const GJob& J = jobs[j];
+  const long long local = b - J.bsplit_base;
+  const int gx = (J.N + kTile - 1) / kTile;
+  b_split_body(J.B, J.K, J.N, static_cast<__nv_bfloat16*>(J.b_hi), static_cast<__nv_bfloat16*>(J.b_lo),
+               static_cast<int>(local % gx), static_cast<int>(local / gx));
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kEncThreads) encode_group_kernel(const GJob* __restrict__ jobs, int njobs) {
+  const long long b = blockIdx.x;
+  const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.enc_base; });
+  const GJob& J = jobs[j];
+  const long long local = b - J.enc_base;
+  const long long rows = static_cast<long long>(J.g.num_cells) * J.h;
+  encode_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, nullptr, static_cast<__nv_bfloat16*>(J.a_hi),
+                     static_cast<__nv_bfloat16*>(J.a_lo), static_cast<int>(local % rows),
+                     static_cast<int>(local / rows));
+}
+
 }  // namespace
 
 cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* A, int M, int K,
@@ -136,6 +172,18 @@ cudaError_t launch_encode_split(const DevGraph& g, const DevPlan& p, const float
     encode_kernel<2><<<grid, kEncThreads, 0, st>>>(g, p, A, M, K, h, nullptr, hi, lo);
   else
     encode_kernel<1><<<grid, kEncThreads, 0, st>>>(g, p, A, M, K, h, nullptr, hi, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st) {
+  if (total_ctas <= 0) return cudaSuccess;
+  b_split_group_kernel<<<static_cast<unsigned>(total_ctas), 256, 0, st>>>(d_jobs, njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st) {
+  if (total_ctas <= 0) return cudaSuccess;
+  encode_group_kernel<2><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, njobs);
   return cudaGetLastError();
 }
 

@@ -52,9 +52,9 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
 // round reads and updates) live in shared memory when they fit, else in the
 // plan's global arrays.
 template <bool kSmem>
-__global__ void __launch_bounds__(kThreads, 1)
-schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
-                uint8_t* recovered, int32_t* info_out) {
+__device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& p,
+                                              const uint8_t* __restrict__ mask, int32_t* peel_order,
+                                              uint8_t* recovered, int32_t* info_out) {
   extern __shared__ int32_t dyn_smem[];
   __shared__ int s_warp[32];
   __shared__ int s_nf, s_nnew, s_nnext;
@@ -250,7 +250,35 @@ schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t
   }
 }
 
+template <bool kSmem>
+__global__ void __launch_bounds__(kThreads, 1)
+schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
+                uint8_t* recovered, int32_t* info_out) {
+  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out);
+}
+
+// Grouped launch: CTA j plans job j.
+template <bool kSmem>
+__global__ void __launch_bounds__(kThreads, 1) schedule_group_kernel(const GJob* __restrict__ jobs) {
+  const GJob& J = jobs[blockIdx.x];
+  schedule_body<kSmem>(J.g, J.p, J.mask, nullptr, nullptr, J.info_out);
+}
+
 }  // namespace
+
+cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  if (max_state_bytes <= kSmemStateMax) {
+    cudaError_t e = cudaFuncSetAttribute(schedule_group_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemStateMax));
+    if (e != cudaSuccess) return e;
+    schedule_group_kernel<true><<<njobs, kThreads, max_state_bytes, st>>>(d_jobs);
+  } else {
+    schedule_group_kernel<false><<<njobs, kThreads, 0, st>>>(d_jobs);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,

@@ -106,3 +106,43 @@ def device_inputs(M: int, K: int, N: int, dist: str, seed: int, device="cuda"):
     else:
         raise ValueError(dist)
     return A, B
+
+
+def batch_specs(njobs: int, seed: int, lo: int = 256, hi: int = 4096):
+    """Job descriptions of a batch of independent coded multiplications:
+    M, N, K each 128 * round(x / 128) with x log-uniform on [lo, hi]; half
+    array codes (Table I, Table III, systematic Mojette n in 6..32 with e in
+    {2, 3}), half projection codes (Construction A, n in 6..32, e =
+    floor(n / 4)); grid height b = max(1, M // (16 k)); h = ceil(M / S);
+    each job's erasure mask drawn from its own seed.  Returns dicts with
+    code=(kind, *params), M, N, K, h, e, n, mask_seed."""
+    out = []
+    for i in range(njobs):
+        g = rng(seed * 100003 + i)
+
+        def dim():
+            x = float(np.exp(g.uniform(np.log(lo), np.log(hi))))
+            return max(128, 128 * int(round(x / 128)))
+
+        M, N, K = dim(), dim(), dim()
+        if g.random() < 0.5:
+            pick = int(g.integers(0, 3))
+            if pick == 0:
+                code, S, n, e = ("table1",), 4, 5, 3
+            elif pick == 1:
+                code, S, n, e = ("table3",), 9, 5, 2
+            else:
+                n = int(g.integers(6, 33))
+                e = int(g.integers(2, 4))
+                k = n - e
+                b = max(1, M // (16 * k))
+                code, S = ("systematic", k, e, b), k * b
+        else:
+            n = int(g.integers(6, 33))
+            e = n // 4
+            k = n - e
+            b = max(1, M // (16 * k))
+            code, S = ("mojette_a", n, k, b), k * b
+        h = -(-M // S)
+        out.append(dict(code=code, M=M, N=N, K=K, h=h, e=e, n=n, mask_seed=seed * 100003 + i + 7))
+    return out

@@ -1,0 +1,144 @@
+"""Grouped runs (bpx_grouped_run): many coded multiplications, each with its
+own code, shapes and erasure mask, in one launch per stage -- checked job by
+job against the FP64 oracle, replayed from a CUDA graph, and re-planned by
+the tile autotuner."""
+import numpy as np
+import pytest
+
+from oracle import bpx_oracle as o
+from paper_1904_11563_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _codes(bpx, spec):
+    kind, *args = spec["code"]
+    if kind == "table1":
+        return bpx.Code.table1(), o.table1()
+    if kind == "table3":
+        return bpx.Code.table3(), o.table3()
+    if kind == "systematic":
+        k, e, b = args
+        return bpx.Code.systematic(k, e, b), o.systematic_mojette(k, e, b)
+    n, k, b = args
+    return bpx.Code.mojette_a(n, k, b), o.construction_a(n, k, b)
+
+
+def _build(bpx, specs, dist, seed):
+    jobs, refs = [], []
+    for i, sp in enumerate(specs):
+        code, ref = _codes(bpx, sp)
+        A = W.matrix((sp["M"], sp["K"]), dist, seed + 2 * i)
+        B = W.matrix((sp["K"], sp["N"]), dist, seed + 2 * i + 1)
+        m = W.erasure_mask(code.n, sp["e"], sp["mask_seed"])
+        jobs.append(dict(code=code, A=torch.from_numpy(A).cuda(), B=torch.from_numpy(B).cuda(),
+                         C=bpx.alloc_C(code, sp["h"], sp["N"]), mask=torch.from_numpy(m).cuda(),
+                         info=torch.zeros(16, dtype=torch.int32, device="cuda"), h=sp["h"]))
+        refs.append((ref, A, B, m))
+    return jobs, refs
+
+
+def _check_exact(bpx, jobs, refs):
+    for j, (ref, A, B, m) in zip(jobs, refs):
+        assert j["info"].cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+        C = j["C"][:A.shape[0]].cpu().numpy()
+        assert np.array_equal(C, o.reference_product(A, B))
+
+
+SPECS = W.batch_specs(14, 5, lo=128, hi=640)
+
+
+def test_specs_cover_every_family():
+    kinds = {s["code"][0] for s in W.batch_specs(64, 5)}
+    assert kinds == {"table1", "table3", "systematic", "mojette_a"}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_grouped_integer_bit_exact(libbpx, prec):
+    bpx = libbpx
+    jobs, refs = _build(bpx, SPECS, "int", 100)
+    G = bpx.Group(jobs, bpx.PRECISIONS[prec])
+    G.run()
+    torch.cuda.synchronize()
+    _check_exact(bpx, jobs, refs)
+
+
+def test_grouped_random_within_tolerance(libbpx):
+    bpx = libbpx
+    jobs, refs = _build(bpx, SPECS[:8], "normal", 200)
+    G = bpx.Group(jobs, bpx.BF16X3)
+    G.run()
+    torch.cuda.synchronize()
+    for j, (ref, A, B, m) in zip(jobs, refs):
+        h = j["h"]
+        cells = o.surviving_cells(ref, list(np.nonzero(m)[0]))
+        sch = o.wave_schedule(ref, cells)
+        used = sorted(set(r for _s, r, _d in sch.order))
+        P = o.coded_products(ref, A, B, h, used)
+        Cd = o.peel_decode(ref, P, sch, h, B.shape[1])
+        nu = o.propagation(ref, sch, P, Cd)
+        C = j["C"].cpu().numpy()
+        for s, blk in Cd.items():
+            err = np.linalg.norm(C[s * h:(s + 1) * h] - blk) / max(np.linalg.norm(blk), 1e-30)
+            assert err <= 1e-5 * max(1.0, nu[s]), (ref.name, s, err, nu[s])
+
+
+def test_graph_replay_and_new_masks(libbpx):
+    """The captured graph reads the masks at every replay: changing them in
+    place changes the decode, and each replay is exact."""
+    bpx = libbpx
+    jobs, refs = _build(bpx, SPECS, "int", 300)
+    G = bpx.Group(jobs, bpx.BF16X3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        G.graph_launch()
+        stream.synchronize()
+        _check_exact(bpx, jobs, refs)
+        for j, r in zip(jobs, refs):
+            j["C"].zero_()
+            new = W.erasure_mask(j["code"].n, int(r[3].sum()), 999 + j["code"].n)
+            j["mask"].copy_(torch.from_numpy(new))
+        new_refs = [(ref, A, B, j["mask"].cpu().numpy()) for j, (ref, A, B, _m) in zip(jobs, refs)]
+        G.graph_launch()
+        stream.synchronize()
+    _check_exact(bpx, jobs, new_refs)
+
+
+def test_autotune_replans_and_stays_exact(libbpx):
+    bpx = libbpx
+    jobs, refs = _build(bpx, SPECS, "int", 400)
+    G = bpx.Group(jobs, bpx.BF16X3)
+    best, ms = G.autotune([16042, 16022, 8041])
+    assert best in (16042, 16022, 8041) and ms > 0
+    for j in jobs:
+        j["C"].zero_()
+    G.run()
+    torch.cuda.synchronize()
+    _check_exact(bpx, jobs, refs)
+    # force the other tile width and run again
+    G.set_config(16041 if best % 10 == 2 else 16042)
+    for j in jobs:
+        j["C"].zero_()
+    G.run()
+    torch.cuda.synchronize()
+    _check_exact(bpx, jobs, refs)
+
+
+def test_single_job_autotune_and_tile_configs(libbpx):
+    bpx = libbpx
+    code, ref = bpx.Code.systematic(8, 3, 8), o.systematic_mojette(8, 3, 8)
+    h, M, K, N = 128, 8192, 256, 1000
+    A = W.matrix((M, K), "int", 51)
+    B = W.matrix((K, N), "int", 52)
+    m = torch.from_numpy(W.erasure_mask(11, 3, 3)).cuda()
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    ws = bpx.Workspace(code, M, N, K, h, bpx.BF16X3)
+    best, ms = bpx.autotune(code, dA, dB, h, bpx.BF16X3, m, ws, configs=[16041, 16022, 4012, 32082])
+    assert best in (16041, 16022, 4012, 32082)
+    refC = o.reference_product(A, B)
+    for cfg in (16041, 16022, 4012, 32082, best):
+        C, info = bpx.coded_matmul(code, dA, dB, h, bpx.BF16X3, m, ws, opts=bpx.default_opts(gemm_config=cfg))
+        torch.cuda.synchronize()
+        assert np.array_equal(C[:M].cpu().numpy(), refC), cfg
