@@ -125,7 +125,8 @@ int peel_chunk_for(long long nv, int ctas_hint);
 // Launchers (defined in the .cu files).  All return cudaError_t of the launch.
 cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, cudaStream_t st);
 cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st);
-cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st);
+cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, bool split,
+                                      cudaStream_t st);
 cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
                               int compensate_depth, cudaStream_t st);
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,

@@ -74,7 +74,7 @@ int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
     return cuda_fail(e, "grouped B split");
   mark(o, BPX_STAGE_B_PREP, 1, st);
   mark(o, BPX_STAGE_A_PREP, 0, st);
-  if ((e = bpx::launch_encode_split_group(gj, njobs, G->enc_total, st)) != cudaSuccess)
+  if ((e = bpx::launch_encode_split_group(gj, njobs, G->enc_total, split, st)) != cudaSuccess)
     return cuda_fail(e, "grouped encode");
   mark(o, BPX_STAGE_A_PREP, 1, st);
   mark(o, BPX_STAGE_GEMM, 0, st);

@@ -181,9 +181,14 @@ cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_
   return cudaGetLastError();
 }
 
-cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st) {
+cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, bool split,
+                                      cudaStream_t st) {
   if (total_ctas <= 0) return cudaSuccess;
-  encode_group_kernel<2><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, njobs);
+  // plain bf16 jobs have no lo buffer: the hi-only variant never touches it
+  if (split)
+    encode_group_kernel<2><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, njobs);
+  else
+    encode_group_kernel<1><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, njobs);
   return cudaGetLastError();
 }
 
