@@ -117,9 +117,25 @@ __device__ __forceinline__ int find_job(const GJob* jobs, int njobs, long long x
   return lo;
 }
 
+// Encode grid geometry: 128 threads of 8 columns; a row takes
+// min(128, next power of two >= K/8) threads, the CTA the rest in rows.
+__host__ __device__ inline int enc_threads_per_row(int K) {
+  int t = 1;
+  while (t < 128 && t * 8 < K) t <<= 1;
+  return t;
+}
+__host__ __device__ inline long long enc_row_blocks(long long rows, int K) {
+  const int rpc = 128 / enc_threads_per_row(K);
+  return (rows + rpc - 1) / rpc;
+}
+__host__ __device__ inline int enc_k_chunks(int K) {
+  const int cols = enc_threads_per_row(K) * 8;
+  return (K + cols - 1) / cols;
+}
+
 // Grid sizes of the multi-job kernels for one job.
 inline long long bsplit_ctas(int N, int K) { return static_cast<long long>((N + 63) / 64) * ((K + 63) / 64); }
-inline long long encode_ctas(long long rows, int K) { return rows * ((K / 8 + 127) / 128); }
+inline long long encode_ctas(long long rows, int K) { return enc_row_blocks(rows, K) * enc_k_chunks(K); }
 int peel_chunk_for(long long nv, int ctas_hint);
 
 // Launchers (defined in the .cu files).  All return cudaError_t of the launch.

@@ -15,23 +15,27 @@
 namespace bpx {
 namespace {
 
-constexpr int kEncThreads = 128;  // 1024 columns per CTA: one K-chunk of A stays L2-resident
+constexpr int kEncThreads = 128;
 constexpr int kEncVec = 8;  // consecutive K elements per thread (two float4 loads per source)
 
-// One CTA per (coded row, 1024-column chunk); blockIdx.x walks the coded rows
-// fastest so that CTAs resident together read the same K-chunk of A (L2 reuse
-// of a source block across the cells that contain it).
+// A CTA covers `rows` coded rows x `cols` columns (cols = min(1024, K rounded
+// up to a power of two), rows = 1024 / cols): short K still fills the CTA.
+// blockIdx.x walks the coded rows fastest so that CTAs resident together read
+// the same K-chunk of A (L2 reuse of a source block across the cells that
+// contain it).
 template <int kMode>  // 0: FP32 out, 1: bf16 hi only, 2: bf16 hi + lo
 __device__ __forceinline__ void encode_body(const DevGraph& g, const DevPlan& p,
                                             const float* __restrict__ A, int M, int K, int h,
                                             float* out_f32, __nv_bfloat16* out_hi,
-                                            __nv_bfloat16* out_lo, int row, int kchunk) {
+                                            __nv_bfloat16* out_lo, int rblock, int kchunk) {
+  const int tpr = enc_threads_per_row(K);  // threads per row
+  const int row = rblock * (kEncThreads / tpr) + threadIdx.x / tpr;  // coded row, compacted order
   const int nsurv = p.ctr[CTR_NSURV];
-  if (row >= nsurv * h) return;  // row: coded row in the compacted order
+  if (row >= nsurv * h) return;
   const int ci = row / h, j = row - ci * h;
   const int cell = p.surv[ci];
   const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
-  const int k8 = (kchunk * kEncThreads + threadIdx.x) * kEncVec;
+  const int k8 = (kchunk * tpr + threadIdx.x % tpr) * kEncVec;
   if (k8 >= K) return;
   const bool full = k8 + kEncVec <= K;  // K % 8 == 0, so a chunk is full or absent
   float acc[kEncVec];
@@ -144,10 +148,10 @@ __global__ void __launch_bounds__(kEncThreads) encode_group_kernel(const GJob* _
   const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.enc_base; });
   const GJob& J = jobs[j];
   const long long local = b - J.enc_base;
-  const long long rows = static_cast<long long>(J.g.num_cells) * J.h;
+  const long long rblocks = enc_row_blocks(static_cast<long long>(J.g.num_cells) * J.h, J.K);
   encode_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, nullptr, static_cast<__nv_bfloat16*>(J.a_hi),
-                     static_cast<__nv_bfloat16*>(J.a_lo), static_cast<int>(local % rows),
-                     static_cast<int>(local / rows));
+                     static_cast<__nv_bfloat16*>(J.a_lo), static_cast<int>(local % rblocks),
+                     static_cast<int>(local / rblocks));
 }
 
 }  // namespace
@@ -156,7 +160,7 @@ cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* 
                               int h, float* out, cudaStream_t st) {
   const long long rows = static_cast<long long>(g.num_cells) * h;
   if (rows == 0 || K == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(rows), (K / kEncVec + kEncThreads - 1) / kEncThreads);
+  dim3 grid(static_cast<unsigned>(enc_row_blocks(rows, K)), static_cast<unsigned>(enc_k_chunks(K)));
   encode_kernel<0><<<grid, kEncThreads, 0, st>>>(g, p, A, M, K, h, out, nullptr, nullptr);
   return cudaGetLastError();
 }
@@ -165,7 +169,7 @@ cudaError_t launch_encode_split(const DevGraph& g, const DevPlan& p, const float
                                 int h, void* a_hi, void* a_lo, cudaStream_t st) {
   const long long rows = static_cast<long long>(g.num_cells) * h;
   if (rows == 0 || K == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(rows), (K / kEncVec + kEncThreads - 1) / kEncThreads);
+  dim3 grid(static_cast<unsigned>(enc_row_blocks(rows, K)), static_cast<unsigned>(enc_k_chunks(K)));
   auto hi = static_cast<__nv_bfloat16*>(a_hi);
   auto lo = static_cast<__nv_bfloat16*>(a_lo);
   if (lo)

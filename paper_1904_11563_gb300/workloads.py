@@ -113,7 +113,8 @@ def batch_specs(njobs: int, seed: int, lo: int = 256, hi: int = 4096):
     M, N, K each 128 * round(x / 128) with x log-uniform on [lo, hi]; half
     array codes (Table I, Table III, systematic Mojette n in 6..32 with e in
     {2, 3}), half projection codes (Construction A, n in 6..32, e =
-    floor(n / 4)); grid height b = max(1, M // (16 k)); h = ceil(M / S);
+    floor(n / 4)); grid height b = max(1, M // k), the tallest grid the rows
+    allow (a projection code's overhead falls as 1 / b); h = ceil(M / S);
     each job's erasure mask drawn from its own seed.  Returns dicts with
     code=(kind, *params), M, N, K, h, e, n, mask_seed."""
     out = []
@@ -135,13 +136,13 @@ def batch_specs(njobs: int, seed: int, lo: int = 256, hi: int = 4096):
                 n = int(g.integers(6, 33))
                 e = int(g.integers(2, 4))
                 k = n - e
-                b = max(1, M // (16 * k))
+                b = max(1, M // k)
                 code, S = ("systematic", k, e, b), k * b
         else:
             n = int(g.integers(6, 33))
             e = n // 4
             k = n - e
-            b = max(1, M // (16 * k))
+            b = max(1, M // k)
             code, S = ("mojette_a", n, k, b), k * b
         h = -(-M // S)
         out.append(dict(code=code, M=M, N=N, K=K, h=h, e=e, n=n, mask_seed=seed * 100003 + i + 7))
