@@ -308,6 +308,16 @@ int bpx_schedule_noalloc(const bpx_code* code, const uint8_t* d_erasure_mask,
                          int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info,
                          bpx_stream stream);
 
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * thread that waits, through the same bounded mbarrier wait the tensor-core
+ * GEMM uses, on a barrier nothing ever arrives at.  After budget_cycles
+ * (0 < budget <= the GEMM's own budget of 4e9 cycles) the wait gives up and the
+ * kernel writes BPX_ERR_TIMEOUT into d_info[BPX_INFO_STATUS] and
+ * [BPX_INFO_DEVICE_ERR] (cycles waited in d_info[6]) and returns normally, so
+ * the context stays usable.  The GEMM handles an expired wait the same way
+ * (after letting its in-flight copies land and freeing its TMEM). */
+int bpx_selftest_wait_timeout(long long budget_cycles, int32_t* d_info, bpx_stream stream);
+
 /* Default options (direct_write = 1, compensate_depth = -1, autos). */
 bpx_opts bpx_default_opts(void);
 

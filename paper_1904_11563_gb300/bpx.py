@@ -102,6 +102,7 @@ def lib():
         "bpx_autotune": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, vp, sz, ct.POINTER(ct.c_int), i, vp,
                              ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
         "bpx_group_free": (None, [vp]),
+        "bpx_selftest_wait_timeout": (i, [ct.c_longlong, vp, vp]),
         "bpx_default_opts": (Opts, []),
         "bpx_build_info": (ct.c_char_p, []),
     }

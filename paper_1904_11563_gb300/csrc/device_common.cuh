@@ -144,7 +144,7 @@ cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_
 cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, bool split,
                                       cudaStream_t st);
 cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
-                              int compensate_depth, cudaStream_t st);
+                              int compensate_depth, int max_sigma, cudaStream_t st);
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st);
 size_t tc_job_bytes();

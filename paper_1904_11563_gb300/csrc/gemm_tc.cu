@@ -61,8 +61,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait for the phase with the given parity; false on timeout, or on
+// abort when an abort flag is given.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          long long budget = kWaitBudget) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -74,8 +76,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (abort_flag && *abort_flag) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -304,6 +306,14 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * BK, T.n * kBN);
         }
       }
+      if (!ok || abort_flag) {
+        // Stopping early: let the copies this CTA still has in flight land
+        // (bounded waits, abort ignored) before its shared memory goes away.
+        for (int i = 0; i < kStages && i < kb_all; ++i) {
+          const int kb = kb_all - 1 - i;
+          mbar_wait(smem_u32(&full_bar[kb % kStages]), static_cast<uint32_t>((kb / kStages) & 1), nullptr);
+        }
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -421,6 +431,21 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
                  "r"(kTmemCols)
                  : "memory");
   }
+}
+
+// Failure-detection self-test: one thread waits on an mbarrier that nothing
+// will ever arrive at, through the same bounded wait the GEMM uses, and
+// reports BPX_ERR_TIMEOUT when the budget runs out.
+__global__ void wait_timeout_kernel(long long budget, int32_t* info) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const long long t0 = clock64();
+  const bool done = mbar_wait(smem_u32(&bar), 0u, nullptr, budget);
+  info[BPX_INFO_STATUS] = done ? BPX_OK : BPX_ERR_TIMEOUT;
+  info[BPX_INFO_DEVICE_ERR] = done ? 0 : BPX_ERR_TIMEOUT;
+  info[6] = static_cast<int32_t>(min(clock64() - t0, static_cast<long long>(INT32_MAX)));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
@@ -578,3 +603,14 @@ cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long tota
 }
 
 }  // namespace bpx
+
+extern "C" int bpx_selftest_wait_timeout(long long budget_cycles, int32_t* d_info, bpx_stream stream) {
+  bpx::clear_error();
+  if (!d_info || budget_cycles <= 0 || budget_cycles > bpx::kWaitBudget)
+    return bpx::fail(BPX_ERR_INVAL, "bpx_selftest_wait_timeout: need d_info and 0 < budget <= %lld cycles",
+                     bpx::kWaitBudget);
+  bpx::wait_timeout_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(budget_cycles, d_info);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bpx::fail(BPX_ERR_CUDA, "bpx_selftest_wait_timeout: %s", cudaGetErrorString(e));
+  return BPX_OK;
+}

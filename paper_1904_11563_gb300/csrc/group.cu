@@ -20,6 +20,7 @@ struct bpx_group {
   std::vector<size_t> offsets;
   size_t gjob_off = 0, tc_off = 0, total = 0;
   size_t max_state_bytes = 0;
+  int max_sigma = 1;
   long long bsplit_total = 0, enc_total = 0, peel_total = 0, tiles_total = 0;
   void* ws = nullptr;
   int table_config = -1;  // tile config the device GEMM table was built for
@@ -84,7 +85,7 @@ int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
   mark(o, BPX_STAGE_GEMM, 1, st);
   (void)direct;
   mark(o, BPX_STAGE_PEEL, 0, st);
-  if ((e = bpx::launch_peel_group(gj, njobs, G->peel_total, 2, comp, st)) != cudaSuccess)
+  if ((e = bpx::launch_peel_group(gj, njobs, G->peel_total, 2, comp, G->max_sigma, st)) != cudaSuccess)
     return cuda_fail(e, "grouped peel");
   mark(o, BPX_STAGE_PEEL, 1, st);
   return BPX_OK;
@@ -117,6 +118,7 @@ extern "C" int bpx_group_create(const bpx_job* jobs, int njobs, int precision, b
     off = bpx::align_up(off + L.total, 256);
     G->max_state_bytes =
         std::max(G->max_state_bytes, (static_cast<size_t>(c->num_cells) + c->S) * sizeof(int32_t));
+    G->max_sigma = std::max(G->max_sigma, c->sigma);
   }
   G->gjob_off = off;
   off = bpx::align_up(off + sizeof(bpx::GJob) * njobs, 256);

@@ -34,7 +34,7 @@ __device__ __forceinline__ void sub4(float4& a, const float4& x) {
 
 // One (source, float4) item: C_s[v] = P_r[v] - sum of the listed blocks,
 // subtracted in ascending source id.
-template <bool kF64>
+template <bool kF64, int kB>
 __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, float4* C4, long long nv,
                                           int i, long long v) {
   const int s = p.order[i];
@@ -43,9 +43,11 @@ __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, fl
   const int e1 = p.pl_ptr[i + 1];
   const float4 pr = ldg_stream(P4 + static_cast<long long>(r) * nv + v);
   if (!kF64) {
-    // 16 list entries, then 16 independent block loads, then the ascending
-    // subtractions: two round trips per 16 subtrahends.
-    constexpr int kB = 16;
+    // kB list entries, then kB independent block loads, then the ascending
+    // subtractions: two round trips per kB subtrahends.  kB follows the
+    // code's largest degree: wide batches hide latency on deep, sparse
+    // waves; narrow ones keep registers low for the wide, bandwidth-bound
+    // waves of tall blocks.
     float4 acc = pr;
     for (; e < e1; e += kB) {
       int t[kB];
@@ -76,6 +78,7 @@ __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, fl
   }
 }
 
+template <int kB>
 __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restrict__ P, float* C,
                                           long long nv, int chunk, int first_wave,
                                           int compensate_depth, long long cta) {
@@ -94,28 +97,32 @@ __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restr
       const int j = it / clen;
       const long long v = v0 + (it - j * clen);
       if (comp)
-        peel_item<true>(p, P4, C4, nv, o0 + j, v);
+        peel_item<true, kB>(p, P4, C4, nv, o0 + j, v);
       else
-        peel_item<false>(p, P4, C4, nv, o0 + j, v);
+        peel_item<false, kB>(p, P4, C4, nv, o0 + j, v);
     }
     __syncthreads();
   }
 }
 
+template <int kB>
 __global__ void __launch_bounds__(kPeelThreads)
 peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk, int first_wave,
             int compensate_depth) {
-  peel_body(p, P, C, nv, chunk, first_wave, compensate_depth, blockIdx.x);
+  peel_body<kB>(p, P, C, nv, chunk, first_wave, compensate_depth, blockIdx.x);
 }
 
+template <int kB>
 __global__ void __launch_bounds__(kPeelThreads)
 peel_group_kernel(const GJob* __restrict__ jobs, int njobs, int first_wave, int compensate_depth) {
   const long long b = blockIdx.x;
   const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.peel_base; });
   const GJob& J = jobs[j];
   const long long nv = static_cast<long long>(J.h) * J.N / 4;
-  peel_body(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - J.peel_base);
+  peel_body<kB>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - J.peel_base);
 }
+
+int batch_for(int sigma) { return sigma > 9 ? 16 : (sigma > 5 ? 8 : 4); }
 
 }  // namespace
 
@@ -126,10 +133,14 @@ int peel_chunk_for(long long nv, int ctas_hint) {
 }
 
 cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
-                              int compensate_depth, cudaStream_t st) {
+                              int compensate_depth, int max_sigma, cudaStream_t st) {
   if (total_ctas <= 0) return cudaSuccess;
-  peel_group_kernel<<<static_cast<unsigned>(total_ctas), kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave,
-                                                                                compensate_depth);
+  const unsigned grid = static_cast<unsigned>(total_ctas);
+  switch (batch_for(max_sigma)) {
+    case 4: peel_group_kernel<4><<<grid, kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave, compensate_depth); break;
+    case 8: peel_group_kernel<8><<<grid, kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave, compensate_depth); break;
+    default: peel_group_kernel<16><<<grid, kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave, compensate_depth);
+  }
   return cudaGetLastError();
 }
 
@@ -139,8 +150,13 @@ cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, flo
   if (nv <= 0) return cudaSuccess;
   const long long chunk = peel_chunk_for(nv, ctas);
   const long long grid = (nv + chunk - 1) / chunk;
-  peel_kernel<<<static_cast<unsigned>(grid), kPeelThreads, 0, st>>>(
-      p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);
+  const unsigned gr = static_cast<unsigned>(grid);
+  const int ck = static_cast<int>(chunk);
+  switch (batch_for(g.sigma)) {
+    case 4: peel_kernel<4><<<gr, kPeelThreads, 0, st>>>(p, P, C, nv, ck, first_wave, compensate_depth); break;
+    case 8: peel_kernel<8><<<gr, kPeelThreads, 0, st>>>(p, P, C, nv, ck, first_wave, compensate_depth); break;
+    default: peel_kernel<16><<<gr, kPeelThreads, 0, st>>>(p, P, C, nv, ck, first_wave, compensate_depth);
+  }
   return cudaGetLastError();
 }
 

@@ -382,3 +382,22 @@ def test_construction_a_full_size_integer_bit_exact(libbpx, prec):
     An = A[rows].cpu().numpy().astype(np.float64)
     ref = An @ Bh
     assert np.array_equal(Cn, ref), (prec, np.abs(Cn - ref).max())
+
+
+@pytest.mark.parametrize("wl_name,code_name", [("table1_logu", "table1"), ("table3_logu", "table3")])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_precision_study_loguniform(libbpx, wl_name, code_name, prec):
+    """Precision workload: magnitudes log-uniform on [1e-3, 1e3] with random
+    signs (cancellation in the peel), every mask of <= 2 erased columns
+    (Table I also its 3-column ones), compensated (FP64) peel below depth 3;
+    every block within its tolerance times its propagation factor."""
+    bpx = libbpx
+    wl = W.WORKLOADS[wl_name]
+    code, ref = _pair(bpx, code_name)
+    A, B = W.inputs(wl["M"], wl["K"], wl["N"], wl["dist"], wl["seed"])
+    opts = bpx.default_opts(compensate_depth=3)
+    for m in _masks(ref, 3 if code_name == "table1" else 2):
+        C, info = _run(bpx, code, A, B, wl["h"], bpx.PRECISIONS[prec], m, opts=opts)
+        R, sch = _oracle_decode(ref, A, B, wl["h"], m)
+        assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
+        _check_blocks(C, R, ref, A, B, wl["h"], m, prec)
