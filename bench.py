@@ -71,7 +71,8 @@ def _parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--gemm-config", type=int, default=0)
+    ap.add_argument("--gemm-config", type=int, default=0,
+                    help="tensor-core GEMM tile config; 0 = run the library's autotuner first")
     ap.add_argument("--precisions", default="",
                     help="comma list overriding the timed precisions (e.g. 'bf16x3' for profiling)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(CODE_TEXT))
@@ -287,6 +288,7 @@ def run_ours(args, wl):
     if cvd and cvd.split(",")[0].strip().isdigit():
         gpu_index = int(cvd.split(",")[local].strip())
 
+    tuned = {}
     surv_rows = []
     col_cells = np.diff(code.col_ptr)
     for t in range(trials):
@@ -301,7 +303,11 @@ def run_ours(args, wl):
             continue
         C = bpx.alloc_C(code, h, N, dev)
         info = torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device=dev)
-        opts = bpx.default_opts(gemm_config=args.gemm_config)
+        cfg = args.gemm_config
+        if cfg == 0 and prec in ("bf16x3", "bf16"):
+            cfg, _tuned_ms = bpx.autotune(code, A, Bm, h, P, masks[0], ws, C=C)
+        tuned[prec] = cfg
+        opts = bpx.default_opts(gemm_config=cfg)
         try:
             for i in range(warm):
                 bpx.coded_matmul(code, A, Bm, h, P, masks[i % wl["trials"]], ws, C=C, opts=opts, info=info)
@@ -321,7 +327,7 @@ def run_ours(args, wl):
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
         for i in range(steps):
-            o = bpx.default_opts(gemm_config=args.gemm_config)
+            o = bpx.default_opts(gemm_config=cfg)
             o.stage_events = sev.ptr(i)
             bpx.coded_matmul(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o, info=info)
         t1.record()
@@ -425,6 +431,7 @@ def run_ours(args, wl):
             "warmup": warm, "ms_per_step": R["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": head, "data": "synthetic", "config": _config(wl)}
     line["stages_ms"] = R["stage"]
+    line["gemm_config"] = tuned
     for prec, r in results.items():
         line[f"{prec}_tflops"] = world * useful / (r["ms"] * 1e-3) / 1e12
         line[f"{prec}_ms_per_step"] = r["ms"]
@@ -461,7 +468,7 @@ def run_ours(args, wl):
         t_s = time.perf_counter()
         for i in range(e2e_steps):
             rc, _ = bpx.coded_matmul_host(code, hA, hB, h, P, hmasks[i % wl["trials"]], hC, dA, dB,
-                                          dmask, dC, ws)
+                                          dmask, dC, ws, opts=bpx.default_opts(gemm_config=tuned.get(head, 0)))
             assert rc == bpx.OK
         dt = (time.perf_counter() - t_s) / e2e_steps
         line["e2e"] = {"value": useful / dt / 1e12, "unit": "TFLOP/s",

@@ -180,6 +180,24 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
         return fail(BPX_ERR_UNSUPPORTED, "bf16 tensor-core path not available in this build");
       break;
     }
+    case BPX_MXFP8: {
+      if (K % 128 != 0) return fail(BPX_ERR_INVAL, "BPX_MXFP8 needs K %% 128 == 0 (K = %d)", K);
+      void* a8 = base + L.a_hi;
+      void* b8 = base + L.b_hi;
+      void* sfa = base + L.a_scale;
+      void* sfb = base + L.b_scale;
+      stage_mark(opts, BPX_STAGE_B_PREP, 0, st);
+      e = bpx::launch_b_mx(d_B, K, N, b8, sfb, st);
+      stage_mark(opts, BPX_STAGE_B_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
+      if (e == cudaSuccess) e = bpx::launch_encode_mx(g, p, d_A, M, K, h, a8, sfa, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 0, st);
+      if (e == cudaSuccess)
+        e = bpx::launch_gemm_mx(p, a8, sfa, b8, sfb, c->num_cells, N, K, h, d_products, d_C, config, d_info, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 1, st);
+      break;
+    }
     default:
       return fail(BPX_ERR_UNSUPPORTED, "precision %d not supported", precision);
   }

@@ -317,10 +317,14 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
       L.b_lo = take(Np * Kp * 2);
     }
   } else if (precision == BPX_MXFP8) {
+    // E4M3 operands (K-major rows) and UE8M0 scales, one per 32 K-elements,
+    // stored per (tile, 128-wide K stage) in the order the GEMM copies them
+    // to tensor memory: 512 B per 128-row A tile, 1 KB per 256-column B tile.
+    const size_t ks = (Kp + 127) / 128;
     L.a_hi = take(rowsA * Kp);
     L.b_hi = take(Np * Kp);
-    L.a_scale = take(rowsA * ((Kp + 31) / 32) + 128 * 64);
-    L.b_scale = take(Np * ((Kp + 31) / 32) + 128 * 64);
+    L.a_scale = take(((rowsA + 127) / 128) * ks * 512);
+    L.b_scale = take(((Np + 255) / 256) * ks * 1024);
   }
   L.total = off;
   return L;

@@ -173,6 +173,13 @@ cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* 
 cudaError_t launch_encode_split(const DevGraph& g, const DevPlan& p, const float* A, int M, int K,
                                 int h, void* a_hi, void* a_lo, cudaStream_t st);
 cudaError_t launch_b_split(const float* B, int K, int N, void* b_hi, void* b_lo, cudaStream_t st);
+// MXFP8 staging (E4M3 data + UE8M0 scales in the GEMM's per-stage order) and GEMM.
+cudaError_t launch_encode_mx(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
+                             void* out, void* sfa, cudaStream_t st);
+cudaError_t launch_b_mx(const float* B, int K, int N, void* bt, void* sfb, cudaStream_t st);
+cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, const void* b8, const void* sfb,
+                           int num_cells, int N, int K, int h, float* products, float* C_direct, int config,
+                           int32_t* info_out, cudaStream_t st);
 cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* A, const float* B,
                             int M, int N, int K, int h, float* products, float* C_direct,
                             cudaStream_t st);

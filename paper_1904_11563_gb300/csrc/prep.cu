@@ -9,6 +9,7 @@
 // c_i is the i-th surviving cell of the plan.  Rows of A past M read as zero
 // (the zero padding of the last source blocks).  All are HBM-bound streams.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "device_common.cuh"
 
@@ -154,7 +155,146 @@ __global__ void __launch_bounds__(kEncThreads) encode_group_kernel(const GJob* _
                      static_cast<int>(local / rblocks));
 }
 
+// ---- MXFP8 staging -------------------------------------------------------
+//
+// Every run of 32 consecutive K-elements of a row gets one UE8M0 scale 2^e,
+// e = the smallest integer with amax / 2^e <= 448 (the largest finite E4M3),
+// and its elements become RN-satfinite E4M3 of x / 2^e.  The four threads
+// that own a 32-run (8 elements each) agree on amax through shuffles.
+
+__device__ __forceinline__ int ue8m0_of(float amax) {
+  if (!(amax > 0.f)) return 0;
+  const float y = amax / 448.f;
+  const uint32_t bits = __float_as_uint(y);
+  int e = static_cast<int>((bits >> 23) & 0xFF) - 127;
+  if ((bits & 0x7FFFFF) != 0 || ((bits >> 23) & 0xFF) == 0) e += 1;  // ceil(log2 y)
+  return max(0, min(254, e + 127));
+}
+
+__device__ __forceinline__ uint2 e4m3x8(const float (&v)[8], int sbyte) {
+  const int e = sbyte - 127;
+  uint32_t w[2] = {0u, 0u};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_fp8x2_storage_t q = __nv_cvt_float2_to_fp8x2(
+        make_float2(ldexpf(v[2 * i], -e), ldexpf(v[2 * i + 1], -e)), __NV_SATFINITE, __NV_E4M3);
+    w[i >> 1] |= static_cast<uint32_t>(q) << (16 * (i & 1));
+  }
+  return make_uint2(w[0], w[1]);
+}
+
+// Coded A -> E4M3 rows + A scale blocks (512 B per 128-row tile and 128-wide
+// K stage: byte 16 l + 4 q + j holds row 32 q + l, K-run 4 s + j).
+__device__ __forceinline__ void encode_mx_body(const DevGraph& g, const DevPlan& p,
+                                               const float* __restrict__ A, int M, int K, int h,
+                                               uint8_t* out, uint8_t* sfa, int rblock, int kchunk) {
+  const int tpr = enc_threads_per_row(K);
+  const int row = rblock * (kEncThreads / tpr) + threadIdx.x / tpr;
+  const int nsurv = p.ctr[CTR_NSURV];
+  const int k8 = (kchunk * tpr + threadIdx.x % tpr) * kEncVec;
+  const bool valid = row < nsurv * h && k8 < K;
+  float acc[kEncVec];
+#pragma unroll
+  for (int i = 0; i < kEncVec; ++i) acc[i] = 0.f;
+  if (valid) {
+    const int ci = row / h, j = row - ci * h;
+    const int cell = p.surv[ci];
+    for (int e = g.cell_ptr[cell]; e < g.cell_ptr[cell + 1]; ++e) {
+      const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+      if (arow >= M) continue;
+      const float4* src = reinterpret_cast<const float4*>(A + arow * K + k8);
+      const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+      acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
+      acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
+    }
+  }
+  float am = 0.f;
+#pragma unroll
+  for (int i = 0; i < kEncVec; ++i) am = fmaxf(am, fabsf(acc[i]));
+  am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+  am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+  if (!valid) return;
+  const int sbyte = ue8m0_of(am);
+  *reinterpret_cast<uint2*>(out + static_cast<long long>(row) * K + k8) = e4m3x8(acc, sbyte);
+  if ((k8 & 31) == 0) {
+    const int kblk = k8 >> 5, ks = kblk >> 2, kb = kblk & 3, KS = K / 128;
+    const int mt = row >> 7, rr = row & 127;
+    sfa[(static_cast<long long>(mt) * KS + ks) * 512 + 16 * (rr & 31) + 4 * (rr >> 5) + kb] =
+        static_cast<uint8_t>(sbyte);
+  }
+}
+
+__global__ void __launch_bounds__(kEncThreads)
+encode_mx_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, int h, uint8_t* out,
+                 uint8_t* sfa) {
+  encode_mx_body(g, p, A, M, K, h, out, sfa, blockIdx.x, blockIdx.y);
+}
+
+// B (K x N FP32) -> B^T E4M3 (N x K) + B scale blocks (1 KB per 256-column
+// tile and 128-wide K stage: byte 512 t + 16 l + 4 c + j holds column
+// 128 t + 32 c + l, K-run 4 s + j).
+__global__ void __launch_bounds__(256)
+b_mx_kernel(const float* __restrict__ B, int K, int N, uint8_t* bt, uint8_t* sfb) {
+  __shared__ float tile[kTile][kTile + 1];
+  const int n0 = blockIdx.x * kTile, k0 = blockIdx.y * kTile;
+  {
+    const int c4 = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + 16 * i, k = k0 + r, n = n0 + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < K && n < N) v = __ldg(reinterpret_cast<const float4*>(B + static_cast<long long>(k) * N + n));
+      tile[r][4 * c4 + 0] = v.x;
+      tile[r][4 * c4 + 1] = v.y;
+      tile[r][4 * c4 + 2] = v.z;
+      tile[r][4 * c4 + 3] = v.w;
+    }
+  }
+  __syncthreads();
+  const int KS = K / 128;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int t = threadIdx.x + 256 * i;
+    const int r = t >> 3, kc = t & 7;  // 8 consecutive lanes share a column; 4 lanes = one 32-run
+    const int n = n0 + r, k = k0 + 8 * kc;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = tile[8 * kc + q][r];
+    float am = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) am = fmaxf(am, fabsf(v[q]));
+    am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+    am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+    if (n >= N || k >= K) continue;
+    const int sbyte = ue8m0_of(am);
+    *reinterpret_cast<uint2*>(bt + static_cast<long long>(n) * K + k) = e4m3x8(v, sbyte);
+    if ((kc & 3) == 0) {
+      const int kblk = k >> 5, ks = kblk >> 2, kb = kblk & 3;
+      const int nt = n >> 8, nn = n & 255;
+      sfb[(static_cast<long long>(nt) * KS + ks) * 1024 + 512 * (nn >> 7) + 16 * (nn & 31) +
+          4 * ((nn & 127) >> 5) + kb] = static_cast<uint8_t>(sbyte);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_encode_mx(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
+                             void* out, void* sfa, cudaStream_t st) {
+  const long long rows = static_cast<long long>(g.num_cells) * h;
+  if (rows == 0 || K == 0) return cudaSuccess;
+  dim3 grid(static_cast<unsigned>(enc_row_blocks(rows, K)), static_cast<unsigned>(enc_k_chunks(K)));
+  encode_mx_kernel<<<grid, kEncThreads, 0, st>>>(g, p, A, M, K, h, static_cast<uint8_t*>(out),
+                                                 static_cast<uint8_t*>(sfa));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_mx(const float* B, int K, int N, void* bt, void* sfb, cudaStream_t st) {
+  if (K == 0 || N == 0) return cudaSuccess;
+  dim3 grid((N + kTile - 1) / kTile, (K + kTile - 1) / kTile);
+  b_mx_kernel<<<grid, 256, 0, st>>>(B, K, N, static_cast<uint8_t*>(bt), static_cast<uint8_t*>(sfb));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* A, int M, int K,
                               int h, float* out, cudaStream_t st) {

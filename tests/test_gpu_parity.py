@@ -401,3 +401,54 @@ def test_precision_study_loguniform(libbpx, wl_name, code_name, prec):
         R, sch = _oracle_decode(ref, A, B, wl["h"], m)
         assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
         _check_blocks(C, R, ref, A, B, wl["h"], m, prec)
+
+
+TOL["mxfp8"] = 6e-2
+
+
+@pytest.mark.parametrize("name,h,M,K,N", [
+    ("table1", 16, 64, 256, 96),
+    ("table3", 8, 70, 384, 200),
+    ("table1", 130, 520, 128, 260),
+])
+def test_mxfp8_exact_on_small_integers(libbpx, name, h, M, K, N):
+    """MXFP8 (E4M3 with one UE8M0 scale per 32 K-elements): with degree-two
+    codes and integers in [-2, 2] every coded 32-run scales onto E4M3 values
+    exactly (|x| <= 4 becomes a multiple of 64 or 128 not above 448), so the
+    decode is bit-exact."""
+    bpx = libbpx
+    code, ref = _pair(bpx, name)
+    A = W.matrix((M, K), "int", 71)
+    B = W.matrix((K, N), "int", 72)
+    ref_C = o.reference_product(A, B)
+    for t in range(5):
+        m = W.erasure_mask(code.n, t % (code.e + 1), 300 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m)
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        assert np.array_equal(C[:M], ref_C), (name, m, np.abs(C[:M] - ref_C).max())
+
+
+def test_mxfp8_table1_all_masks(libbpx):
+    bpx = libbpx
+    wl = W.WORKLOADS["table1_512"]
+    code, ref = _pair(bpx, "table1")
+    A, B = W.inputs(wl["M"], wl["K"], wl["N"], wl["dist"], wl["seed"])
+    for m in _masks(ref, 3):
+        C, info = _run(bpx, code, A, B, wl["h"], bpx.MXFP8, m)
+        R, sch = _oracle_decode(ref, A, B, wl["h"], m)
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        _check_blocks(C, R, ref, A, B, wl["h"], m, "mxfp8")
+
+
+def test_mxfp8_many_tiles(libbpx):
+    """~600 tiles of 128 x 256 on the benchmark code: the single TMEM
+    accumulator is drained and refilled on every tile of every CTA."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 128, 8192, 512, 2048
+    A, B = W.inputs(M, K, N, "uniform", 91)
+    m = W.erasure_mask(11, 3, 2001)
+    C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m)
+    assert info[bpx.INFO_STATUS] == bpx.OK
+    R, sch = _oracle_decode(ref, A, B, h, m)
+    _check_blocks(C, R, ref, A, B, h, m, "mxfp8")
