@@ -68,7 +68,7 @@ def _parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "mxfp8", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemm-config", type=int, default=0,
@@ -278,7 +278,7 @@ def run_ours(args, wl):
     if args.precisions:
         precs = [x for x in args.precisions.split(",") if x]
     elif args.precision == "auto":
-        precs = ["bf16x3", "fp32"]
+        precs = ["bf16x3", "fp32", "mxfp8"]
     else:
         precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
     results = {}
@@ -344,6 +344,7 @@ def run_ours(args, wl):
         assert inf[bpx.INFO_STATUS] == bpx.OK, inf
         stage = {}
         recorded = ["schedule", "gemm", "peel"] + (["b_prep", "a_prep"] if prec != "fp32" else [])
+        # (the autotuner covers the bf16 tensor-core kernels only)
         for si, nm in enumerate(bpx.STAGE_NAMES):
             if nm not in recorded:
                 continue
@@ -439,6 +440,26 @@ def run_ours(args, wl):
         line["speedup_bf16x3_vs_fp32"] = results["fp32"]["ms"] / results["bf16x3"]["ms"]
     line["rel_err"] = rel
     line["roofline"] = roof
+    # every precision's GEMM against its own peak (FP8: the measured bf16 peak
+    # times the nominal fp8 / bf16 ratio of 2)
+    gr = {}
+    for prec, r in results.items():
+        gm = r["stage"].get("gemm", 0.0)
+        rows_m = sum(r["rows"]) / len(r["rows"])
+        if gm <= 0:
+            continue
+        if prec == "fp32":
+            mhz = peaks.get("sm_max_mhz", 2070.0)
+            pk, unit = sms * 128 * 2 * mhz * 1e6 / 1e12, "FFMA"
+            work = 2.0 * rows_m * N * K
+        else:
+            mult = {"bf16x3": 3, "bf16": 1, "mxfp8": 1}[prec]
+            pk = peaks.get("bf16_tflops", 1900.0) * (2.0 if prec == "mxfp8" else 1.0)
+            unit = "measured bf16 burst" + (" x 2 (nominal fp8/bf16)" if prec == "mxfp8" else "")
+            work = 2.0 * rows_m * N * K * mult
+        ach = work / (gm * 1e-3) / 1e12
+        gr[prec] = {"achieved_tflops": ach, "peak_tflops": pk, "frac": ach / pk, "peak": unit, "gemm_ms": gm}
+    line["gemm_roofline"] = gr
     line["peel_ms"] = peel_ms
     hbm = peaks.get("hbm_gbs", 6800.0)
     line["decode"] = {"bytes_per_step": peel_b, "ms": peel_ms,
@@ -446,7 +467,7 @@ def run_ours(args, wl):
                       "frac_hbm": (peel_b / (peel_ms * 1e-3) / 1e9) / hbm if peel_ms > 0 else None,
                       "bytes_def": "sum over non-direct sources of (deg(resolver)+1) h N 4"}
     line["clocks"] = R["clocks"]
-    per_step = {"bf16x3": 5, "bf16": 5, "fp32": 3}[head]
+    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 3}[head]
     line["gpu_launches"] = per_step * steps
 
     # end to end through the host entry point (pinned host buffers)
