@@ -206,7 +206,10 @@ struct TileRef {
   bool live;
 };
 
-__device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group) {
+// live_mc >= 0: a single job whose surviving row count is already known; its
+// tile space then holds the live m-tiles only (no skipped tiles inside the
+// rasterisation bands).
+__device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {  // last job with tile_base <= t
     const int mid = (lo + hi + 1) >> 1;
@@ -217,13 +220,14 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   R.J = &jobs[lo];
   const TcJob& J = *R.J;
   const int lt = static_cast<int>(t - J.tile_base);
+  R.Mc = live_mc >= 0 ? live_mc : J.ctr[CTR_NSURV] * J.h;
+  const int m_tiles = live_mc >= 0 ? (live_mc + BM - 1) / BM : J.m_tiles_max;
   const int band_tiles = group * J.n_tiles;
   const int band = lt / band_tiles;
   const int r = lt - band * band_tiles;
-  const int rows_in_band = min(group, J.m_tiles_max - band * group);
+  const int rows_in_band = min(group, m_tiles - band * group);
   R.m = band * group + r % rows_in_band;
   R.n = r / rows_in_band;
-  R.Mc = J.ctr[CTR_NSURV] * J.h;
   R.k_blocks = (J.K + BK - 1) / BK;
   R.live = R.m * BM < R.Mc;
   return R;
@@ -246,6 +250,9 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   const TcJob* jobs = table ? table : &single;
   const bool grouped = table != nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // A single job reads its surviving row count once and walks live tiles only.
+  const int live_mc = grouped ? -1 : single.ctr[CTR_NSURV] * single.h;
+  if (!grouped) total_tiles = static_cast<long long>((live_mc + BM - 1) / BM) * single.n_tiles;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -278,7 +285,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       bool ok = true;
       const TcJob* fenced = nullptr;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileRef T = locate(jobs, njobs, t, group);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc);
         if (!T.live) continue;
         if (grouped && T.J != fenced) {
           tensormap_acquire(&T.J->map_ahi);
@@ -320,7 +327,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       int kb_all = 0, g = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileRef T = locate(jobs, njobs, t, group);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc);
         if (!T.live) continue;
         const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
@@ -374,7 +381,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     int g = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-      const TileRef T = locate(jobs, njobs, t, group);
+      const TileRef T = locate(jobs, njobs, t, group, live_mc);
       if (!T.live) continue;
       const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
       float accum[kCols];
