@@ -280,8 +280,10 @@ int bpx_group_autotune(bpx_group* group, const int* configs, int nconfigs, bpx_s
 /* Tile autotuner for one coded multiplication on the tensor cores: runs the
  * whole path once, then times the GEMM under each candidate configuration.
  * gemm_config = band * 1000 + seg_kb * 10 + tile, tile 1 = 128x256 and
- * 2 = 128x128 output tiles, seg_kb = k-blocks of 64 per TMEM accumulation
- * segment, band = m-tiles per rasterisation band.  Synchronizes. */
+ * 2 = 128x128 output tiles, 3 / 4 = the same in clusters of two CTAs that
+ * share (multicast) each B tile; seg_kb = k-blocks of 64 per TMEM
+ * accumulation segment, band = m-tiles (or m-tile pairs) per rasterisation
+ * band.  Synchronizes. */
 int bpx_autotune(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
                  int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
                  const int* configs, int nconfigs, bpx_stream stream, int* best_config, float* best_ms);

@@ -208,8 +208,11 @@ struct TileRef {
 
 // live_mc >= 0: a single job whose surviving row count is already known; its
 // tile space then holds the live m-tiles only (no skipped tiles inside the
-// rasterisation bands).
-__device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc) {
+// rasterisation bands).  pair: the tile space counts pairs of vertically
+// adjacent m-tiles (two CTAs of a cluster share the B tile); m is then the
+// pair index and `live` tells whether the pair covers surviving rows.
+__device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc,
+                                          bool pair) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {  // last job with tile_base <= t
     const int mid = (lo + hi + 1) >> 1;
@@ -221,19 +224,50 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   const TcJob& J = *R.J;
   const int lt = static_cast<int>(t - J.tile_base);
   R.Mc = live_mc >= 0 ? live_mc : J.ctr[CTR_NSURV] * J.h;
-  const int m_tiles = live_mc >= 0 ? (live_mc + BM - 1) / BM : J.m_tiles_max;
+  int m_units = live_mc >= 0 ? (live_mc + BM - 1) / BM : J.m_tiles_max;
+  if (pair) m_units = (m_units + 1) / 2;
   const int band_tiles = group * J.n_tiles;
   const int band = lt / band_tiles;
   const int r = lt - band * band_tiles;
-  const int rows_in_band = min(group, m_tiles - band * group);
+  const int rows_in_band = min(group, m_units - band * group);
   R.m = band * group + r % rows_in_band;
   R.n = r / rows_in_band;
   R.k_blocks = (J.K + BK - 1) / BK;
-  R.live = R.m * BM < R.Mc;
+  R.live = (pair ? 2 * R.m : R.m) * BM < R.Mc;
   return R;
 }
 
-template <bool kSplit, int kStages, int kBN>
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+
+// kPair: launched in clusters of two CTAs that take the two m-tiles of a pair
+// with the same B tile; each CTA TMA-loads half of the B tile and multicasts
+// it into both CTAs' stage, and each MMA commit releases the stage in both
+// CTAs, so a stage is refilled only once both have consumed it.
+template <bool kSplit, int kStages, int kBN, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ table, int njobs,
                long long total_tiles, int group, int seg_kb) {
@@ -252,13 +286,20 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // A single job reads its surviving row count once and walks live tiles only.
   const int live_mc = grouped ? -1 : single.ctr[CTR_NSURV] * single.h;
-  if (!grouped) total_tiles = static_cast<long long>((live_mc + BM - 1) / BM) * single.n_tiles;
+  if (!grouped) {
+    int units = (live_mc + BM - 1) / BM;
+    if (kPair) units = (units + 1) / 2;
+    total_tiles = static_cast<long long>(units) * single.n_tiles;
+  }
+  const uint32_t rank = kPair ? cluster_rank() : 0u;
+  const int cid = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int nclusters = kPair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), kPair ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&sfull_bar[a]), 1);
@@ -276,6 +317,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   }
   fence_before();
   __syncthreads();
+  if (kPair) cluster_sync();  // the peer's barriers exist before any multicast lands
   fence_after();
   const uint32_t tmem_base = tmem_base_sh;
 
@@ -284,8 +326,8 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       int kb_all = 0;
       bool ok = true;
       const TcJob* fenced = nullptr;
-      for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc);
+      for (long long t = cid; t < total_tiles && ok; t += nclusters) {
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair);
         if (!T.live) continue;
         if (grouped && T.J != fenced) {
           tensormap_acquire(&T.J->map_ahi);
@@ -307,10 +349,19 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           const uint32_t base = smem_u32(smem + s * St::kBytes);
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, St::kBytes);
-          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, kb * BK, T.m * BM);
-          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, kb * BK, T.m * BM);
-          tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, kb * BK, T.n * kBN);
-          if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * BK, T.n * kBN);
+          const int m_cta = kPair ? 2 * T.m + static_cast<int>(rank) : T.m;
+          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, kb * BK, m_cta * BM);
+          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, kb * BK, m_cta * BM);
+          if (kPair) {
+            // this CTA's half of the B tile, into both CTAs of the pair
+            constexpr uint32_t kHalf = (kBN / 2) * BK * 2;
+            const int yb = T.n * kBN + static_cast<int>(rank) * (kBN / 2);
+            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, kb * BK, yb, 3);
+            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, kb * BK, yb, 3);
+          } else {
+            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, kb * BK, T.n * kBN);
+            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * BK, T.n * kBN);
+          }
         }
       }
       if (!ok || abort_flag) {
@@ -326,8 +377,8 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     if (lane == 0) {
       int kb_all = 0, g = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc);
+      for (long long t = cid; t < total_tiles && ok; t += nclusters) {
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair);
         if (!T.live) continue;
         const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
@@ -365,7 +416,10 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
                 umma_bf16<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
               }
             }
-            umma_commit(smem_u32(&empty_bar[s]));
+            if (kPair)
+              umma_commit_mc(smem_u32(&empty_bar[s]), 3);
+            else
+              umma_commit(smem_u32(&empty_bar[s]));
           }
           if (!ok) break;
           umma_commit(smem_u32(&sfull_bar[buf]));
@@ -380,8 +434,8 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     const int row = quarter * 32 + lane;
     int g = 0;
     bool ok = true;
-    for (long long t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-      const TileRef T = locate(jobs, njobs, t, group, live_mc);
+    for (long long t = cid; t < total_tiles && ok; t += nclusters) {
+      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair);
       if (!T.live) continue;
       const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
       float accum[kCols];
@@ -410,7 +464,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       }
       if (!ok) break;
       const TcJob& J = *T.J;
-      const int r = T.m * BM + row;
+      const int r = (kPair ? 2 * T.m + static_cast<int>(rank) : T.m) * BM + row;
       if (r < T.Mc) {
         const int ci = r / J.h;
         const int j = r - ci * J.h;
@@ -432,6 +486,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
 
   fence_before();
   __syncthreads();
+  if (kPair) cluster_sync();  // no CTA leaves while its peer may still write into it
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -744,40 +799,76 @@ bool make_map_u8(CUtensorMap* map, const void* base, long long rows, int K, int 
   return r == CUDA_SUCCESS;
 }
 
-// Tile configurations the autotuner chooses among (gemm_config % 10).
-int tile_bn(int config) { return (config % 10) == 2 ? 128 : 256; }
+// Tile configurations the autotuner chooses among (gemm_config % 10):
+// 1 = 128x256, 2 = 128x128, 3 = 128x256 paired (B multicast), 4 = 128x128 paired.
+int tile_bn(int config) {
+  const int t = config % 10;
+  return (t == 2 || t == 4) ? 128 : 256;
+}
+bool tile_pair(int config) { return (config % 10) >= 3; }
 
-template <bool kSplit, int kStages, int kBN>
+template <bool kSplit, int kStages, int kBN, bool kPair>
 cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, long long total_tiles,
                            int group, int seg_kb, cudaStream_t st) {
   const size_t smem = static_cast<size_t>(kStages) * Stage<kSplit, kBN>::kBytes + 1024;
-  auto kern = gemm_tc_kernel<kSplit, kStages, kBN>;
+  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  const int grid = static_cast<int>(std::min<long long>(total_tiles, num_sms()));
-  if (grid <= 0) return cudaSuccess;
-  kern<<<grid, kThreads, smem, st>>>(single, table, njobs, total_tiles, group, seg_kb);
-  return cudaGetLastError();
+  if (total_tiles <= 0) return cudaSuccess;
+  if (!kPair) {
+    const int grid = static_cast<int>(std::min<long long>(total_tiles, num_sms()));
+    kern<<<grid, kThreads, smem, st>>>(single, table, njobs, total_tiles, group, seg_kb);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // as many CTA pairs as can be resident at once (pairs must share a GPC)
+  cfg.gridDim = dim3(2 * (num_sms() / 2));
+  int resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) != cudaSuccess || resident <= 0) {
+    cudaGetLastError();
+    resident = num_sms() / 2;
+  }
+  const int clusters = static_cast<int>(std::min<long long>(total_tiles, resident));
+  cfg.gridDim = dim3(2 * clusters);
+  return cudaLaunchKernelEx(&cfg, kern, single, table, njobs, total_tiles, group, seg_kb);
 }
 
-cudaError_t dispatch(bool split3, int bn, const TcJob& single, const TcJob* table, int njobs,
+cudaError_t dispatch(bool split3, int bn, bool pair, const TcJob& single, const TcJob* table, int njobs,
                      long long total_tiles, int group, int seg_kb, cudaStream_t st) {
   if (split3) {
-    if (bn == 128) return launch_variant<true, 3, 128>(single, table, njobs, total_tiles, group, seg_kb, st);
-    return launch_variant<true, 2, 256>(single, table, njobs, total_tiles, group, seg_kb, st);
+    if (bn == 128)
+      return pair ? launch_variant<true, 3, 128, true>(single, table, njobs, total_tiles, group, seg_kb, st)
+                  : launch_variant<true, 3, 128, false>(single, table, njobs, total_tiles, group, seg_kb, st);
+    return pair ? launch_variant<true, 2, 256, true>(single, table, njobs, total_tiles, group, seg_kb, st)
+                : launch_variant<true, 2, 256, false>(single, table, njobs, total_tiles, group, seg_kb, st);
   }
-  if (bn == 128) return launch_variant<false, 6, 128>(single, table, njobs, total_tiles, group, seg_kb, st);
-  return launch_variant<false, 4, 256>(single, table, njobs, total_tiles, group, seg_kb, st);
+  if (bn == 128)
+    return pair ? launch_variant<false, 6, 128, true>(single, table, njobs, total_tiles, group, seg_kb, st)
+                : launch_variant<false, 6, 128, false>(single, table, njobs, total_tiles, group, seg_kb, st);
+  return pair ? launch_variant<false, 4, 256, true>(single, table, njobs, total_tiles, group, seg_kb, st)
+              : launch_variant<false, 4, 256, false>(single, table, njobs, total_tiles, group, seg_kb, st);
 }
 
-// gemm_config: 0 = defaults (BN 256, band 16, segment 4 k-blocks), else
-// band * 1000 + seg_kb * 10 + tile (tile 1 = 128x256, 2 = 128x128).
-void decode_config(int config, int* group, int* seg_kb, int* bn) {
+// gemm_config: 0 = defaults (128x256 tiles, band 16, segment 4 k-blocks),
+// else band * 1000 + seg_kb * 10 + tile (see tile_bn / tile_pair).
+void decode_config(int config, int* group, int* seg_kb, int* bn, bool* pair) {
   *group = 16;
   *seg_kb = 4;
   *bn = 256;
+  *pair = false;
   if (config > 0) {
     *bn = tile_bn(config);
+    *pair = tile_pair(config);
     if ((config / 10) % 100 > 0) *seg_kb = (config / 10) % 100;
     if (config / 1000 > 0) *group = config / 1000;
   }
@@ -788,13 +879,14 @@ void decode_config(int config, int* group, int* seg_kb, int* bn) {
 namespace {
 
 bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
-                 const void* b_lo, int num_cells, int N, int K, int h, int bn, float* products,
+                 const void* b_lo, int num_cells, int N, int K, int h, int bn, bool pair, float* products,
                  float* C_direct, int32_t* info_out) {
   memset(J, 0, sizeof *J);
   const long long rows = static_cast<long long>(num_cells) * h;
-  if (!make_map(&J->map_ahi, a_hi, rows, K, BM) || !make_map(&J->map_bhi, b_hi, N, K, bn)) return false;
+  const int box_b = pair ? bn / 2 : bn;  // a paired CTA loads half of the B tile
+  if (!make_map(&J->map_ahi, a_hi, rows, K, BM) || !make_map(&J->map_bhi, b_hi, N, K, box_b)) return false;
   if (a_lo) {
-    if (!make_map(&J->map_alo, a_lo, rows, K, BM) || !make_map(&J->map_blo, b_lo, N, K, bn)) return false;
+    if (!make_map(&J->map_alo, a_lo, rows, K, BM) || !make_map(&J->map_blo, b_lo, N, K, box_b)) return false;
   } else {
     J->map_alo = J->map_ahi;
     J->map_blo = J->map_bhi;
@@ -819,12 +911,14 @@ bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo,
 
 // Builds the device job table of a grouped GEMM for the given tile config:
 // jobs ordered by decreasing K (longest tiles first, so the static striding
-// of persistent CTAs over the tile space balances), tile_base prefix sums.
-// Copies the table to d_table (n * tc_job_bytes() bytes) and synchronises.
+// of persistent CTAs over the tile space balances), tile_base prefix sums
+// (in tiles, or in tile pairs for paired configs).  Copies the table to
+// d_table (n * tc_job_bytes() bytes) and synchronises.
 cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
                            long long* total_tiles, cudaStream_t st) {
   int group, seg_kb, bn;
-  decode_config(config, &group, &seg_kb, &bn);
+  bool pair;
+  decode_config(config, &group, &seg_kb, &bn, &pair);
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return specs[a].K > specs[b].K; });
@@ -833,10 +927,11 @@ cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, 
   for (int r = 0; r < n; ++r) {
     const TcSpec& S = specs[idx[r]];
     if (!tc_fill_job(&tab[r], S.p, S.a_hi, split3 ? S.a_lo : nullptr, S.b_hi, split3 ? S.b_lo : nullptr,
-                     S.num_cells, S.N, S.K, S.h, bn, S.products, S.C_direct, S.info_out))
+                     S.num_cells, S.N, S.K, S.h, bn, pair, S.products, S.C_direct, S.info_out))
       return cudaErrorInvalidValue;
     tab[r].tile_base = base;
-    base += static_cast<long long>(tab[r].m_tiles_max) * tab[r].n_tiles;
+    const int units = pair ? (tab[r].m_tiles_max + 1) / 2 : tab[r].m_tiles_max;
+    base += static_cast<long long>(units) * tab[r].n_tiles;
   }
   *total_tiles = base;
   cudaError_t e = cudaMemcpyAsync(d_table, tab.data(), sizeof(TcJob) * n, cudaMemcpyHostToDevice, st);
@@ -852,23 +947,26 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
                            int32_t* info_out, cudaStream_t st) {
   (void)g;
   int group, seg_kb, bn;
-  decode_config(config, &group, &seg_kb, &bn);
+  bool pair;
+  decode_config(config, &group, &seg_kb, &bn, &pair);
   TcJob J;
   if (!tc_fill_job(&J, p, a_hi, split3 ? a_lo : nullptr, b_hi, split3 ? b_lo : nullptr, num_cells, N, K, h,
-                   bn, products, C_direct, info_out))
+                   bn, pair, products, C_direct, info_out))
     return cudaErrorInvalidValue;
-  const long long tiles = static_cast<long long>(J.m_tiles_max) * J.n_tiles;
-  return dispatch(split3, bn, J, nullptr, 1, tiles, group, seg_kb, st);
+  const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
+  const long long tiles = static_cast<long long>(units) * J.n_tiles;
+  return dispatch(split3, bn, pair, J, nullptr, 1, tiles, group, seg_kb, st);
 }
 
 // Grouped launch over a device table of jobs (tile_base set, maps encoded).
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st) {
   int group, seg_kb, bn;
-  decode_config(config, &group, &seg_kb, &bn);
+  bool pair;
+  decode_config(config, &group, &seg_kb, &bn, &pair);
   TcJob dummy;
   memset(&dummy, 0, sizeof dummy);
-  return dispatch(split3, bn, dummy, static_cast<const TcJob*>(d_jobs), njobs, total_tiles, group, seg_kb, st);
+  return dispatch(split3, bn, pair, dummy, static_cast<const TcJob*>(d_jobs), njobs, total_tiles, group, seg_kb, st);
 }
 
 }  // namespace bpx

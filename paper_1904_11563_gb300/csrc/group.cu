@@ -45,7 +45,8 @@ void mark(const bpx_opts* o, int stage, int end, cudaStream_t st) {
   if (ev) cudaEventRecord(static_cast<cudaEvent_t>(ev), st);
 }
 
-int tile_of(int config) { return (config % 10) == 2 ? 128 : 256; }
+// The device GEMM table depends on the tile shape and pairing (gemm_config % 10).
+int tile_of(int config) { return (config % 10) == 0 ? 1 : config % 10; }
 
 // (Re)builds the device GEMM table when the tile width changes.
 int ensure_table(bpx_group* G, int config, cudaStream_t st) {
@@ -203,7 +204,7 @@ extern "C" int bpx_grouped_run(bpx_group* G, const bpx_opts* opts, bpx_stream st
   if (!G || !G->ws) return fail(BPX_ERR_INVAL, "bpx_grouped_run: group not initialised");
   const int config = (opts && opts->gemm_config) ? opts->gemm_config : G->tuned_config;
   if (tile_of(config) != tile_of(G->table_config))
-    return fail(BPX_ERR_INVAL, "bpx_grouped_run: tile width %d differs from the planned one; "
+    return fail(BPX_ERR_INVAL, "bpx_grouped_run: tile shape %d differs from the planned one; "
                 "call bpx_group_autotune or bpx_group_set_config first", tile_of(config));
   return run_group(G, opts, config, S(stream));
 }
@@ -247,7 +248,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
 
 namespace {
 
-const int kDefaultConfigs[] = {16041, 8041, 32041, 16021, 16081, 16042, 8042, 32042, 16022, 16082};
+const int kDefaultConfigs[] = {16041, 8041, 32041, 16021, 16043, 8043, 32043, 16023, 16042, 16044};
 
 // Times `launch` on each config (one warm-up, then the best of three) and
 // returns the fastest.

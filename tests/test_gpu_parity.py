@@ -306,8 +306,9 @@ def test_host_entry_point_matches_device(libbpx):
     assert np.array_equal(hC.numpy(), C_dev[:M])
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32"])
-def test_many_tiles_per_cta(libbpx, prec):
+@pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16043), ("bf16x3", 8044),
+                                      ("bf16", 16043), ("bf16x3", 16022)])
+def test_many_tiles_per_cta(libbpx, prec, cfg):
     """Bench-shaped code and block height at reduced N, K: ~600 output tiles
     of 128 x 256, so every persistent CTA runs several tiles and both TMEM
     accumulators and every barrier phase are exercised."""
@@ -317,7 +318,7 @@ def test_many_tiles_per_cta(libbpx, prec):
     A, B = W.inputs(M, K, N, "normal", 81)
     for t in range(2):
         m = W.erasure_mask(11, 3, 2000 + t)
-        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=bpx.default_opts(gemm_config=cfg))
         assert info[bpx.INFO_STATUS] == bpx.OK
         R, sch = _oracle_decode(ref, A, B, h, m)
         _check_blocks(C, R, ref, A, B, h, m, prec)
