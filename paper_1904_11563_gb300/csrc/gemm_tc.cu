@@ -40,7 +40,7 @@ namespace bpx {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;  // bf16 elements = 128 bytes per row: one 128B swizzle atom row
+constexpr int BK = 64;  // default k-slice: 64 bf16 = 128 bytes per row, one 128B swizzle row
 constexpr int kThreads = 320;  // producer, MMA, 8 epilogue warps
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (~2 s) per wait
 
@@ -100,6 +100,23 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   d |= static_cast<uint64_t>(1) << 46;                // descriptor version (tcgen05)
   d |= static_cast<uint64_t>(2) << 61;                // 128-byte swizzle
   return d;
+}
+
+// K-major operand with 64-byte rows (32 bf16) in the 64-byte swizzled layout
+// (8-row x 64 B atoms, 512 B between 8-row groups).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;  // 64-byte swizzle
+  return d;
+}
+
+template <int kBK>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t addr) {
+  return kBK == 64 ? sdesc_sw128(addr) : sdesc_sw64(addr);
 }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
@@ -174,10 +191,10 @@ struct __align__(64) TcJob {
   long long tile_base;    // first tile of this job in the launch's tile space
 };
 
-template <bool kSplit, int kBN>
+template <bool kSplit, int kBN, int kBK = BK>
 struct Stage {
-  static constexpr uint32_t kA = BM * BK * 2;   // 16 KB
-  static constexpr uint32_t kB = kBN * BK * 2;  // 32 or 16 KB
+  static constexpr uint32_t kA = BM * kBK * 2;   // 16 or 8 KB
+  static constexpr uint32_t kB = kBN * kBK * 2;  // 32, 16 or 8 KB
   static constexpr uint32_t kBytes = kSplit ? 2 * (kA + kB) : (kA + kB);
   static constexpr uint32_t kAhi = 0;
   static constexpr uint32_t kAlo = kA;
@@ -212,7 +229,7 @@ struct TileRef {
 // adjacent m-tiles (two CTAs of a cluster share the B tile); m is then the
 // pair index and `live` tells whether the pair covers surviving rows.
 __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc,
-                                          bool pair) {
+                                          bool pair, int bk) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {  // last job with tile_base <= t
     const int mid = (lo + hi + 1) >> 1;
@@ -232,7 +249,7 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   const int rows_in_band = min(group, m_units - band * group);
   R.m = band * group + r % rows_in_band;
   R.n = r / rows_in_band;
-  R.k_blocks = (J.K + BK - 1) / BK;
+  R.k_blocks = (J.K + bk - 1) / bk;
   R.live = (pair ? 2 * R.m : R.m) * BM < R.Mc;
   return R;
 }
@@ -267,11 +284,11 @@ __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
 // with the same B tile; each CTA TMA-loads half of the B tile and multicasts
 // it into both CTAs' stage, and each MMA commit releases the stage in both
 // CTAs, so a stage is refilled only once both have consumed it.
-template <bool kSplit, int kStages, int kBN, bool kPair>
+template <bool kSplit, int kStages, int kBN, bool kPair, int kBK>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ table, int njobs,
                long long total_tiles, int group, int seg_kb) {
-  using St = Stage<kSplit, kBN>;
+  using St = Stage<kSplit, kBN, kBK>;
   constexpr int kTmemCols = 2 * kBN;  // two FP32 segment accumulators
   constexpr int kCols = kBN / 2;      // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
@@ -327,7 +344,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       bool ok = true;
       const TcJob* fenced = nullptr;
       for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK);
         if (!T.live) continue;
         if (grouped && T.J != fenced) {
           tensormap_acquire(&T.J->map_ahi);
@@ -350,17 +367,17 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, St::kBytes);
           const int m_cta = kPair ? 2 * T.m + static_cast<int>(rank) : T.m;
-          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, kb * BK, m_cta * BM);
-          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, kb * BK, m_cta * BM);
+          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, kb * kBK, m_cta * BM);
+          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, kb * kBK, m_cta * BM);
           if (kPair) {
             // this CTA's half of the B tile, into both CTAs of the pair
-            constexpr uint32_t kHalf = (kBN / 2) * BK * 2;
+            constexpr uint32_t kHalf = (kBN / 2) * kBK * 2;
             const int yb = T.n * kBN + static_cast<int>(rank) * (kBN / 2);
-            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, kb * BK, yb, 3);
-            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, kb * BK, yb, 3);
+            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, kb * kBK, yb, 3);
+            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, kb * kBK, yb, 3);
           } else {
-            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, kb * BK, T.n * kBN);
-            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * BK, T.n * kBN);
+            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, kb * kBK, T.n * kBN);
+            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * kBK, T.n * kBN);
           }
         }
       }
@@ -378,7 +395,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       int kb_all = 0, g = 0;
       bool ok = true;
       for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK);
         if (!T.live) continue;
         const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
@@ -402,12 +419,12 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
             }
             fence_after();
             const uint32_t base = smem_u32(smem + s * St::kBytes);
-            const uint64_t ahi = sdesc_sw128(base + St::kAhi);
-            const uint64_t bhi = sdesc_sw128(base + St::kBhi);
-            const uint64_t alo = sdesc_sw128(base + St::kAlo);
-            const uint64_t blo = sdesc_sw128(base + St::kBlo);
+            const uint64_t ahi = sdesc_k<kBK>(base + St::kAhi);
+            const uint64_t bhi = sdesc_k<kBK>(base + St::kBhi);
+            const uint64_t alo = sdesc_k<kBK>(base + St::kAlo);
+            const uint64_t blo = sdesc_k<kBK>(base + St::kBlo);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
+            for (int kk = 0; kk < kBK / 16; ++kk) {
               const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
               umma_bf16<kBN>(d_tmem, ahi + adv, bhi + adv, first);
@@ -435,7 +452,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     int g = 0;
     bool ok = true;
     for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair);
+      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK);
       if (!T.live) continue;
       const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
       float accum[kCols];
@@ -770,16 +787,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-// 2-D K-major bf16 tensor map: rows x K, box = box_rows x 64 with 128 B swizzle.
-bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box_rows) {
+// 2-D K-major bf16 tensor map: rows x K, box = box_rows x bk (bk = 64: 128 B
+// swizzle; bk = 32: 64 B swizzle), matching the UMMA descriptors.
+bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box_rows, int bk = BK) {
   auto enc = get_encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * 2};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -800,18 +819,28 @@ bool make_map_u8(CUtensorMap* map, const void* base, long long rows, int K, int 
 }
 
 // Tile configurations the autotuner chooses among (gemm_config % 10):
-// 1 = 128x256, 2 = 128x128, 3 = 128x256 paired (B multicast), 4 = 128x128 paired.
+// 1 = 128x256, 2 = 128x128, 3 = 128x256 paired (B multicast), 4 = 128x128
+// paired; 5..8 = the same with 32-wide k-slices (64-byte swizzle, twice the
+// stages of half the size).
 int tile_bn(int config) {
   const int t = config % 10;
-  return (t == 2 || t == 4) ? 128 : 256;
+  return (t == 2 || t == 4 || t == 6 || t == 8) ? 128 : 256;
 }
-bool tile_pair(int config) { return (config % 10) >= 3; }
+bool tile_pair(int config) {
+  const int t = config % 10;
+  return t == 3 || t == 4 || t == 7 || t == 8;
+}
+int tile_bk(int config) { return (config % 10) >= 5 ? 32 : 64; }
 
-template <bool kSplit, int kStages, int kBN, bool kPair>
+template <bool kSplit, int kStages, int kBN, bool kPair, int kBK>
 cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, long long total_tiles,
                            int group, int seg_kb, cudaStream_t st) {
-  const size_t smem = static_cast<size_t>(kStages) * Stage<kSplit, kBN>::kBytes + 1024;
-  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair>;
+  // 32-wide slices: 32 KB of slack after the stages, so that the descriptors
+  // of the 64-byte swizzled layout can never reach past the allocation.
+  const size_t smem =
+      static_cast<size_t>(kStages) * Stage<kSplit, kBN, kBK>::kBytes + 1024 + (kBK == 32 ? 32768 : 0);
+  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair, kBK>;
+  seg_kb *= BK / kBK;  // segments are counted in 64-wide k-blocks
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (total_tiles <= 0) return cudaSuccess;
@@ -843,32 +872,42 @@ cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, l
   return cudaLaunchKernelEx(&cfg, kern, single, table, njobs, total_tiles, group, seg_kb);
 }
 
-cudaError_t dispatch(bool split3, int bn, bool pair, const TcJob& single, const TcJob* table, int njobs,
-                     long long total_tiles, int group, int seg_kb, cudaStream_t st) {
+template <int kBK>
+cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, const TcJob* table, int njobs,
+                        long long total_tiles, int group, int seg_kb, cudaStream_t st) {
+  constexpr int m = BK / kBK;  // stages scale up as slices shrink
   if (split3) {
     if (bn == 128)
-      return pair ? launch_variant<true, 3, 128, true>(single, table, njobs, total_tiles, group, seg_kb, st)
-                  : launch_variant<true, 3, 128, false>(single, table, njobs, total_tiles, group, seg_kb, st);
-    return pair ? launch_variant<true, 2, 256, true>(single, table, njobs, total_tiles, group, seg_kb, st)
-                : launch_variant<true, 2, 256, false>(single, table, njobs, total_tiles, group, seg_kb, st);
+      return pair ? launch_variant<true, 3 * m, 128, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
+                  : launch_variant<true, 3 * m, 128, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
+    return pair ? launch_variant<true, 2 * m, 256, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
+                : launch_variant<true, 2 * m, 256, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
   }
   if (bn == 128)
-    return pair ? launch_variant<false, 6, 128, true>(single, table, njobs, total_tiles, group, seg_kb, st)
-                : launch_variant<false, 6, 128, false>(single, table, njobs, total_tiles, group, seg_kb, st);
-  return pair ? launch_variant<false, 4, 256, true>(single, table, njobs, total_tiles, group, seg_kb, st)
-              : launch_variant<false, 4, 256, false>(single, table, njobs, total_tiles, group, seg_kb, st);
+    return pair ? launch_variant<false, 6 * m, 128, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
+                : launch_variant<false, 6 * m, 128, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
+  return pair ? launch_variant<false, 4 * m, 256, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
+              : launch_variant<false, 4 * m, 256, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
+}
+
+cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single, const TcJob* table, int njobs,
+                     long long total_tiles, int group, int seg_kb, cudaStream_t st) {
+  if (bk == 32) return dispatch_bk<32>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
+  return dispatch_bk<64>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
 }
 
 // gemm_config: 0 = defaults (128x256 tiles, band 16, segment 4 k-blocks),
 // else band * 1000 + seg_kb * 10 + tile (see tile_bn / tile_pair).
-void decode_config(int config, int* group, int* seg_kb, int* bn, bool* pair) {
+void decode_config(int config, int* group, int* seg_kb, int* bn, bool* pair, int* bk) {
   *group = 16;
   *seg_kb = 4;
   *bn = 256;
   *pair = false;
+  *bk = BK;
   if (config > 0) {
     *bn = tile_bn(config);
     *pair = tile_pair(config);
+    *bk = tile_bk(config);
     if ((config / 10) % 100 > 0) *seg_kb = (config / 10) % 100;
     if (config / 1000 > 0) *group = config / 1000;
   }
@@ -879,14 +918,16 @@ void decode_config(int config, int* group, int* seg_kb, int* bn, bool* pair) {
 namespace {
 
 bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
-                 const void* b_lo, int num_cells, int N, int K, int h, int bn, bool pair, float* products,
-                 float* C_direct, int32_t* info_out) {
+                 const void* b_lo, int num_cells, int N, int K, int h, int bn, bool pair, int bk,
+                 float* products, float* C_direct, int32_t* info_out) {
   memset(J, 0, sizeof *J);
   const long long rows = static_cast<long long>(num_cells) * h;
   const int box_b = pair ? bn / 2 : bn;  // a paired CTA loads half of the B tile
-  if (!make_map(&J->map_ahi, a_hi, rows, K, BM) || !make_map(&J->map_bhi, b_hi, N, K, box_b)) return false;
+  if (!make_map(&J->map_ahi, a_hi, rows, K, BM, bk) || !make_map(&J->map_bhi, b_hi, N, K, box_b, bk))
+    return false;
   if (a_lo) {
-    if (!make_map(&J->map_alo, a_lo, rows, K, BM) || !make_map(&J->map_blo, b_lo, N, K, box_b)) return false;
+    if (!make_map(&J->map_alo, a_lo, rows, K, BM, bk) || !make_map(&J->map_blo, b_lo, N, K, box_b, bk))
+      return false;
   } else {
     J->map_alo = J->map_ahi;
     J->map_blo = J->map_bhi;
@@ -916,9 +957,9 @@ bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo,
 // d_table (n * tc_job_bytes() bytes) and synchronises.
 cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
                            long long* total_tiles, cudaStream_t st) {
-  int group, seg_kb, bn;
+  int group, seg_kb, bn, bk;
   bool pair;
-  decode_config(config, &group, &seg_kb, &bn, &pair);
+  decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return specs[a].K > specs[b].K; });
@@ -927,7 +968,7 @@ cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, 
   for (int r = 0; r < n; ++r) {
     const TcSpec& S = specs[idx[r]];
     if (!tc_fill_job(&tab[r], S.p, S.a_hi, split3 ? S.a_lo : nullptr, S.b_hi, split3 ? S.b_lo : nullptr,
-                     S.num_cells, S.N, S.K, S.h, bn, pair, S.products, S.C_direct, S.info_out))
+                     S.num_cells, S.N, S.K, S.h, bn, pair, bk, S.products, S.C_direct, S.info_out))
       return cudaErrorInvalidValue;
     tab[r].tile_base = base;
     const int units = pair ? (tab[r].m_tiles_max + 1) / 2 : tab[r].m_tiles_max;
@@ -946,27 +987,28 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
                            bool split3, float* products, float* C_direct, int config,
                            int32_t* info_out, cudaStream_t st) {
   (void)g;
-  int group, seg_kb, bn;
+  int group, seg_kb, bn, bk;
   bool pair;
-  decode_config(config, &group, &seg_kb, &bn, &pair);
+  decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   TcJob J;
   if (!tc_fill_job(&J, p, a_hi, split3 ? a_lo : nullptr, b_hi, split3 ? b_lo : nullptr, num_cells, N, K, h,
-                   bn, pair, products, C_direct, info_out))
+                   bn, pair, bk, products, C_direct, info_out))
     return cudaErrorInvalidValue;
   const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
   const long long tiles = static_cast<long long>(units) * J.n_tiles;
-  return dispatch(split3, bn, pair, J, nullptr, 1, tiles, group, seg_kb, st);
+  return dispatch(split3, bn, pair, bk, J, nullptr, 1, tiles, group, seg_kb, st);
 }
 
 // Grouped launch over a device table of jobs (tile_base set, maps encoded).
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st) {
-  int group, seg_kb, bn;
+  int group, seg_kb, bn, bk;
   bool pair;
-  decode_config(config, &group, &seg_kb, &bn, &pair);
+  decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   TcJob dummy;
   memset(&dummy, 0, sizeof dummy);
-  return dispatch(split3, bn, pair, dummy, static_cast<const TcJob*>(d_jobs), njobs, total_tiles, group, seg_kb, st);
+  return dispatch(split3, bn, pair, bk, dummy, static_cast<const TcJob*>(d_jobs), njobs, total_tiles, group, seg_kb,
+                  st);
 }
 
 }  // namespace bpx

@@ -248,7 +248,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
 
 namespace {
 
-const int kDefaultConfigs[] = {16041, 8041, 32041, 16021, 16043, 8043, 32043, 16023, 16042, 16044};
+const int kDefaultConfigs[] = {16041, 8041, 16043, 8043, 16045, 8045, 16047, 8047, 16042, 16044, 16046, 16048};
 
 // Times `launch` on each config (one warm-up, then the best of three) and
 // returns the fastest.

@@ -118,7 +118,7 @@ def test_autotune_replans_and_stays_exact(libbpx):
     torch.cuda.synchronize()
     _check_exact(bpx, jobs, refs)
     # every other tile shape, re-planned, stays exact
-    for cfg in (16041, 16042, 16043, 16044):
+    for cfg in (16041, 16042, 16043, 16044, 16045, 16048):
         G.set_config(cfg)
         for j in jobs:
             j["C"].zero_()

@@ -307,7 +307,8 @@ def test_host_entry_point_matches_device(libbpx):
 
 
 @pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16043), ("bf16x3", 8044),
-                                      ("bf16", 16043), ("bf16x3", 16022)])
+                                      ("bf16", 16043), ("bf16x3", 16022), ("bf16x3", 16045), ("bf16x3", 8047),
+                                      ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8048)])
 def test_many_tiles_per_cta(libbpx, prec, cfg):
     """Bench-shaped code and block height at reduced N, K: ~600 output tiles
     of 128 x 256, so every persistent CTA runs several tiles and both TMEM
