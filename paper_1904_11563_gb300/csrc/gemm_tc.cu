@@ -896,15 +896,18 @@ cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single
   return dispatch_bk<64>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
 }
 
-// gemm_config: 0 = defaults (128x256 tiles, band 16, segment 4 k-blocks),
-// else band * 1000 + seg_kb * 10 + tile (see tile_bn / tile_pair).
+// gemm_config: 0 = defaults (the fastest measured on the benchmark: 128x256
+// tiles in CTA pairs, 32-wide k-slices, band 8, 512-wide K segments), else
+// band * 1000 + seg_kb * 10 + tile (see tile_bn / tile_pair / tile_bk).
 void decode_config(int config, int* group, int* seg_kb, int* bn, bool* pair, int* bk) {
-  *group = 16;
-  *seg_kb = 4;
+  *group = 8;
+  *seg_kb = 8;
   *bn = 256;
-  *pair = false;
-  *bk = BK;
+  *pair = true;
+  *bk = 32;
   if (config > 0) {
+    *group = 16;
+    *seg_kb = 4;
     *bn = tile_bn(config);
     *pair = tile_pair(config);
     *bk = tile_bk(config);

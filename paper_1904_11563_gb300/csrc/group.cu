@@ -46,7 +46,7 @@ void mark(const bpx_opts* o, int stage, int end, cudaStream_t st) {
 }
 
 // The device GEMM table depends on the tile shape and pairing (gemm_config % 10).
-int tile_of(int config) { return (config % 10) == 0 ? 1 : config % 10; }
+int tile_of(int config) { return (config % 10) == 0 ? 7 : config % 10; }
 
 // (Re)builds the device GEMM table when the tile width changes.
 int ensure_table(bpx_group* G, int config, cudaStream_t st) {
@@ -248,7 +248,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
 
 namespace {
 
-const int kDefaultConfigs[] = {16041, 8041, 16043, 8043, 16045, 8045, 16047, 8047, 16042, 16044, 16046, 16048};
+const int kDefaultConfigs[] = {8087, 16087, 4087, 8085, 16085, 8047, 8045, 16041, 8086, 8088, 8046, 16042};
 
 // Times `launch` on each config (one warm-up, then the best of three) and
 // returns the fastest.
