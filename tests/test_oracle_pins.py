@@ -534,3 +534,161 @@ def test_propagation_factors():
             err = np.linalg.norm(Cn[s] - Cd[s]) / np.linalg.norm(Cd[s])
             ratios.append(err / (eps * nu[s]))
     assert 0.7 < np.mean(ratios) < 1.3
+
+
+# ---------------------------------------------------------------- exact-slice products
+
+def _exact_bound(A, B, h, sigma):
+    """Elementwise bound on |C_exact - A B| for the exact-slice path from the
+    representation alone: rounding A and B to the fixed-point grid
+    (half a unit each), the dropped digit pairs i + l >= S (each digit at
+    most 2^(w-1)), and the final rounding to FP32."""
+    w, S, bits = o.exact_slice_params(sigma)
+    eA = o.exact_row_exponents(A, h).astype(float)
+    eB = o.exact_col_exponents(B).astype(float)
+    K = A.shape[1]
+    M = A.shape[0]
+    ea = eA[np.arange(M) % h][:, None]
+    eb = eB[None, :]
+    quant = K * (2.0 ** (ea - bits - 1) * 2.0 ** eb + 2.0 ** ea * (1 + 2.0 ** -bits) * 2.0 ** (eb - bits - 1))
+    trunc_q = K * sum((2 * S - 1 - d) * 2.0 ** (w * (2 * S - 2 - d)) * 2.0 ** (2 * (w - 1))
+                      for d in range(S, 2 * S - 1))
+    trunc = trunc_q * 2.0 ** (ea + eb - 2 * bits)
+    ref = A.astype(np.float64) @ B.astype(np.float64)
+    return quant + trunc + 2.0 ** -24 * (np.abs(ref) + quant + trunc), ref
+
+
+def test_exact_digits_recompose_and_stay_small():
+    """x = sum_i 2^(w (S-1-i)) D_i exactly, |D_i| <= 2^(w-1), for every
+    digit width the codes use, on random and extreme fixed-point values."""
+    rng = np.random.default_rng(5)
+    for sigma in (1, 2, 3, 5, 8, 12, 24, 40, 64):
+        w, S, bits = o.exact_slice_params(sigma)
+        assert sigma * 2 ** (w - 1) <= 256 and S * w >= bits + 1 and bits >= 23
+        x = rng.integers(-(2 ** bits), 2 ** bits + 1, size=4000, dtype=np.int64)
+        x[:4] = [2 ** bits, -(2 ** bits), 0, 2 ** bits - 1]
+        D = o.balanced_digits(x, w, S)
+        back = sum(D[i] << (w * (S - 1 - i)) for i in range(S))
+        assert np.array_equal(back, x)
+        for d in D:
+            assert np.abs(d).max() <= 2 ** (w - 1)
+
+
+def test_fixed_point_exponents_frexp_convention():
+    A = np.array([[0.75, -3.0], [0.0, 0.0], [1.0, 0.5]], dtype=np.float32)
+    assert list(o.exact_row_exponents(A, 3)) == [2, 0, 1]   # 3 < 2^2, 0 -> 0, 1 < 2^1
+    assert list(o.exact_col_exponents(A)) == [1, 2]
+
+
+@pytest.mark.parametrize("maker,h", [(o.table1, 4), (o.table3, 3),
+                                     (lambda: o.systematic_mojette(4, 2, 3), 2),
+                                     (lambda: o.construction_a(6, 4, 4), 1)])
+def test_exact_slice_small_integers_give_the_exact_product(maker, h):
+    """Small-integer inputs sit on the fixed-point grid with one nonzero
+    digit, so the exact-slice path must return A B exactly (integer matmul),
+    for every decodable erasure pattern."""
+    code = maker()
+    rng = np.random.default_rng(7)
+    M, K, N = code.num_sources * h - 1, 24, 8
+    A, B = _int_inputs(rng, M, K, N)
+    exact = A.astype(np.int64) @ B.astype(np.int64)
+    for er in o.all_erasure_patterns(code.n, code.n - code.k):
+        if not o.decodable(code, er):
+            continue
+        C, _Q, sched = o.exact_slice_coded_matmul(code, A, B, h, er)
+        assert sched.ok
+        assert np.array_equal(C[:M], exact.astype(np.float32))
+
+
+@pytest.mark.parametrize("maker,h,dist", [(o.table1, 16, "normal"), (o.table3, 8, "loguniform"),
+                                          (lambda: o.systematic_mojette(4, 3, 4), 4, "uniform"),
+                                          (lambda: o.construction_a(7, 4, 5), 2, "normal")])
+def test_exact_slice_is_mask_and_depth_independent(maker, h, dist):
+    """Every decodable pattern yields bit-identical C and identical exact
+    integers Q_s, equal to the exact-slice product of the source computed
+    directly without the code: the coded digit planes are linear in the
+    sources and the peel is exact, so nothing depends on the resolver or the
+    peel depth.  Also within the representation's error bound of A B."""
+    code = maker()
+    rng = np.random.default_rng(11)
+    M, K, N = code.num_sources * h, 40, 12
+    if dist == "normal":
+        A = rng.standard_normal((M, K)).astype(np.float32)
+        B = rng.standard_normal((K, N)).astype(np.float32)
+    elif dist == "uniform":
+        A = rng.uniform(-1, 1, (M, K)).astype(np.float32)
+        B = rng.uniform(-1, 1, (K, N)).astype(np.float32)
+    else:
+        A = (rng.choice([-1.0, 1.0], (M, K)) * 10.0 ** rng.uniform(-3, 3, (M, K))).astype(np.float32)
+        B = (rng.choice([-1.0, 1.0], (K, N)) * 10.0 ** rng.uniform(-3, 3, (K, N))).astype(np.float32)
+    direct = {}
+    for s in range(code.num_sources):
+        blk, q = o.exact_slice_block(A, B, s, h, code.sigma)
+        direct[s] = (blk, q)
+    bound, ref = _exact_bound(A, B, h, code.sigma)
+    depths = set()
+    patterns = list(o.all_erasure_patterns(code.n, code.n - code.k))
+    for er in patterns[:: max(1, len(patterns) // 25)]:
+        if not o.decodable(code, er):
+            continue
+        C, Q, sched = o.exact_slice_coded_matmul(code, A, B, h, er)
+        depths.update(d for _s, _r, d in sched.order)
+        for s in range(code.num_sources):
+            assert np.array_equal(Q[s], direct[s][1])
+            assert np.array_equal(C[s * h:(s + 1) * h], direct[s][0])
+        assert np.all(np.abs(C.astype(np.float64) - ref) <= bound)
+    assert max(depths) >= 2
+
+
+def test_exact_slice_error_tracks_fp32_scale():
+    """On N(0,1) data the exact-slice result is as close to A B as an FP32
+    product (relative to max |A B|, below 1e-6) -- and no deeper source is
+    worse than a direct one."""
+    code = o.systematic_mojette(8, 3, 8)
+    h = 4
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((code.num_sources * h, 256)).astype(np.float32)
+    B = rng.standard_normal((256, 16)).astype(np.float32)
+    C, _Q, sched = o.exact_slice_coded_matmul(code, A, B, h, (0, 3, 9))
+    ref = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.abs(C - ref).max() / np.abs(ref).max() < 1e-6
+    assert max(d for _s, _r, d in sched.order) >= 3
+
+
+def test_exact_slice_planted_mistakes_are_caught(monkeypatch):
+    """Dropping the last kept diagonal, or forming coded digit planes with
+    carries (digits of the coded sum instead of the sum of digits), must
+    fail the bound or the mask-independence pin."""
+    code = o.table1()
+    h = 8
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((code.num_sources * h, 64)).astype(np.float32)
+    B = rng.standard_normal((64, 8)).astype(np.float32)
+    bound, ref = _exact_bound(A, B, h, code.sigma)
+    good_q = o.exact_q
+
+    def drop_last(Ad, Bd, w, S):
+        q = np.zeros((Ad[0].shape[0], Bd[0].shape[1]), dtype=np.int64)
+        for d in range(S - 1):
+            q += sum(Ad[i] @ Bd[d - i] for i in range(d + 1)) << (w * (S - 1 - d))
+        return q
+
+    monkeypatch.setattr(o, "exact_q", drop_last)
+    C, _Q, _ = o.exact_slice_coded_matmul(code, A, B, h, (0, 1))
+    assert not np.all(np.abs(C.astype(np.float64) - ref) <= bound)
+    monkeypatch.setattr(o, "exact_q", good_q)
+
+    w, S, bits = o.exact_slice_params(code.sigma)
+    eA = o.exact_row_exponents(A, h)
+    eB = o.exact_col_exponents(B)
+    Bd = o.balanced_digits(o.fixed_point(B, eB[None, :], bits), w, S)
+    sched = o.wave_schedule(code, o.surviving_cells(code, (0, 1)))
+    Qc = {}
+    for c in set(r for _s, r, _d in sched.order):
+        tot = sum(o.fixed_point(o.row_block(A, s, h), eA[:, None], bits) for s in code.cells[c])
+        Qc[c] = o.exact_q(o.balanced_digits(tot, w, S), Bd, w, S)   # carries: wrong
+    CQ = {}
+    for s, r, _d in sched.order:
+        CQ[s] = Qc[r] - sum((CQ[t] for t in code.cells[r] if t != s), np.zeros_like(Qc[r]))
+    direct = {s: o.exact_slice_block(A, B, s, h, code.sigma)[1] for s in range(code.num_sources)}
+    assert any(not np.array_equal(CQ[s], direct[s]) for s in CQ)
