@@ -68,7 +68,7 @@ def _parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "mxfp8", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "mxfp8", "fp32", "exact"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gemm-config", type=int, default=0,
@@ -278,7 +278,7 @@ def run_ours(args, wl):
     if args.precisions:
         precs = [x for x in args.precisions.split(",") if x]
     elif args.precision == "auto":
-        precs = ["bf16x3", "fp32", "mxfp8"]
+        precs = ["bf16x3", "fp32", "mxfp8", "exact"]
     else:
         precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
     results = {}
@@ -304,7 +304,7 @@ def run_ours(args, wl):
         C = bpx.alloc_C(code, h, N, dev)
         info = torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device=dev)
         cfg = args.gemm_config
-        if cfg == 0 and prec in ("bf16x3", "bf16"):
+        if cfg == 0 and prec in ("bf16x3", "bf16", "exact"):
             cfg, _tuned_ms = bpx.autotune(code, A, Bm, h, P, masks[0], ws, C=C)
         tuned[prec] = cfg
         opts = bpx.default_opts(gemm_config=cfg)
@@ -453,7 +453,11 @@ def run_ours(args, wl):
             pk, unit = sms * 128 * 2 * mhz * 1e6 / 1e12, "FFMA"
             work = 2.0 * rows_m * N * K
         else:
-            mult = {"bf16x3": 3, "bf16": 1, "mxfp8": 1}[prec]
+            if prec == "exact":
+                S_ex = bpx.exact_params(code, K)["S"]
+                mult = S_ex * (S_ex + 1) // 2     # digit pairs (i, l) with i + l < S
+            else:
+                mult = {"bf16x3": 3, "bf16": 1, "mxfp8": 1}[prec]
             pk = peaks.get("bf16_tflops", 1900.0) * (2.0 if prec == "mxfp8" else 1.0)
             unit = "measured bf16 burst" + (" x 2 (nominal fp8/bf16)" if prec == "mxfp8" else "")
             work = 2.0 * rows_m * N * K * mult
@@ -467,7 +471,7 @@ def run_ours(args, wl):
                       "frac_hbm": (peel_b / (peel_ms * 1e-3) / 1e9) / hbm if peel_ms > 0 else None,
                       "bytes_def": "sum over non-direct sources of (deg(resolver)+1) h N 4"}
     line["clocks"] = R["clocks"]
-    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 3}[head]
+    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 3, "exact": 7}[head]
     line["gpu_launches"] = per_step * steps
 
     # end to end through the host entry point (pinned host buffers)

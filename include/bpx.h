@@ -68,7 +68,8 @@ enum bpx_precision {
   BPX_FP32 = 0,   /* plain FP32 FFMA (CUDA cores), encode fused into the operand load */
   BPX_BF16 = 1,   /* coded A and B rounded to bf16, one tcgen05 MMA per k-step */
   BPX_BF16X3 = 2, /* split bf16: a = a_hi + a_lo; hi*hi + hi*lo + lo*hi on tcgen05 */
-  BPX_MXFP8 = 3   /* E4M3 with one UE8M0 scale per 32 K-elements (tcgen05 block-scaled) */
+  BPX_MXFP8 = 3,  /* E4M3 with one UE8M0 scale per 32 K-elements (tcgen05 block-scaled) */
+  BPX_EXACT = 4   /* exact slices: the decode is exact at every peel depth (bpx_exact_params) */
 };
 
 enum bpx_status {
@@ -194,7 +195,9 @@ int bpx_encode(const bpx_code* code, const float* d_A, int M, int K, int h, cons
  * P_c goes to d_products + c h N (d_products: num_cells h N floats, row-major
  * h x N per cell), except that with d_C non-NULL the product of each depth-1
  * resolver goes straight to its source block d_C + s h N.  Requires the plan
- * of bpx_schedule in d_ws. */
+ * of bpx_schedule in d_ws.  BPX_EXACT: d_products is int32 storage for the S
+ * diagonal planes (see bpx_peel_decode_exact), d_C is ignored, and the
+ * scales of A and B are left in d_ws for the peel. */
 int bpx_coded_products(const bpx_code* code, const float* d_A, const float* d_B, int M, int N,
                        int K, int h, int precision, void* d_ws, size_t ws_bytes,
                        float* d_products, float* d_C, const bpx_opts* opts, bpx_stream stream);
@@ -207,9 +210,55 @@ int bpx_coded_products(const bpx_code* code, const float* d_A, const float* d_B,
 int bpx_peel_decode(const bpx_code* code, const float* d_products, int N, int h, float* d_C,
                     int direct_written, const bpx_opts* opts, const void* d_ws, bpx_stream stream);
 
+/* ---------------------------------------------------------------- exact slices
+ *
+ * BPX_EXACT restores over the reals the exactness the paper's XOR over bits
+ * has (Section II: XOR coding and peeling are exact): the peel subtracts exact
+ * integers, so a source decoded at depth 700 carries the same error as one
+ * copied from a degree-1 cell, and the result does not depend on which
+ * columns straggled.  The representation (an Ozaki-style error-free
+ * splitting) is not in the paper:
+ *   - A is scaled per row position j in [0, h) (shared by every source block,
+ *     so that rows summed into one coded row share a scale) and B per column
+ *     n, by 2^(bits - e) with 2^(e-1) <= max|x| < 2^e, and rounded to
+ *     integers (round to nearest even);
+ *   - each integer is cut into S balanced base-2^w digits (most significant
+ *     first, |digit| <= 2^(w-1)), stored as bf16 digit planes;
+ *   - a coded digit plane is the sum of its sources' planes (no carries), so
+ *     it is linear in the sources; w is chosen from the code's largest degree
+ *     sigma so that sigma 2^(w-1) <= 256 keeps coded digits exact in bf16;
+ *   - the digit pairs (i, l) with i + l <= S - 1 are kept and grouped by
+ *     diagonal d = i + l: the tensor core accumulates each diagonal over K in
+ *     FP32 in segments whose absolute sums stay below 2^23 (exact), each
+ *     segment is promoted to int32, and plane d of the products holds
+ *     P_c^d = sum_{i+l=d} D_i(A_c) D_l(B) exactly;
+ *   - the peel forms Q_c = sum_d 2^(w (S-1-d)) P_c^d in int64, subtracts
+ *     exactly, and writes C_s = RN_fp32(Q_s 2^(w (S-1) - 2 bits + e_A[j] +
+ *     e_B[n])) (Q_s exact in FP64, one rounding).
+ * The only errors are the fixed-point rounding of A and B and the dropped
+ * pairs, both about 2^-24 relative to max|A row j| max|B column n| per K term.
+ * Products cost S (S+1) / 2 bf16 MMAs per k-step (sigma 2: 6; sigma 8: 10;
+ * sigma 24: 21) and the staged planes S times the bf16 operand bytes. */
+
+/* out[5] = { w, S, bits, K elements per exact FP32 segment, K padded to 64 }
+ * for this code and K (host only).  BPX_ERR_UNSUPPORTED when sigma > 64 (digits
+ * below 3 bits) or K is so large that the int32 diagonal sums or the int64 /
+ * FP64 decoded integers could lose exactness. */
+int bpx_exact_params(const bpx_code* code, int K, int32_t* out);
+
+/* a4 for BPX_EXACT: d_planes = the S int32 product planes written by
+ * bpx_coded_products(..., BPX_EXACT, ...) (plane d at d_planes + d num_cells h N,
+ * each num_cells h N, row-major h x N per cell); the scales and an int64 copy
+ * of every decoded block live in d_ws, which must be the workspace that
+ * bpx_coded_products used (sized for BPX_EXACT).  Every recovered source,
+ * depth 1 included, is written to d_C.  opts: only stage_events and peel_ctas
+ * are read. */
+int bpx_peel_decode_exact(const bpx_code* code, const int32_t* d_planes, int N, int h, float* d_C,
+                          const bpx_opts* opts, void* d_ws, size_t ws_bytes, bpx_stream stream);
+
 /* The whole path for one erasure pattern: schedule, encode + products, peel.
- * d_products may be NULL when ws was sized for it (products then live in the
- * workspace).  d_info as in bpx_schedule. */
+ * The products live in the workspace.  d_info as in bpx_schedule.  With
+ * BPX_EXACT, direct_write and compensate_depth are ignored. */
 int bpx_coded_matmul(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K,
                      int h, int precision, const uint8_t* d_erasure_mask, float* d_C,
                      const bpx_opts* opts, void* d_ws, size_t ws_bytes, int32_t* d_info,
@@ -283,7 +332,9 @@ int bpx_group_autotune(bpx_group* group, const int* configs, int nconfigs, bpx_s
  * 2 = 128x128 output tiles, 3 / 4 = the same in clusters of two CTAs that
  * share (multicast) each B tile; seg_kb = k-blocks of 64 per TMEM
  * accumulation segment, band = m-tiles (or m-tile pairs) per rasterisation
- * band.  Synchronizes. */
+ * band.  Precisions BPX_BF16, BPX_BF16X3 and BPX_EXACT (which uses the tile
+ * width, pairing and band, with 32-wide k-slices and its own exact segment
+ * length).  Synchronizes. */
 int bpx_autotune(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
                  int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
                  const int* configs, int nconfigs, bpx_stream stream, int* best_config, float* best_ms);

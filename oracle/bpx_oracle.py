@@ -639,14 +639,32 @@ def exact_source_digits(A: np.ndarray, eA: np.ndarray, s: int, h: int, w: int, S
     return balanced_digits(fixed_point(blk, eA[:, None], bits), w, S)
 
 
-def exact_q(Ad: list, Bd: list, w: int, S: int) -> np.ndarray:
-    """Q = sum_{d <= S-1} 2^(w (S-1-d)) sum_{i+l=d} Ad[i] Bd[l], exact int64
-    (numpy's integer matmul)."""
-    q = np.zeros((Ad[0].shape[0], Bd[0].shape[1]), dtype=np.int64)
+def int_matmul(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Exact product of integer matrices through the FP64 matmul: every partial
+    sum is an integer of magnitude at most K max|X| max|Y| < 2^53, so any
+    summation order gives the exact result."""
+    K = X.shape[1]
+    bound = float(K) * float(np.abs(X).max(initial=0)) * float(np.abs(Y).max(initial=0))
+    if bound >= 2.0 ** 53:
+        raise ValueError("integer product not exact in FP64")
+    return (X.astype(np.float64) @ Y.astype(np.float64)).astype(np.int64)
+
+
+def exact_diagonals(Ad: list, Bd: list, S: int) -> list:
+    """P^d = sum_{i+l=d} Ad[i] Bd[l] for d = 0 .. S-1 (exact int64)."""
+    out = []
     for d in range(S):
-        Pd = np.zeros_like(q)
+        Pd = np.zeros((Ad[0].shape[0], Bd[0].shape[1]), dtype=np.int64)
         for i in range(d + 1):
-            Pd += Ad[i] @ Bd[d - i]
+            Pd += int_matmul(Ad[i], Bd[d - i])
+        out.append(Pd)
+    return out
+
+
+def exact_q(Ad: list, Bd: list, w: int, S: int) -> np.ndarray:
+    """Q = sum_{d <= S-1} 2^(w (S-1-d)) P^d, exact int64."""
+    q = np.zeros((Ad[0].shape[0], Bd[0].shape[1]), dtype=np.int64)
+    for d, Pd in enumerate(exact_diagonals(Ad, Bd, S)):
         q += Pd << (w * (S - 1 - d))
     return q
 
@@ -696,14 +714,31 @@ def exact_slice_coded_matmul(code: Code, A: np.ndarray, B: np.ndarray, h: int, e
     return C, CQ, sched
 
 
-def exact_slice_block(A: np.ndarray, B: np.ndarray, s: int, h: int, sigma: int, cols=None):
+def exact_coded_diagonals(code: Code, A: np.ndarray, B: np.ndarray, h: int, cell: int) -> list:
+    """The S diagonal digit products P_c^d of one cell (what a worker's
+    exact-slice product computes), from the carry-free coded digit planes."""
+    w, S, bits = exact_slice_params(code.sigma)
+    eA = exact_row_exponents(A, h)
+    eB = exact_col_exponents(B)
+    Bd = balanced_digits(fixed_point(B, eB[None, :], bits), w, S)
+    Dc = [np.zeros((h, A.shape[1]), dtype=np.int64) for _ in range(S)]
+    for s in code.cells[cell]:
+        sd = exact_source_digits(A, eA, s, h, w, S, bits)
+        for i in range(S):
+            Dc[i] += sd[i]
+    return exact_diagonals(Dc, Bd, S)
+
+
+def exact_slice_block(A: np.ndarray, B: np.ndarray, s: int, h: int, sigma: int, cols=None, eA=None):
     """The exact-slice product of one source block computed directly (no
     code, no peel), optionally on a subset of B's columns: (float32 block,
-    exact int64 Q_s).  e_A comes from all of A, e_B from the chosen columns
-    (a column's exponent depends on that column only)."""
+    exact int64 Q_s).  e_A comes from all of A (pass it when sampling many
+    blocks of a large A), e_B from the chosen columns (a column's exponent
+    depends on that column only)."""
     w, S, bits = exact_slice_params(sigma)
     Bc = np.asarray(B)[:, cols] if cols is not None else np.asarray(B)
-    eA = exact_row_exponents(A, h)
+    if eA is None:
+        eA = exact_row_exponents(A, h)
     eB = exact_col_exponents(Bc)
     Bd = balanced_digits(fixed_point(Bc, eB[None, :], bits), w, S)
     q = exact_q(exact_source_digits(A, eA, s, h, w, S, bits), Bd, w, S)

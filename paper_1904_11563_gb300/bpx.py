@@ -17,12 +17,12 @@ LIB_PATH = os.path.join(_HERE, "libbpx.so")
 
 # enums of bpx.h
 TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B = 0, 1, 2, 3, 4
-FP32, BF16, BF16X3, MXFP8 = 0, 1, 2, 3
+FP32, BF16, BF16X3, MXFP8, EXACT = 0, 1, 2, 3, 4
 OK, ERR_INVAL, ERR_UNSUPPORTED, ERR_UNDECODABLE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(7)
 INFO_STATUS, INFO_RECOVERED, INFO_WAVES, INFO_SURVIVING, INFO_DIRECT, INFO_DEVICE_ERR = range(6)
 INFO_LEN = 16
 
-PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "mxfp8": MXFP8}
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "mxfp8": MXFP8, "exact": EXACT}
 
 
 class BpxError(RuntimeError):
@@ -86,6 +86,8 @@ def lib():
         "bpx_coded_products": (i, [vp, f32p, f32p, i, i, i, i, i, vp, sz, f32p, f32p,
                                    ct.POINTER(Opts), vp]),
         "bpx_peel_decode": (i, [vp, f32p, i, i, f32p, i, ct.POINTER(Opts), vp, vp]),
+        "bpx_exact_params": (i, [vp, i, ct.POINTER(ct.c_int32)]),
+        "bpx_peel_decode_exact": (i, [vp, vp, i, i, f32p, ct.POINTER(Opts), vp, sz, vp]),
         "bpx_coded_matmul": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts),
                                  vp, sz, vp, vp]),
         "bpx_coded_matmul_host": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
@@ -265,6 +267,37 @@ def peel_decode(code: Code, products, N, h, C, ws: Workspace, direct_written=Fal
     """a4: numeric peel into C (S*h x N)."""
     _check(lib().bpx_peel_decode(code.handle, _ptr(products), N, h, _ptr(C), int(direct_written),
                                  ct.byref(opts) if opts is not None else None, ws.ptr, _stream()))
+    return C
+
+
+def exact_params(code: Code, K) -> dict:
+    """Exact-slice representation for this code and K (host only):
+    digit width w, digit planes S, fixed-point bits, K elements per exact
+    FP32 segment, padded K."""
+    out = (ct.c_int32 * 5)()
+    _check(lib().bpx_exact_params(code.handle, K, out))
+    return dict(zip(("w", "S", "bits", "seg", "Kp"), list(out)))
+
+
+def exact_products(code: Code, A, B, h, ws: Workspace, planes=None, opts=None):
+    """a3 with exact slices: the S int32 diagonal planes (S, num_cells*h, N)."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[1]
+    S = exact_params(code, K)["S"]
+    if planes is None:
+        planes = torch.zeros((S, code.num_cells * h, N), dtype=torch.int32, device=A.device)
+    _check(lib().bpx_coded_products(code.handle, _ptr(A), _ptr(B), M, N, K, h, EXACT, ws.ptr, ws.nbytes,
+                                    _ptr(planes), None, ct.byref(opts) if opts is not None else None,
+                                    _stream()))
+    return planes
+
+
+def peel_decode_exact(code: Code, planes, N, h, C, ws: Workspace, opts=None):
+    """a4 with exact slices: exact integer peel of the diagonal planes into C."""
+    _check(lib().bpx_peel_decode_exact(code.handle, _ptr(planes), N, h, _ptr(C),
+                                       ct.byref(opts) if opts is not None else None, ws.ptr, ws.nbytes,
+                                       _stream()))
     return C
 
 

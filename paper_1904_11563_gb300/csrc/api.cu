@@ -198,10 +198,53 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
       stage_mark(opts, BPX_STAGE_GEMM, 1, st);
       break;
     }
+    case BPX_EXACT: {
+      bpx::ExactParams P;
+      if (int rc = bpx::exact_params(c, K, &P)) return rc;
+      uint32_t* amax = reinterpret_cast<uint32_t*>(base + L.ex_amax);  // h words (A), then N (B)
+      void* a_pl = base + L.a_hi;
+      void* b_pl = base + L.b_hi;
+      stage_mark(opts, BPX_STAGE_B_PREP, 0, st);
+      e = bpx::launch_exact_b(d_B, K, N, P, amax + h, b_pl, st);
+      stage_mark(opts, BPX_STAGE_B_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
+      if (e == cudaSuccess) e = bpx::launch_exact_a(g, p, d_A, M, K, h, P, amax, a_pl, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 0, st);
+      if (e == cudaSuccess)
+        e = bpx::launch_gemm_exact(p, a_pl, b_pl, c->num_cells, N, K, h, P, reinterpret_cast<int32_t*>(d_products),
+                                   config, d_info, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 1, st);
+      break;
+    }
     default:
       return fail(BPX_ERR_UNSUPPORTED, "precision %d not supported", precision);
   }
   if (e != cudaSuccess) return cuda_fail(e, "bpx_coded_products: launch");
+  return BPX_OK;
+}
+
+int peel_exact_impl(const bpx_code* c, const int32_t* d_planes, int N, int h, float* d_C, const bpx_opts* opts,
+                    void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!c || !d_planes || !d_C || !ws) return fail(BPX_ERR_INVAL, "bpx_peel_decode_exact: NULL argument");
+  if (N <= 0 || h <= 0 || N % 4 != 0) return fail(BPX_ERR_INVAL, "bpx_peel_decode_exact: bad N or h");
+  if (!aligned(d_planes, 16) || !aligned(d_C, 16))
+    return fail(BPX_ERR_INVAL, "bpx_peel_decode_exact: buffers must be 16-byte aligned");
+  bpx::ExactParams P;
+  if (int rc = bpx::exact_params(c, 8, &P)) return rc;  // w, S and bits depend on sigma only
+  // The scales and the int64 blocks sit before every K-dependent region.
+  const bpx::WsLayout L = bpx::ws_layout(c, 0, N, 8, h, BPX_EXACT);
+  if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  const bpx::DevPlan p = bpx::make_plan(ws, L);
+  char* base = static_cast<char*>(ws);
+  const uint32_t* amax = reinterpret_cast<const uint32_t*>(base + L.ex_amax);
+  long long* c64 = reinterpret_cast<long long*>(base + L.ex_c64);
+  const int ctas = opts ? opts->peel_ctas : 0;
+  stage_mark(opts, BPX_STAGE_PEEL, 0, st);
+  cudaError_t e = bpx::launch_peel_exact(p, P, d_planes, static_cast<long long>(c->num_cells) * h * N, c64, d_C,
+                                         amax, amax + h, N, h, ctas, st);
+  stage_mark(opts, BPX_STAGE_PEEL, 1, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_peel_decode_exact: launch");
   return BPX_OK;
 }
 
@@ -241,6 +284,12 @@ extern "C" int bpx_peel_decode(const bpx_code* c, const float* d_products, int N
   return peel_impl(c, d_products, N, h, d_C, direct_written, opts, ws, S(stream));
 }
 
+extern "C" int bpx_peel_decode_exact(const bpx_code* c, const int32_t* d_planes, int N, int h, float* d_C,
+                                     const bpx_opts* opts, void* d_ws, size_t ws_bytes, bpx_stream stream) {
+  bpx::clear_error();
+  return peel_exact_impl(c, d_planes, N, h, d_C, opts, d_ws, ws_bytes, S(stream));
+}
+
 extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float* d_B, int M, int N,
                                 int K, int h, int precision, const uint8_t* d_mask, float* d_C,
                                 const bpx_opts* opts, void* ws, size_t ws_bytes, int32_t* d_info,
@@ -255,6 +304,12 @@ extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float
   if (int rc = bpx_schedule(c, d_mask, ws, ws_bytes, nullptr, nullptr, d_info, stream)) return rc;
   stage_mark(&o, BPX_STAGE_SCHEDULE, 1, S(stream));
   float* products = reinterpret_cast<float*>(static_cast<char*>(ws) + L.products);
+  if (precision == BPX_EXACT) {
+    if (int rc = products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, products, nullptr, &o, d_info,
+                               S(stream)))
+      return rc;
+    return peel_exact_impl(c, reinterpret_cast<const int32_t*>(products), N, h, d_C, &o, ws, ws_bytes, S(stream));
+  }
   if (int rc = products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, products,
                              o.direct_write ? d_C : nullptr, &o, d_info, S(stream)))
     return rc;
@@ -297,5 +352,5 @@ extern "C" int bpx_coded_matmul_host(const bpx_code* c, const float* h_A, const 
 }
 
 extern "C" const char* bpx_build_info(void) {
-  return "libbpx 0.1 (sm_103a; tcgen05/TMA tensor-core path, FP32 SIMT path)";
+  return "libbpx 0.2 (sm_103a; tcgen05/TMA tensor-core paths incl. exact slices, FP32 SIMT path)";
 }

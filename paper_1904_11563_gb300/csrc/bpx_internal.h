@@ -40,10 +40,25 @@ struct WsLayout {
   size_t plan_end;
   // products (float, num_cells * h * N)
   size_t products;
-  // staging for the tensor-core paths (bf16 / fp8 operands)
+  // staging for the tensor-core paths (bf16 / fp8 operands; exact-slice
+  // digit planes in a_hi / b_hi)
   size_t a_hi, a_lo, b_hi, b_lo, a_scale, b_scale;
+  // exact-slice: max |A| per row position (h words) then max |B| per column
+  // (N words), as float bits; decoded sources as exact int64 (S h N)
+  size_t ex_amax, ex_c64;
   size_t total;
 };
+
+// Exact-slice representation of a code (see bpx_exact_params): digit width
+// w, digit planes S (also the number of kept diagonals), fixed-point bits,
+// K elements per exact FP32 accumulation segment, K padded to 64.
+struct ExactParams {
+  int w = 0, S = 0, bits = 0, seg = 0, Kp = 0;
+};
+
+// Fills *P for the code's sigma and K; BPX_ERR_UNSUPPORTED (with a message)
+// when the digits or the exact integer sums would not fit.
+int exact_params(const bpx_code* c, int K, ExactParams* P);
 
 WsLayout ws_layout(const bpx_code* code, int M, int N, int K, int h, int precision);
 

@@ -4,6 +4,7 @@
 // projection's bins placed by Eq. (moj1).  Also the workspace layout and
 // the thread-local error text of the C ABI.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -268,6 +269,36 @@ extern "C" bpx_opts bpx_default_opts(void) {
 
 namespace bpx {
 
+int exact_params(const bpx_code* c, int K, ExactParams* P) {
+  if (!c || !P) return fail(BPX_ERR_INVAL, "exact_params: NULL argument");
+  if (K <= 0 || K % 8 != 0) return fail(BPX_ERR_INVAL, "exact-slice: K = %d must be a positive multiple of 8", K);
+  const int sigma = std::max(1, c->sigma);
+  int lg = 0;
+  while ((1 << lg) < sigma) ++lg;  // ceil(log2 sigma)
+  const int w = std::min(8, 9 - lg);
+  if (w < 3)
+    return fail(BPX_ERR_UNSUPPORTED, "exact-slice: cell degree %d needs digits narrower than 3 bits (at most 64)",
+                sigma);
+  P->w = w;
+  P->S = (24 + w - 1) / w;
+  P->bits = std::min(24, w * P->S - 1);
+  P->Kp = static_cast<int>(align_up(static_cast<size_t>(K), 64));
+  // Largest |coded digit x B digit|; a segment keeps the sum of absolute
+  // products below 2^23, so its FP32 accumulation is exact.
+  const double maxprod = static_cast<double>(sigma) * std::ldexp(1.0, w - 1) * std::ldexp(1.0, w - 1);
+  P->seg = static_cast<int>(std::floor(std::ldexp(1.0, 23) / maxprod / 64.0)) * 64;
+  if (P->seg < 64) return fail(BPX_ERR_UNSUPPORTED, "exact-slice: segment below 64");
+  // Per-diagonal int32 sums: S pairs x Kp elements at most.
+  if (static_cast<double>(P->S) * P->Kp * maxprod >= std::ldexp(1.0, 31))
+    return fail(BPX_ERR_UNSUPPORTED, "exact-slice: K = %d too large for exact int32 diagonal sums", K);
+  // Q and the peel's partial differences stay exact in int64 and in FP64.
+  double q = 0.0;
+  for (int d = 0; d < P->S; ++d) q += std::ldexp(1.0, w * (P->S - 1 - d)) * (d + 1) * P->Kp * maxprod;
+  if (2.0 * q >= std::ldexp(1.0, 52))
+    return fail(BPX_ERR_UNSUPPORTED, "exact-slice: K = %d too large for exact decoded integers", K);
+  return BPX_OK;
+}
+
 WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision) {
   (void)M;
   WsLayout L{};
@@ -305,6 +336,12 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
   L.p_pl_list = take(E * i32);
   L.plan_end = off;
   const size_t hN = static_cast<size_t>(h > 0 ? h : 0) * static_cast<size_t>(N > 0 ? N : 0);
+  if (precision == BPX_EXACT) {
+    // Regions that depend on h and N only come first, so that the exact peel
+    // (which does not know K) finds them at the same offsets.
+    L.ex_amax = take((static_cast<size_t>(h > 0 ? h : 0) + static_cast<size_t>(N > 0 ? N : 0)) * sizeof(uint32_t));
+    L.ex_c64 = take(S * hN * sizeof(int64_t));
+  }
   L.products = take(C * hN * sizeof(float));
   const size_t rowsA = C * static_cast<size_t>(h > 0 ? h : 0);
   const size_t Kp = static_cast<size_t>(K > 0 ? K : 0), Np = static_cast<size_t>(N > 0 ? N : 0);
@@ -316,6 +353,17 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
       L.a_lo = take(rowsA * Kp * 2);
       L.b_lo = take(Np * Kp * 2);
     }
+  } else if (precision == BPX_EXACT) {
+    ExactParams P;
+    if (exact_params(c, K > 0 ? K : 8, &P) != BPX_OK) {
+      clear_error();
+      P.S = 1;
+      P.Kp = static_cast<int>(align_up(Kp, 64));
+    }
+    const size_t planes = static_cast<size_t>(P.S), kp = static_cast<size_t>(P.Kp);
+    take((planes - 1) * C * hN * sizeof(int32_t));  // products: S int32 planes from L.products on
+    L.a_hi = take(rowsA * planes * kp * 2);
+    L.b_hi = take(Np * planes * kp * 2);
   } else if (precision == BPX_MXFP8) {
     // E4M3 operands (K-major rows) and UE8M0 scales, one per 32 K-elements,
     // stored per (tile, 128-wide K stage) in the order the GEMM copies them
@@ -331,6 +379,19 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
 }
 
 }  // namespace bpx
+
+extern "C" int bpx_exact_params(const bpx_code* c, int K, int32_t* out) {
+  bpx::clear_error();
+  if (!out) return bpx::fail(BPX_ERR_INVAL, "bpx_exact_params: out is NULL");
+  bpx::ExactParams P;
+  if (int rc = bpx::exact_params(c, K, &P)) return rc;
+  out[0] = P.w;
+  out[1] = P.S;
+  out[2] = P.bits;
+  out[3] = P.seg;
+  out[4] = P.Kp;
+  return BPX_OK;
+}
 
 extern "C" size_t bpx_workspace_bytes(const bpx_code* c, int M, int N, int K, int h, int precision) {
   if (!c) return 0;

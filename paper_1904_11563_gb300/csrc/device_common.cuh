@@ -189,6 +189,19 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
                            bool split3, float* products, float* C_direct, int config,
                            int32_t* info_out, cudaStream_t st);
 
+// Exact-slice staging (max |B| per column + B digit planes; max |A| per row
+// position + coded A digit planes), digit-product GEMM and exact peel.
+cudaError_t launch_exact_b(const float* B, int K, int N, const ExactParams& P, uint32_t* amax_b, void* bt,
+                           cudaStream_t st);
+cudaError_t launch_exact_a(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
+                           const ExactParams& P, uint32_t* amax_a, void* a_planes, cudaStream_t st);
+cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void* b_planes, int num_cells, int N,
+                              int K, int h, const ExactParams& P, int32_t* planes, int config, int32_t* info_out,
+                              cudaStream_t st);
+cudaError_t launch_peel_exact(const DevPlan& p, const ExactParams& P, const int32_t* planes, long long plane_stride,
+                              long long* C64, float* C, const uint32_t* amax_a, const uint32_t* amax_b, int N,
+                              int h, int ctas, cudaStream_t st);
+
 int num_sms();
 
 }  // namespace bpx

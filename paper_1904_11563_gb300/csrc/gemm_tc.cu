@@ -189,6 +189,11 @@ struct __align__(64) TcJob {
   int N, K, h;
   int m_tiles_max, n_tiles;
   long long tile_base;    // first tile of this job in the launch's tile space
+  // exact slices: int32 diagonal planes (plane d at planes + d plane_stride),
+  // digit planes per operand row (= diagonals), K padded to 64
+  int32_t* planes;
+  long long plane_stride;
+  int ex_S, ex_Kp;
 };
 
 template <bool kSplit, int kBN, int kBK = BK>
@@ -220,6 +225,7 @@ __device__ __forceinline__ void raise_error(const TcJob& J, int code, volatile i
 struct TileRef {
   const TcJob* J;
   int m, n, Mc, k_blocks;
+  int d, k_steps;  // exact slices: diagonal, and k-slices over its digit pairs
   bool live;
 };
 
@@ -228,8 +234,11 @@ struct TileRef {
 // rasterisation bands).  pair: the tile space counts pairs of vertically
 // adjacent m-tiles (two CTAs of a cluster share the B tile); m is then the
 // pair index and `live` tells whether the pair covers surviving rows.
+// exact: a single job's tile space repeats once per diagonal d (outermost);
+// the tile then walks the d + 1 digit pairs (i, d - i), all k-slices of one
+// pair after the other.
 __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc,
-                                          bool pair, int bk) {
+                                          bool pair, int bk, bool exact = false) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {  // last job with tile_base <= t
     const int mid = (lo + hi + 1) >> 1;
@@ -239,10 +248,16 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   TileRef R;
   R.J = &jobs[lo];
   const TcJob& J = *R.J;
-  const int lt = static_cast<int>(t - J.tile_base);
+  const int lt0 = static_cast<int>(t - J.tile_base);
   R.Mc = live_mc >= 0 ? live_mc : J.ctr[CTR_NSURV] * J.h;
   int m_units = live_mc >= 0 ? (live_mc + BM - 1) / BM : J.m_tiles_max;
   if (pair) m_units = (m_units + 1) / 2;
+  int d = 0, lt = lt0;
+  if (exact) {
+    const int per = m_units * J.n_tiles;
+    d = lt / per;
+    lt -= d * per;
+  }
   const int band_tiles = group * J.n_tiles;
   const int band = lt / band_tiles;
   const int r = lt - band * band_tiles;
@@ -250,6 +265,8 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   R.m = band * group + r % rows_in_band;
   R.n = r / rows_in_band;
   R.k_blocks = (J.K + bk - 1) / bk;
+  R.d = d;
+  R.k_steps = exact ? (d + 1) * R.k_blocks : R.k_blocks;
   R.live = (pair ? 2 * R.m : R.m) * BM < R.Mc;
   return R;
 }
@@ -284,7 +301,10 @@ __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
 // with the same B tile; each CTA TMA-loads half of the B tile and multicasts
 // it into both CTAs' stage, and each MMA commit releases the stage in both
 // CTAs, so a stage is refilled only once both have consumed it.
-template <bool kSplit, int kStages, int kBN, bool kPair, int kBK>
+// kExact: exact-slice digit products (plain bf16 MMAs over the digit planes,
+// k-slices of the diagonal's digit pairs in sequence; FP32 segments exact by
+// construction, promoted to int32 and stored to the diagonal's plane).
+template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, bool kExact = false>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ table, int njobs,
                long long total_tiles, int group, int seg_kb) {
@@ -306,7 +326,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   if (!grouped) {
     int units = (live_mc + BM - 1) / BM;
     if (kPair) units = (units + 1) / 2;
-    total_tiles = static_cast<long long>(units) * single.n_tiles;
+    total_tiles = static_cast<long long>(units) * single.n_tiles * (kExact ? single.ex_S : 1);
   }
   const uint32_t rank = kPair ? cluster_rank() : 0u;
   const int cid = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
@@ -344,7 +364,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       bool ok = true;
       const TcJob* fenced = nullptr;
       for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kExact);
         if (!T.live) continue;
         if (grouped && T.J != fenced) {
           tensormap_acquire(&T.J->map_ahi);
@@ -355,8 +375,14 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           }
           fenced = T.J;
         }
-        for (int kb = 0; kb < T.k_blocks; ++kb, ++kb_all) {
+        for (int q = 0; q < T.k_steps; ++q, ++kb_all) {
           const int s = kb_all % kStages;
+          int xa = q * kBK, xb = q * kBK;
+          if (kExact) {  // pair (pi, d - pi), k-slice kb
+            const int pi = q / T.k_blocks, kb = q - pi * T.k_blocks;
+            xa = pi * T.J->ex_Kp + kb * kBK;
+            xb = (T.d - pi) * T.J->ex_Kp + kb * kBK;
+          }
           const uint32_t ph = static_cast<uint32_t>((kb_all / kStages) & 1) ^ 1u;
           if (!mbar_wait(smem_u32(&empty_bar[s]), ph, &abort_flag)) {
             if (!abort_flag) raise_error(*T.J, BPX_ERR_TIMEOUT, &abort_flag);
@@ -367,17 +393,17 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, St::kBytes);
           const int m_cta = kPair ? 2 * T.m + static_cast<int>(rank) : T.m;
-          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, kb * kBK, m_cta * BM);
-          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, kb * kBK, m_cta * BM);
+          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, xa, m_cta * BM);
+          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, xa, m_cta * BM);
           if (kPair) {
             // this CTA's half of the B tile, into both CTAs of the pair
             constexpr uint32_t kHalf = (kBN / 2) * kBK * 2;
             const int yb = T.n * kBN + static_cast<int>(rank) * (kBN / 2);
-            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, kb * kBK, yb, 3);
-            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, kb * kBK, yb, 3);
+            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, xb, yb, 3);
+            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, xb, yb, 3);
           } else {
-            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, kb * kBK, T.n * kBN);
-            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, kb * kBK, T.n * kBN);
+            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, xb, T.n * kBN);
+            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, xb, T.n * kBN);
           }
         }
       }
@@ -395,9 +421,9 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       int kb_all = 0, g = 0;
       bool ok = true;
       for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kExact);
         if (!T.live) continue;
-        const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
+        const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
           const int buf = g & 1;
           if (!mbar_wait(smem_u32(&sempty_bar[buf]), static_cast<uint32_t>((g >> 1) & 1) ^ 1u,
@@ -408,7 +434,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           }
           fence_after();
           const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(buf * kBN);
-          const int kb0 = sg * seg_kb, kb1 = min(T.k_blocks, kb0 + seg_kb);
+          const int kb0 = sg * seg_kb, kb1 = min(T.k_steps, kb0 + seg_kb);
           for (int kb = kb0; kb < kb1; ++kb, ++kb_all) {
             const int s = kb_all % kStages;
             if (!mbar_wait(smem_u32(&full_bar[s]), static_cast<uint32_t>((kb_all / kStages) & 1),
@@ -452,12 +478,16 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     int g = 0;
     bool ok = true;
     for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK);
+      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kExact);
       if (!T.live) continue;
-      const int n_segs = (T.k_blocks + seg_kb - 1) / seg_kb;
+      const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
       float accum[kCols];
+      int iacc[kCols];
 #pragma unroll
-      for (int i = 0; i < kCols; ++i) accum[i] = 0.f;
+      for (int i = 0; i < kCols; ++i) {
+        if constexpr (kExact) iacc[i] = 0;
+        else accum[i] = 0.f;
+      }
       for (int sg = 0; sg < n_segs; ++sg, ++g) {
         const int buf = g & 1;
         if (!mbar_wait(smem_u32(&sfull_bar[buf]), static_cast<uint32_t>((g >> 1) & 1), &abort_flag)) {
@@ -473,7 +503,10 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           float v[32];
           tmem_ld32(taddr + c * 32, v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) accum[c * 32 + i] = __fadd_rn(accum[c * 32 + i], v[i]);
+          for (int i = 0; i < 32; ++i) {
+            if constexpr (kExact) iacc[c * 32 + i] += __float2int_rn(v[i]);  // an exact integer
+            else accum[c * 32 + i] = __fadd_rn(accum[c * 32 + i], v[i]);
+          }
         }
         fence_before();
         __syncwarp();
@@ -486,16 +519,26 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
         const int ci = r / J.h;
         const int j = r - ci * J.h;
         const int cell = J.surv[ci];
-        const int ds = J.C_direct ? J.direct[cell] : -1;
-        float* dst = ds >= 0 ? J.C_direct + (static_cast<long long>(ds) * J.h + j) * J.N
-                             : J.products + (static_cast<long long>(cell) * J.h + j) * J.N;
         const int n0 = T.n * kBN + half * kCols;
+        if constexpr (kExact) {
+          int32_t* dst = J.planes + T.d * J.plane_stride + (static_cast<long long>(cell) * J.h + j) * J.N;
 #pragma unroll
-        for (int q = 0; q < kCols / 4; ++q) {
-          const int n = n0 + 4 * q;
-          if (n < J.N)
-            *reinterpret_cast<float4*>(dst + n) =
-                make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+          for (int q = 0; q < kCols / 4; ++q) {
+            const int n = n0 + 4 * q;
+            if (n < J.N)
+              *reinterpret_cast<int4*>(dst + n) = make_int4(iacc[4 * q], iacc[4 * q + 1], iacc[4 * q + 2], iacc[4 * q + 3]);
+          }
+        } else {
+          const int ds = J.C_direct ? J.direct[cell] : -1;
+          float* dst = ds >= 0 ? J.C_direct + (static_cast<long long>(ds) * J.h + j) * J.N
+                               : J.products + (static_cast<long long>(cell) * J.h + j) * J.N;
+#pragma unroll
+          for (int q = 0; q < kCols / 4; ++q) {
+            const int n = n0 + 4 * q;
+            if (n < J.N)
+              *reinterpret_cast<float4*>(dst + n) =
+                  make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+          }
         }
       }
     }
@@ -832,15 +875,15 @@ bool tile_pair(int config) {
 }
 int tile_bk(int config) { return (config % 10) >= 5 ? 32 : 64; }
 
-template <bool kSplit, int kStages, int kBN, bool kPair, int kBK>
+// seg_kb: k-slices of kBK per TMEM accumulation segment.
+template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, bool kExact = false>
 cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, long long total_tiles,
                            int group, int seg_kb, cudaStream_t st) {
   // 32-wide slices: 32 KB of slack after the stages, so that the descriptors
   // of the 64-byte swizzled layout can never reach past the allocation.
   const size_t smem =
       static_cast<size_t>(kStages) * Stage<kSplit, kBN, kBK>::kBytes + 1024 + (kBK == 32 ? 32768 : 0);
-  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair, kBK>;
-  seg_kb *= BK / kBK;  // segments are counted in 64-wide k-blocks
+  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair, kBK, kExact>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (total_tiles <= 0) return cudaSuccess;
@@ -876,6 +919,7 @@ template <int kBK>
 cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, const TcJob* table, int njobs,
                         long long total_tiles, int group, int seg_kb, cudaStream_t st) {
   constexpr int m = BK / kBK;  // stages scale up as slices shrink
+  seg_kb *= m;                 // configs count segments in 64-wide k-blocks
   if (split3) {
     if (bn == 128)
       return pair ? launch_variant<true, 3 * m, 128, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
@@ -888,6 +932,17 @@ cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, con
                 : launch_variant<false, 6 * m, 128, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
   return pair ? launch_variant<false, 4 * m, 256, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
               : launch_variant<false, 4 * m, 256, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
+}
+
+// Exact slices always use 32-wide k-slices (so that a segment boundary can
+// fall on any 32 elements of the padded K); seg in k-slices.
+cudaError_t dispatch_exact(int bn, bool pair, const TcJob& J, long long total_tiles, int group, int seg,
+                           cudaStream_t st) {
+  if (bn == 128)
+    return pair ? launch_variant<false, 12, 128, true, 32, true>(J, nullptr, 1, total_tiles, group, seg, st)
+                : launch_variant<false, 12, 128, false, 32, true>(J, nullptr, 1, total_tiles, group, seg, st);
+  return pair ? launch_variant<false, 8, 256, true, 32, true>(J, nullptr, 1, total_tiles, group, seg, st)
+              : launch_variant<false, 8, 256, false, 32, true>(J, nullptr, 1, total_tiles, group, seg, st);
 }
 
 cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single, const TcJob* table, int njobs,
@@ -1000,6 +1055,29 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
   const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
   const long long tiles = static_cast<long long>(units) * J.n_tiles;
   return dispatch(split3, bn, pair, bk, J, nullptr, 1, tiles, group, seg_kb, st);
+}
+
+// Exact-slice digit products: a_planes = coded rows x (S Kp) bf16, b_planes =
+// N x (S Kp) bf16 (plane i of a row at column i Kp); diagonal d of cell c's
+// product goes to planes + d * num_cells h N + c h N as int32.
+cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void* b_planes, int num_cells, int N,
+                              int K, int h, const ExactParams& P, int32_t* planes, int config, int32_t* info_out,
+                              cudaStream_t st) {
+  int group, seg_kb, bn, bk;
+  bool pair;
+  decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
+  TcJob J;
+  if (!tc_fill_job(&J, p, a_planes, nullptr, b_planes, nullptr, num_cells, N, P.S * P.Kp, h, bn, pair, 32,
+                   nullptr, nullptr, info_out))
+    return cudaErrorInvalidValue;
+  J.K = K;
+  J.planes = planes;
+  J.plane_stride = static_cast<long long>(num_cells) * h * N;
+  J.ex_S = P.S;
+  J.ex_Kp = P.Kp;
+  const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
+  const long long tiles = static_cast<long long>(units) * J.n_tiles * P.S;
+  return dispatch_exact(bn, pair, J, tiles, group, P.seg / 32, st);
 }
 
 // Grouped launch over a device table of jobs (tile_base set, maps encoded).

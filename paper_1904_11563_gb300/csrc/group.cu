@@ -326,8 +326,8 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
                             const int* configs, int nconfigs, bpx_stream stream, int* best_config,
                             float* best_ms) {
   bpx::clear_error();
-  if (precision != BPX_BF16 && precision != BPX_BF16X3)
-    return fail(BPX_ERR_UNSUPPORTED, "bpx_autotune tunes the tensor-core GEMM (BPX_BF16 / BPX_BF16X3)");
+  if (precision != BPX_BF16 && precision != BPX_BF16X3 && precision != BPX_EXACT)
+    return fail(BPX_ERR_UNSUPPORTED, "bpx_autotune tunes the tensor-core GEMM (BPX_BF16 / BPX_BF16X3 / BPX_EXACT)");
   // one full run: plan, staged operands
   if (int rc = bpx_coded_matmul(c, d_A, d_B, M, N, K, h, precision, d_mask, d_C, nullptr, ws, ws_bytes,
                                 nullptr, stream))
@@ -339,6 +339,17 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
   const bool split = precision == BPX_BF16X3;
   float* products = reinterpret_cast<float*>(base + L.products);
   cudaStream_t st = S(stream);
+  if (precision == BPX_EXACT) {
+    bpx::ExactParams P;
+    if (int rc = bpx::exact_params(c, K, &P)) return rc;
+    return tune(configs, nconfigs, st,
+                [&](int cfg) -> int {
+                  cudaError_t e = bpx::launch_gemm_exact(p, base + L.a_hi, base + L.b_hi, c->num_cells, N, K, h, P,
+                                                         reinterpret_cast<int32_t*>(products), cfg, nullptr, st);
+                  return e == cudaSuccess ? BPX_OK : cuda_fail(e, "autotune launch");
+                },
+                best_config, best_ms);
+  }
   return tune(configs, nconfigs, st,
               [&](int cfg) -> int {
                 cudaError_t e = bpx::launch_gemm_tc(g, p, base + L.a_hi, split ? base + L.a_lo : nullptr,

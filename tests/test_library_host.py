@@ -86,3 +86,38 @@ def test_workspace_bytes_grow_with_shapes(libbpx):
 
 def test_build_info(libbpx):
     assert b"sm_103a" in libbpx.lib().bpx_build_info()
+
+
+def test_exact_params_match_oracle(libbpx):
+    """bpx_exact_params (host only) gives the digit width, plane count and
+    fixed-point bits the oracle derives from sigma, and refuses codes or K
+    where exactness could not be guaranteed."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    cases = [(bpx.Code.table1(), o.table1()), (bpx.Code.table3(), o.table3()),
+             (bpx.Code.systematic(8, 3, 8), o.systematic_mojette(8, 3, 8)),
+             (bpx.Code.mojette_a(32, 24, 683), None), (bpx.Code.mojette_a(7, 4, 10), o.construction_a(7, 4, 10)),
+             (bpx.Code.mojette_b(6, 8, 4, 2), o.construction_b(6, 8, 4, 2))]
+    for code, ref in cases:
+        sigma = ref.sigma if ref is not None else code.sigma
+        p = bpx.exact_params(code, 1000)
+        assert (p["w"], p["S"], p["bits"]) == o.exact_slice_params(sigma)
+        assert p["Kp"] == 1024 and p["seg"] % 64 == 0 and p["seg"] > 0
+        # a segment's absolute sum stays below 2^23
+        assert p["seg"] * sigma * 2 ** (2 * (p["w"] - 1)) <= 2 ** 23
+    with pytest.raises(bpx.BpxError) as e:
+        bpx.exact_params(bpx.Code.table1(), 65536)       # int32 diagonal sums could overflow
+    assert e.value.code == bpx.ERR_UNSUPPORTED
+    big = bpx.Code.systematic(80, 1, 2)                  # a parity of 80 sources: digits below 3 bits
+    assert big.sigma > 64
+    with pytest.raises(bpx.BpxError) as e:
+        bpx.exact_params(big, 64)
+    assert e.value.code == bpx.ERR_UNSUPPORTED
+    with pytest.raises(bpx.BpxError):
+        bpx.exact_params(bpx.Code.table1(), 12)          # K % 8 != 0
+    # the workspace holds S int32 planes, the digit planes, scales and int64 blocks
+    code = bpx.Code.systematic(8, 3, 8)
+    need = bpx.workspace_bytes(code, 1024, 256, 512, 16, bpx.EXACT)
+    S = 4
+    assert need >= S * code.num_cells * 16 * 256 * 4 + (code.num_cells * 16 + 256) * S * 512 * 2 \
+        + code.num_sources * 16 * 256 * 8

@@ -670,7 +670,7 @@ def test_exact_slice_planted_mistakes_are_caught(monkeypatch):
     def drop_last(Ad, Bd, w, S):
         q = np.zeros((Ad[0].shape[0], Bd[0].shape[1]), dtype=np.int64)
         for d in range(S - 1):
-            q += sum(Ad[i] @ Bd[d - i] for i in range(d + 1)) << (w * (S - 1 - d))
+            q += sum(o.int_matmul(Ad[i], Bd[d - i]) for i in range(d + 1)) << (w * (S - 1 - d))
         return q
 
     monkeypatch.setattr(o, "exact_q", drop_last)
@@ -692,3 +692,17 @@ def test_exact_slice_planted_mistakes_are_caught(monkeypatch):
         CQ[s] = Qc[r] - sum((CQ[t] for t in code.cells[r] if t != s), np.zeros_like(Qc[r]))
     direct = {s: o.exact_slice_block(A, B, s, h, code.sigma)[1] for s in range(code.num_sources)}
     assert any(not np.array_equal(CQ[s], direct[s]) for s in CQ)
+
+
+def test_int_matmul_is_exact():
+    """The FP64-matmul integer product equals Python's big-integer dot
+    products, also near the 2^53 limit of its guard."""
+    rng = np.random.default_rng(9)
+    X = rng.integers(-256, 257, size=(5, 300), dtype=np.int64)
+    Y = rng.integers(-(2 ** 20), 2 ** 20, size=(300, 4), dtype=np.int64)
+    got = o.int_matmul(X, Y)
+    for i in range(5):
+        for j in range(4):
+            assert got[i, j] == sum(int(a) * int(b) for a, b in zip(X[i], Y[:, j]))
+    with pytest.raises(ValueError):
+        o.int_matmul(np.full((1, 4), 2 ** 26, dtype=np.int64), np.full((4, 1), 2 ** 26, dtype=np.int64))
