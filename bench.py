@@ -432,6 +432,7 @@ def run_ours(args, wl):
             "warmup": warm, "ms_per_step": R["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": head, "data": "synthetic", "config": _config(wl)}
     line["stages_ms"] = R["stage"]
+    line["stages_ms_by_precision"] = {p_: r_["stage"] for p_, r_ in results.items()}
     line["gemm_config"] = tuned
     for prec, r in results.items():
         line[f"{prec}_tflops"] = world * useful / (r["ms"] * 1e-3) / 1e12

@@ -934,15 +934,24 @@ cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, con
               : launch_variant<false, 4 * m, 256, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
 }
 
-// Exact slices always use 32-wide k-slices (so that a segment boundary can
-// fall on any 32 elements of the padded K); seg in k-slices.
-cudaError_t dispatch_exact(int bn, bool pair, const TcJob& J, long long total_tiles, int group, int seg,
-                           cudaStream_t st) {
+// Exact slices: the tile's width, pairing and k-slice (the padded K is a
+// multiple of 64, so a 64-wide slice never straddles two digit planes);
+// seg in k-slices.
+template <int kBK>
+cudaError_t dispatch_exact_bk(int bn, bool pair, const TcJob& J, long long total_tiles, int group, int seg,
+                              cudaStream_t st) {
+  constexpr int m = BK / kBK;
   if (bn == 128)
-    return pair ? launch_variant<false, 12, 128, true, 32, true>(J, nullptr, 1, total_tiles, group, seg, st)
-                : launch_variant<false, 12, 128, false, 32, true>(J, nullptr, 1, total_tiles, group, seg, st);
-  return pair ? launch_variant<false, 8, 256, true, 32, true>(J, nullptr, 1, total_tiles, group, seg, st)
-              : launch_variant<false, 8, 256, false, 32, true>(J, nullptr, 1, total_tiles, group, seg, st);
+    return pair ? launch_variant<false, 6 * m, 128, true, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st)
+                : launch_variant<false, 6 * m, 128, false, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st);
+  return pair ? launch_variant<false, 4 * m, 256, true, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st)
+              : launch_variant<false, 4 * m, 256, false, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st);
+}
+
+cudaError_t dispatch_exact(int bn, bool pair, int bk, const TcJob& J, long long total_tiles, int group, int seg,
+                           cudaStream_t st) {
+  if (bk == 64) return dispatch_exact_bk<64>(bn, pair, J, total_tiles, group, seg / 64, st);
+  return dispatch_exact_bk<32>(bn, pair, J, total_tiles, group, seg / 32, st);
 }
 
 cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single, const TcJob* table, int njobs,
@@ -1065,9 +1074,12 @@ cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void
                               cudaStream_t st) {
   int group, seg_kb, bn, bk;
   bool pair;
-  decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
+  // Default: 128x256 paired tiles, 64-wide k-slices, bands of 8 (fastest
+  // measured; one MMA per k-slice and digit pair, so the wider slice halves
+  // the stage hand-offs per MMA).
+  decode_config(config > 0 ? config : 8083, &group, &seg_kb, &bn, &pair, &bk);
   TcJob J;
-  if (!tc_fill_job(&J, p, a_planes, nullptr, b_planes, nullptr, num_cells, N, P.S * P.Kp, h, bn, pair, 32,
+  if (!tc_fill_job(&J, p, a_planes, nullptr, b_planes, nullptr, num_cells, N, P.S * P.Kp, h, bn, pair, bk,
                    nullptr, nullptr, info_out))
     return cudaErrorInvalidValue;
   J.K = K;
@@ -1077,7 +1089,7 @@ cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void
   J.ex_Kp = P.Kp;
   const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
   const long long tiles = static_cast<long long>(units) * J.n_tiles * P.S;
-  return dispatch_exact(bn, pair, J, tiles, group, P.seg / 32, st);
+  return dispatch_exact(bn, pair, bk, J, tiles, group, P.seg, st);
 }
 
 // Grouped launch over a device table of jobs (tile_base set, maps encoded).

@@ -342,6 +342,11 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
   if (precision == BPX_EXACT) {
     bpx::ExactParams P;
     if (int rc = bpx::exact_params(c, K, &P)) return rc;
+    static const int kExactConfigs[] = {8083, 8081, 4083, 16083, 8084, 8082, 8087, 8085};
+    if (!configs || nconfigs <= 0) {
+      configs = kExactConfigs;
+      nconfigs = static_cast<int>(sizeof(kExactConfigs) / sizeof(kExactConfigs[0]));
+    }
     return tune(configs, nconfigs, st,
                 [&](int cfg) -> int {
                   cudaError_t e = bpx::launch_gemm_exact(p, base + L.a_hi, base + L.b_hi, c->num_cells, N, K, h, P,
