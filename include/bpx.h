@@ -275,6 +275,22 @@ int bpx_coded_matmul_host(const bpx_code* code, const float* h_A, const float* h
                           float* d_A, float* d_B, uint8_t* d_mask, float* d_C, const bpx_opts* opts,
                           void* d_ws, size_t ws_bytes, int32_t* h_info, bpx_stream stream);
 
+/* The same as bpx_coded_matmul_host without the final synchronization: the
+ * copies in, the path and the copies out are enqueued on `stream` and the call
+ * returns the launch status (BPX_OK or an argument / launch error).  h_C and
+ * h_info (decode status in h_info[BPX_INFO_STATUS], kernel self-check in
+ * [BPX_INFO_DEVICE_ERR]) are valid once `stream` has completed; until then
+ * none of the call's buffers, nor its workspace, may be reused or freed.  A
+ * caller streaming many multiplications keeps several calls in flight on
+ * different streams, each with its own device buffers and workspace, so that
+ * one call's host-to-device copies, another's kernels and a third's
+ * device-to-host copies run at the same time (the two copy directions and the
+ * SMs are separate resources).  Host buffers must be page-locked. */
+int bpx_coded_matmul_host_async(const bpx_code* code, const float* h_A, const float* h_B, int M, int N,
+                                int K, int h, int precision, const uint8_t* h_erasure_mask, float* h_C,
+                                float* d_A, float* d_B, uint8_t* d_mask, float* d_C, const bpx_opts* opts,
+                                void* d_ws, size_t ws_bytes, int32_t* h_info, bpx_stream stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent coded multiplications run together.  Each job is a whole

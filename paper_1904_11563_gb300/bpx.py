@@ -92,6 +92,8 @@ def lib():
                                  vp, sz, vp, vp]),
         "bpx_coded_matmul_host": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
                                       f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
+        "bpx_coded_matmul_host_async": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
+                                            f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_schedule_noalloc": (i, [vp, vp, vp, vp, vp, vp]),
         "bpx_group_create": (i, [ct.POINTER(Job), i, i, ct.POINTER(vp)]),
         "bpx_group_workspace_bytes": (sz, [vp]),
@@ -335,6 +337,20 @@ def coded_matmul_host(code: Code, hA, hB, h, precision, hmask, hC, dA, dB, dmask
     if rc not in (OK, ERR_UNDECODABLE):
         raise BpxError(rc, lib().bpx_last_error().decode())
     return rc, info
+
+
+def coded_matmul_host_async(code: Code, hA, hB, h, precision, hmask, hC, dA, dB, dmask, dC,
+                            ws: Workspace, hinfo, opts=None, stream=None):
+    """Enqueues copies in, the path and copies out on `stream` (default: the
+    current torch stream) without synchronizing; hC and hinfo (a pinned
+    int32[16] tensor) are valid once the stream has completed."""
+    M, K = hA.shape
+    N = hB.shape[1]
+    st = _stream() if stream is None else ct.c_void_p(stream.cuda_stream)
+    _check(lib().bpx_coded_matmul_host_async(
+        code.handle, _ptr(hA), _ptr(hB), M, N, K, h, precision, _ptr(hmask), _ptr(hC),
+        _ptr(dA), _ptr(dB), _ptr(dmask), _ptr(dC), ct.byref(opts) if opts is not None else None,
+        ws.ptr, ws.nbytes, _ptr(hinfo), st))
 
 
 def autotune(code: Code, A, B, h, precision, mask, ws: Workspace, C=None, configs=None):

@@ -316,16 +316,15 @@ extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float
   return peel_impl(c, products, N, h, d_C, o.direct_write, &o, ws, S(stream));
 }
 
-extern "C" int bpx_coded_matmul_host(const bpx_code* c, const float* h_A, const float* h_B, int M,
-                                     int N, int K, int h, int precision, const uint8_t* h_mask,
-                                     float* h_C, float* d_A, float* d_B, uint8_t* d_mask,
-                                     float* d_C, const bpx_opts* opts, void* ws, size_t ws_bytes,
-                                     int32_t* h_info, bpx_stream stream) {
-  bpx::clear_error();
+namespace {
+
+// Copies in, the whole path, copies out; synchronizes at the end when `sync`.
+int host_impl(const bpx_code* c, const float* h_A, const float* h_B, int M, int N, int K, int h, int precision,
+              const uint8_t* h_mask, float* h_C, float* d_A, float* d_B, uint8_t* d_mask, float* d_C,
+              const bpx_opts* opts, void* ws, size_t ws_bytes, int32_t* h_info, cudaStream_t st, bool sync) {
   if (!c || !h_A || !h_B || !h_mask || !h_C || !d_A || !d_B || !d_mask || !d_C || !h_info)
     return fail(BPX_ERR_INVAL, "bpx_coded_matmul_host: NULL argument");
   if (int rc = check_shapes(c, M, N, K, h)) return rc;
-  cudaStream_t st = S(stream);
   cudaError_t e;
   if ((e = cudaMemcpyAsync(d_A, h_A, sizeof(float) * M * static_cast<size_t>(K),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -338,7 +337,7 @@ extern "C" int bpx_coded_matmul_host(const bpx_code* c, const float* h_A, const 
   const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
   int32_t* d_info = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + L.p_info);
   if (int rc = bpx_coded_matmul(c, d_A, d_B, M, N, K, h, precision, d_mask, d_C, opts, ws, ws_bytes,
-                                nullptr, stream))
+                                nullptr, st))
     return rc;
   if ((e = cudaMemcpyAsync(h_C, d_C, sizeof(float) * M * static_cast<size_t>(N),
                            cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -346,9 +345,32 @@ extern "C" int bpx_coded_matmul_host(const bpx_code* c, const float* h_A, const 
   if ((e = cudaMemcpyAsync(h_info, d_info, sizeof(int32_t) * BPX_INFO_LEN, cudaMemcpyDeviceToHost,
                            st)) != cudaSuccess)
     return cuda_fail(e, "copy info");
+  if (!sync) return BPX_OK;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
   if (h_info[BPX_INFO_DEVICE_ERR] != 0) return h_info[BPX_INFO_DEVICE_ERR];
   return h_info[BPX_INFO_STATUS];
+}
+
+}  // namespace
+
+extern "C" int bpx_coded_matmul_host(const bpx_code* c, const float* h_A, const float* h_B, int M,
+                                     int N, int K, int h, int precision, const uint8_t* h_mask,
+                                     float* h_C, float* d_A, float* d_B, uint8_t* d_mask,
+                                     float* d_C, const bpx_opts* opts, void* ws, size_t ws_bytes,
+                                     int32_t* h_info, bpx_stream stream) {
+  bpx::clear_error();
+  return host_impl(c, h_A, h_B, M, N, K, h, precision, h_mask, h_C, d_A, d_B, d_mask, d_C, opts, ws, ws_bytes,
+                   h_info, S(stream), true);
+}
+
+extern "C" int bpx_coded_matmul_host_async(const bpx_code* c, const float* h_A, const float* h_B, int M, int N,
+                                           int K, int h, int precision, const uint8_t* h_mask, float* h_C,
+                                           float* d_A, float* d_B, uint8_t* d_mask, float* d_C,
+                                           const bpx_opts* opts, void* ws, size_t ws_bytes, int32_t* h_info,
+                                           bpx_stream stream) {
+  bpx::clear_error();
+  return host_impl(c, h_A, h_B, M, N, K, h, precision, h_mask, h_C, d_A, d_B, d_mask, d_C, opts, ws, ws_bytes,
+                   h_info, S(stream), false);
 }
 
 extern "C" const char* bpx_build_info(void) {

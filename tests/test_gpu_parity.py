@@ -306,6 +306,43 @@ def test_host_entry_point_matches_device(libbpx):
     assert np.array_equal(hC.numpy(), C_dev[:M])
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "exact"])
+def test_async_host_calls_in_flight(libbpx, prec):
+    """Three bpx_coded_matmul_host_async calls in flight on three streams
+    (own buffers and workspaces, different masks), launched twice round:
+    every result equals the synchronous call's, bit for bit."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 32, 64 * 32, 256, 512
+    A, B = W.inputs(M, K, N, "normal", 73)
+    P = bpx.PRECISIONS[prec]
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    masks = [torch.from_numpy(W.erasure_mask(code.n, 3, 300 + t)).pin_memory() for t in range(6)]
+    want = []
+    for t in range(6):
+        C_dev, info = _run(bpx, code, A, B, h, P, masks[t].numpy())
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        want.append(C_dev[:M])
+    sets = []
+    for j in range(3):
+        sets.append(dict(dA=torch.empty((M, K), device="cuda"), dB=torch.empty((K, N), device="cuda"),
+                         dm=torch.empty(code.n, dtype=torch.uint8, device="cuda"), dC=bpx.alloc_C(code, h, N),
+                         ws=bpx.Workspace(code, M, N, K, h, P),
+                         hC=torch.zeros((M, N), dtype=torch.float32).pin_memory(),
+                         hinfo=torch.zeros(bpx.INFO_LEN, dtype=torch.int32).pin_memory(),
+                         stream=torch.cuda.Stream()))
+    for rnd in range(2):
+        for j, S_ in enumerate(sets):
+            t = 3 * rnd + j
+            bpx.coded_matmul_host_async(code, hA, hB, h, P, masks[t], S_["hC"], S_["dA"], S_["dB"], S_["dm"],
+                                        S_["dC"], S_["ws"], S_["hinfo"], stream=S_["stream"])
+        for j, S_ in enumerate(sets):
+            S_["stream"].synchronize()
+            assert int(S_["hinfo"][bpx.INFO_STATUS]) == bpx.OK
+            assert np.array_equal(S_["hC"].numpy(), want[3 * rnd + j])
+
+
 @pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16043), ("bf16x3", 8044),
                                       ("bf16", 16043), ("bf16x3", 16022), ("bf16x3", 16045), ("bf16x3", 8047),
                                       ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8048)])
