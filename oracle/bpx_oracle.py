@@ -31,7 +31,14 @@ Matrix Multiplication"):
   decoded C_s is the same number at every peel depth and under every
   decodable erasure pattern -- the exactness the paper's XOR over bits has
   (Section II) restored over the reals.  The digit representation is not in
-  the paper; it is an Ozaki-style error-free splitting.
+  the paper; it is an Ozaki-style error-free splitting;
+* the two-dimensional scheme of Section III-A (Examples 1 and 2): source
+  (z, l) is the output block A_z B_l (row block z of A, column block l of
+  B), a cell is the sum of its sources' block products, and the same peel
+  rebuilds every block of C.  A cell factors into T products of summed
+  operands (sum of A blocks) x (sum of B blocks); the cells with T > 1
+  (for sigma = 2: the two products share neither a block of A nor one of B)
+  are the ones whose encoding the paper says must happen on the worker.
 
 Every function cites the passage it follows.  Nothing here is blocked, fused
 or reordered beyond what the definition states; a library primitive (numpy's
@@ -743,3 +750,87 @@ def exact_slice_block(A: np.ndarray, B: np.ndarray, s: int, h: int, sigma: int, 
     Bd = balanced_digits(fixed_point(Bc, eB[None, :], bits), w, S)
     q = exact_q(exact_source_digits(A, eA, s, h, w, S, bits), Bd, w, S)
     return exact_to_float(q, eA, eB, w, S, bits), q
+
+
+# --------------------------------------------------------------------------
+# Two-dimensional scheme (Section III-A, Examples 1 and 2)
+# --------------------------------------------------------------------------
+#
+# C = A B with A cut into b row blocks of h rows and B into k column blocks
+# of w columns; source s = z k + l (the grid pixel of Section III-C) is the
+# output block C_s = A_z B_l.  Table I's v_{(i-1)m+j} = a_i b_j is the
+# b = k = m case with z = i - 1, l = j - 1.
+
+
+def source_zl(code: Code, s: int):
+    """(row block of A, column block of B) of source s: s = z k + l."""
+    return divmod(s, code.k)
+
+
+def terms_2d(code: Code, cell: int):
+    """Factoring of a cell's sum of block products into products of summed
+    operands: grouped by A block (each z with its set of l), blocks of A with
+    the same set of l merged -- or the same by B block -- whichever needs
+    fewer products (ties: by A block).  Returns a list of (Z, L) with
+    sum_{s in cell} A_z(s) B_l(s) = sum_terms (sum_{z in Z} A_z)(sum_{l in L} B_l)."""
+    zl = [source_zl(code, s) for s in code.cells[cell]]
+
+    def factor(pairs):
+        groups = {}
+        for a, b_ in pairs:
+            groups.setdefault(a, set()).add(b_)
+        merged = {}
+        for a, bs in groups.items():
+            merged.setdefault(tuple(sorted(bs)), []).append(a)
+        return [(tuple(sorted(as_)), bs) for bs, as_ in merged.items()]
+
+    by_row = factor(zl)
+    by_col = [(Z, L) for (L, Z) in factor([(l, z) for z, l in zl])]
+    best = by_row if len(by_row) <= len(by_col) else by_col
+    return sorted(best)
+
+
+def gray_cells_2d(code: Code) -> list:
+    """Cells that are not one product of a summed A operand and a summed B
+    operand (T > 1): the encoding of these has to happen on the worker
+    (Section III-A, the gray cells of Tables I and III)."""
+    return [c for c in range(code.num_cells) if len(terms_2d(code, c)) > 1]
+
+
+def col_block(B: np.ndarray, l: int, w: int) -> np.ndarray:
+    """Column block l of B (columns past the end read as zero)."""
+    K, N = B.shape
+    out = np.zeros((K, w), dtype=np.float64)
+    lo, hi = l * w, min((l + 1) * w, N)
+    if lo < hi:
+        out[:, : hi - lo] = B[:, lo:hi]
+    return out
+
+
+def coded_products_2d(code: Code, A: np.ndarray, B: np.ndarray, h: int, w: int, cells):
+    """P_c = sum_{s in supp(c)} A_z(s) B_l(s), the definition (one block
+    product per source, summed in ascending source id), FP64."""
+    out = {}
+    for c in cells:
+        acc = np.zeros((h, w))
+        for s in code.cells[c]:
+            z, l = source_zl(code, s)
+            acc += row_block(A, z, h) @ col_block(B, l, w)
+        out[c] = acc
+    return out
+
+
+def coded_matmul_2d(code: Code, A: np.ndarray, B: np.ndarray, h: int, w: int, erased_cols):
+    """Whole two-dimensional path: schedule, products of the resolvers, the
+    peel (the same wave contract), C assembled from its b x k blocks.
+    Returns (C as (b h) x (k w) FP64 with unrecovered blocks NaN, schedule)."""
+    cells = surviving_cells(code, erased_cols)
+    sched = wave_schedule(code, cells)
+    used = sorted(set(r for _s, r, _d in sched.order))
+    P = coded_products_2d(code, A, B, h, w, used)
+    Cd = peel_decode(code, P, sched, h, w)
+    C = np.full((code.b * h, code.k * w), np.nan)
+    for s, blk in Cd.items():
+        z, l = source_zl(code, s)
+        C[z * h:(z + 1) * h, l * w:(l + 1) * w] = blk
+    return C, sched

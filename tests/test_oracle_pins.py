@@ -706,3 +706,70 @@ def test_int_matmul_is_exact():
             assert got[i, j] == sum(int(a) * int(b) for a, b in zip(X[i], Y[:, j]))
     with pytest.raises(ValueError):
         o.int_matmul(np.full((1, 4), 2 ** 26, dtype=np.int64), np.full((4, 1), 2 ** 26, dtype=np.int64))
+
+
+# ---------------------------------------------------------------- two-dimensional scheme
+
+def test_gray_cells_match_paper():
+    """Example 1 / Example 2: 2 of Table I's 10 cells and 6 of Table III's
+    15 combine products sharing neither a block of A nor a block of B."""
+    assert len(o.gray_cells_2d(o.table1())) == CLAIMS["table1_gray_cells"]
+    assert o.table1().num_cells == CLAIMS["table1_cells"]
+    assert len(o.gray_cells_2d(o.table3())) == CLAIMS["table3_gray_cells"]
+    assert o.table3().num_cells == CLAIMS["table3_cells"]
+    # for sigma = 2 "gray" is exactly: the two sources differ in both blocks
+    for code in (o.table1(), o.table3()):
+        for c in range(code.num_cells):
+            zl = [o.source_zl(code, s) for s in code.cells[c]]
+            neither = len(zl) == 2 and zl[0][0] != zl[1][0] and zl[0][1] != zl[1][1]
+            assert (c in o.gray_cells_2d(code)) == neither
+
+
+def test_terms_2d_partition_the_cell():
+    """The factored products cover every source of the cell exactly once:
+    the union of Z x L over the terms is the cell's set of (z, l), disjoint;
+    a full rectangle of blocks is one product."""
+    codes = [o.table1(), o.table3(), o.systematic_mojette(8, 3, 8), o.construction_a(7, 4, 5),
+             o.construction_b(6, 8, 4, 2)]
+    for code in codes:
+        for c in range(code.num_cells):
+            want = sorted(o.source_zl(code, s) for s in code.cells[c])
+            got = sorted((z, l) for Z, L in o.terms_2d(code, c) for z in Z for l in L)
+            assert got == want
+            T = len(o.terms_2d(code, c))
+            assert 1 <= T <= len(code.cells[c])
+    full = o.Code(name="rect", n=1, k=3, b=3, num_sources=9, cells=[(0, 1, 3, 4)], col_of_cell=[0], heights=[1])
+    assert o.terms_2d(full, 0) == [((0, 1), (0, 1))]
+
+
+@pytest.mark.parametrize("maker,h,w", [(o.table1, 3, 4), (o.table3, 2, 4), (lambda: o.systematic_mojette(4, 2, 3), 2, 4),
+                                       (lambda: o.construction_a(6, 4, 4), 1, 8)])
+def test_2d_integer_inputs_decode_exactly(maker, h, w):
+    """Integer inputs: every block of the two-dimensional decode equals the
+    block of A B exactly, for every decodable erasure pattern; the factored
+    products equal the definition."""
+    code = maker()
+    rng = np.random.default_rng(17)
+    M, K, N = code.b * h - 1, 10, code.k * w
+    A, B = _int_inputs(rng, M, K, N)
+    ref = o.reference_product(A, B)
+    for er in o.all_erasure_patterns(code.n, code.n - code.k):
+        if not o.decodable(code, er):
+            continue
+        C, sched = o.coded_matmul_2d(code, A, B, h, w, er)
+        assert sched.ok
+        assert np.array_equal(C[:M], ref)
+    P = o.coded_products_2d(code, A, B, h, w, range(code.num_cells))
+    for c in range(code.num_cells):
+        fac = sum((sum(o.row_block(A, z, h) for z in Z) @ sum(o.col_block(B, l, w) for l in L))
+                  for Z, L in o.terms_2d(code, c))
+        assert np.array_equal(fac, P[c])
+
+
+def test_2d_example1_source_numbering():
+    """Example 1: v1 = a1 b1, v2 = a1 b2, v3 = a2 b1, v4 = a2 b2, so the
+    Table I cell v2 + v3 is A_0 B_1 + A_1 B_0."""
+    code = o.table1()
+    assert [o.source_zl(code, s) for s in range(4)] == [(0, 0), (0, 1), (1, 0), (1, 1)]
+    c = code.cells.index((1, 2))
+    assert o.terms_2d(code, c) == [((0,), (1,)), ((1,), (0,))]
