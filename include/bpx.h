@@ -291,6 +291,46 @@ int bpx_coded_matmul_host_async(const bpx_code* code, const float* h_A, const fl
                                 float* d_A, float* d_B, uint8_t* d_mask, float* d_C, const bpx_opts* opts,
                                 void* d_ws, size_t ws_bytes, int32_t* h_info, bpx_stream stream);
 
+/* ---------------------------------------------------------------- two-dimensional scheme
+ *
+ * The paper's own scheme (Section III-A, Examples 1 and 2): C = A B with A cut
+ * into b row blocks of h rows and B into k column blocks of w = N / k columns;
+ * source s = z k + l (the grid pixel of Section III-C; Table I's
+ * v_{(i-1)m+j} = a_i b_j) is the output block C[z h .., l w ..] = A_z B_l, and
+ * a cell's coded product is the sum of its sources' block products.  The
+ * library computes a cell as few products of summed operands as its support
+ * allows: its sources grouped by A block (each z with the set of l it pairs
+ * with, A blocks with equal sets merged) or by B block, whichever gives
+ * fewer products, each product (sum_{z in Z} A_z)(sum_{l in L} B_l).  A cell
+ * with more than one product cannot be formed from one summed A operand and
+ * one summed B operand (the gray cells of Tables I and III), so the worker
+ * evaluates several block products (a K-concatenated product).  The peel is
+ * the one-dimensional scheme's (same schedule), over h x w blocks. */
+
+/* Host-only summary of the factoring: terms_per_cell[num_cells] (or NULL) and
+ * summary[4] (or NULL) = { total products over all cells, cells with more
+ * than one product, distinct summed A operands, distinct summed B operands }. */
+int bpx_terms_2d(const bpx_code* code, int32_t* terms_per_cell, int32_t* summary);
+
+/* Workspace for bpx_coded_matmul_2d: graph and plan (as bpx_workspace_bytes),
+ * products (num_cells h w floats) and the staged operands (every summed A
+ * operand as h bf16 rows of K, every summed B operand as w rows of B^T; hi and
+ * lo for BPX_BF16X3).  The workspace is bound with bpx_workspace_init. */
+size_t bpx_workspace_bytes_2d(const bpx_code* code, int M, int N, int K, int h, int precision);
+
+/* Schedule (a1, shared with the one-dimensional scheme), staging of the summed
+ * operands, the coded products of every surviving cell on the tensor cores
+ * (one persistent launch over all cells' h x w tiles, most products first),
+ * and the peel.  d_C: b h rows of N floats (row stride N; rows >= M are
+ * scratch); block (z, l) at row z h, column l w.  N must be a multiple of k
+ * with w = N / k a multiple of 4; K a multiple of 8; M <= b h.  precision:
+ * BPX_BF16 or BPX_BF16X3.  opts: direct_write (depth-1 blocks written by the
+ * GEMM), gemm_config (tile config as for bpx_autotune), peel_ctas,
+ * stage_events (BPX_STAGE_A_PREP covers the staging of both operands). */
+int bpx_coded_matmul_2d(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
+                        int precision, const uint8_t* d_erasure_mask, float* d_C, const bpx_opts* opts, void* d_ws,
+                        size_t ws_bytes, int32_t* d_info, bpx_stream stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent coded multiplications run together.  Each job is a whole

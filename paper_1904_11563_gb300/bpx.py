@@ -95,6 +95,9 @@ def lib():
         "bpx_coded_matmul_host_async": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
                                             f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_schedule_noalloc": (i, [vp, vp, vp, vp, vp, vp]),
+        "bpx_terms_2d": (i, [vp, vp, vp]),
+        "bpx_workspace_bytes_2d": (sz, [vp, i, i, i, i, i]),
+        "bpx_coded_matmul_2d": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_group_create": (i, [ct.POINTER(Job), i, i, ct.POINTER(vp)]),
         "bpx_group_workspace_bytes": (sz, [vp]),
         "bpx_group_init": (i, [vp, vp, sz, vp]),
@@ -301,6 +304,47 @@ def peel_decode_exact(code: Code, planes, N, h, C, ws: Workspace, opts=None):
                                        ct.byref(opts) if opts is not None else None, ws.ptr, ws.nbytes,
                                        _stream()))
     return C
+
+
+def terms_2d(code: Code):
+    """Two-dimensional scheme factoring (host only): (products per cell,
+    {total, gray, a_operands, b_operands})."""
+    per = np.zeros(code.num_cells, dtype=np.int32)
+    summ = np.zeros(4, dtype=np.int32)
+    _check(lib().bpx_terms_2d(code.handle, per.ctypes.data_as(ct.c_void_p), summ.ctypes.data_as(ct.c_void_p)))
+    return per, dict(zip(("total", "gray", "a_operands", "b_operands"), (int(x) for x in summ)))
+
+
+class Workspace2D:
+    """Device workspace of the two-dimensional scheme (bound to a code)."""
+
+    def __init__(self, code: Code, M, N, K, h, precision, device="cuda"):
+        torch = _torch()
+        self.nbytes = int(lib().bpx_workspace_bytes_2d(code.handle, M, N, K, h, precision))
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.base = self.buf[off:off + self.nbytes]
+        self.code = code
+        _check(lib().bpx_workspace_init(code.handle, ct.c_void_p(self.base.data_ptr()), self.nbytes, _stream()))
+
+    @property
+    def ptr(self):
+        return ct.c_void_p(self.base.data_ptr())
+
+
+def coded_matmul_2d(code: Code, A, B, h, precision, mask, ws: Workspace2D, C=None, opts=None, info=None):
+    """Two-dimensional scheme: C ((b h) x N) with block (z, l) = A_z B_l."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = torch.zeros((code.b * h, N), dtype=torch.float32, device=A.device)
+    if info is None:
+        info = torch.zeros(INFO_LEN, dtype=torch.int32, device=A.device)
+    _check(lib().bpx_coded_matmul_2d(code.handle, _ptr(A), _ptr(B), M, N, K, h, precision, _ptr(mask), _ptr(C),
+                                     ct.byref(opts) if opts is not None else None, ws.ptr, ws.nbytes, _ptr(info),
+                                     _stream()))
+    return C, info
 
 
 def alloc_C(code: Code, h, N, device="cuda"):

@@ -91,6 +91,14 @@ extern "C" int bpx_workspace_init(const bpx_code* c, void* ws, size_t ws_bytes, 
       {L.g_cell_src, c->cell_src.data(), c->cell_src.size() * 4},
       {L.g_src_ptr, c->src_ptr.data(), c->src_ptr.size() * 4},
       {L.g_src_cell, c->src_cell.data(), c->src_cell.size() * 4},
+      {L.g_t2_ptr, c->t2_ptr.data(), c->t2_ptr.size() * 4},
+      {L.g_t2_a, c->t2_a.data(), c->t2_a.size() * 4},
+      {L.g_t2_b, c->t2_b.data(), c->t2_b.size() * 4},
+      {L.g_a2_ptr, c->a2_ptr.data(), c->a2_ptr.size() * 4},
+      {L.g_a2_blk, c->a2_blk.data(), c->a2_blk.size() * 4},
+      {L.g_b2_ptr, c->b2_ptr.data(), c->b2_ptr.size() * 4},
+      {L.g_b2_blk, c->b2_blk.data(), c->b2_blk.size() * 4},
+      {L.g_t2_order, c->t2_order.data(), c->t2_order.size() * 4},
   };
   for (const Part& pt : parts) {
     if (pt.bytes == 0) continue;
@@ -288,6 +296,75 @@ extern "C" int bpx_peel_decode_exact(const bpx_code* c, const int32_t* d_planes,
                                      const bpx_opts* opts, void* d_ws, size_t ws_bytes, bpx_stream stream) {
   bpx::clear_error();
   return peel_exact_impl(c, d_planes, N, h, d_C, opts, d_ws, ws_bytes, S(stream));
+}
+
+// ---- two-dimensional scheme ------------------------------------------------
+
+extern "C" int bpx_terms_2d(const bpx_code* c, int32_t* terms_per_cell, int32_t* summary) {
+  bpx::clear_error();
+  if (!c) return fail(BPX_ERR_INVAL, "bpx_terms_2d: code is NULL");
+  if (terms_per_cell)
+    for (int i = 0; i < c->num_cells; ++i) terms_per_cell[i] = c->t2_ptr[i + 1] - c->t2_ptr[i];
+  if (summary) {
+    summary[0] = static_cast<int32_t>(c->t2_a.size());
+    summary[1] = c->gray2;
+    summary[2] = static_cast<int32_t>(c->a2_ptr.size()) - 1;
+    summary[3] = static_cast<int32_t>(c->b2_ptr.size()) - 1;
+  }
+  return BPX_OK;
+}
+
+extern "C" size_t bpx_workspace_bytes_2d(const bpx_code* c, int M, int N, int K, int h, int precision) {
+  if (!c) return 0;
+  return bpx::ws_layout(c, M, N, K, h, precision, true).total;
+}
+
+extern "C" int bpx_coded_matmul_2d(const bpx_code* c, const float* d_A, const float* d_B, int M, int N, int K, int h,
+                                   int precision, const uint8_t* d_mask, float* d_C, const bpx_opts* opts, void* ws,
+                                   size_t ws_bytes, int32_t* d_info, bpx_stream stream) {
+  bpx::clear_error();
+  if (!c || !d_A || !d_B || !d_mask || !d_C || !ws) return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: NULL argument");
+  if (M < 0 || N <= 0 || K <= 0 || h <= 0) return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: bad shape");
+  if (N % c->k != 0) return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: N = %d must be k w (k = %d)", N, c->k);
+  const int w = N / c->k;
+  if (w % 4 != 0) return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: block width w = N / k = %d must be a multiple of 4", w);
+  if (K % 8 != 0) return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: K = %d must be a multiple of 8", K);
+  if (static_cast<long long>(M) > static_cast<long long>(c->b) * h)
+    return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: M = %d exceeds b h = %lld rows", M, 1LL * c->b * h);
+  if (precision != BPX_BF16 && precision != BPX_BF16X3)
+    return fail(BPX_ERR_UNSUPPORTED, "bpx_coded_matmul_2d: precision BPX_BF16 or BPX_BF16X3");
+  if (!aligned(d_A, 16) || !aligned(d_B, 16) || !aligned(d_C, 16))
+    return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: buffers must be 16-byte aligned");
+  const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision, true);
+  if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  const bpx_opts o = opts ? *opts : bpx_default_opts();
+  cudaStream_t st = S(stream);
+  stage_mark(&o, BPX_STAGE_SCHEDULE, 0, st);
+  if (int rc = bpx_schedule(c, d_mask, ws, ws_bytes, nullptr, nullptr, d_info, stream)) return rc;
+  stage_mark(&o, BPX_STAGE_SCHEDULE, 1, st);
+  const bpx::DevGraph g = bpx::make_graph(c, ws, L);
+  const bpx::DevPlan p = bpx::make_plan(ws, L);
+  char* base = static_cast<char*>(ws);
+  const bool split = precision == BPX_BF16X3;
+  void* a_hi = base + L.a_hi;
+  void* a_lo = split ? base + L.a_lo : nullptr;
+  void* b_hi = base + L.b_hi;
+  void* b_lo = split ? base + L.b_lo : nullptr;
+  float* products = reinterpret_cast<float*>(base + L.products);
+  stage_mark(&o, BPX_STAGE_A_PREP, 0, st);
+  cudaError_t e = bpx::launch_stage_2d(g, d_A, d_B, M, N, K, h, w, a_hi, a_lo, b_hi, b_lo, st);
+  stage_mark(&o, BPX_STAGE_A_PREP, 1, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_coded_matmul_2d: staging");
+  stage_mark(&o, BPX_STAGE_GEMM, 0, st);
+  e = bpx::launch_gemm_2d(g, p, a_hi, a_lo, b_hi, b_lo, N, K, h, w, split, products, o.direct_write ? d_C : nullptr,
+                          o.gemm_config, d_info, st);
+  stage_mark(&o, BPX_STAGE_GEMM, 1, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_coded_matmul_2d: GEMM");
+  stage_mark(&o, BPX_STAGE_PEEL, 0, st);
+  e = bpx::launch_peel_2d(g, p, products, d_C, N, h, w, o.direct_write ? 2 : 1, o.peel_ctas, st);
+  stage_mark(&o, BPX_STAGE_PEEL, 1, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_coded_matmul_2d: peel");
+  return BPX_OK;
 }
 
 extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float* d_B, int M, int N,

@@ -17,6 +17,14 @@ struct bpx_code {
   double eps = 0.0;
   std::vector<int32_t> col_ptr, cell_ptr, cell_src, col_of_cell, heights, proj_p, proj_q;
   std::vector<int32_t> src_ptr, src_cell;  // source -> cells (ascending cell id)
+  // Two-dimensional scheme (source s = z k + l is the block product A_z B_l):
+  // every cell as a list of products of summed operands, term i of cell c at
+  // [t2_ptr[c], t2_ptr[c+1]) = (A operand t2_a[i], B operand t2_b[i]); A
+  // operand e sums the row blocks a2_blk[a2_ptr[e] ..], B operand f the
+  // column blocks b2_blk[b2_ptr[f] ..]; t2_order lists the cells by
+  // decreasing term count (ties by id); gray2 counts cells with > 1 term.
+  std::vector<int32_t> t2_ptr, t2_a, t2_b, a2_ptr, a2_blk, b2_ptr, b2_blk, t2_order;
+  int gray2 = 0;
 };
 
 namespace bpx {
@@ -33,6 +41,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct WsLayout {
   // graph (int32)
   size_t g_hdr, g_col_of_cell, g_cell_ptr, g_cell_src, g_src_ptr, g_src_cell;
+  size_t g_t2_ptr, g_t2_a, g_t2_b, g_a2_ptr, g_a2_blk, g_b2_ptr, g_b2_blk, g_t2_order;
   // plan (int32)
   size_t p_info, p_ctr, p_cnt, p_surv, p_direct, p_front0, p_front1, p_cand;
   size_t p_depth, p_resolver, p_order, p_newsrc, p_wave_ptr, p_cursor;
@@ -60,7 +69,13 @@ struct ExactParams {
 // when the digits or the exact integer sums would not fit.
 int exact_params(const bpx_code* c, int K, ExactParams* P);
 
-WsLayout ws_layout(const bpx_code* code, int M, int N, int K, int h, int precision);
+// twod: the two-dimensional scheme (products are h x (N / k) blocks, operand
+// staging holds the summed A and B operands of the code's factored cells).
+WsLayout ws_layout(const bpx_code* code, int M, int N, int K, int h, int precision, bool twod = false);
+
+// Factors every cell for the two-dimensional scheme (fills the t2_* / a2_* /
+// b2_* arrays of the code).
+void build_terms_2d(bpx_code* c);
 
 constexpr int32_t kWsMagic = 0x42505831;  // "BPX1"
 

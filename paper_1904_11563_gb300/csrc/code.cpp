@@ -226,6 +226,7 @@ extern "C" int bpx_code_build(int variant, int n, int k, int e, int b, int q_e, 
   }
   c->e = derived_e;
   B.finish();
+  bpx::build_terms_2d(c);
   *out = c;
   return BPX_OK;
 }
@@ -299,7 +300,7 @@ int exact_params(const bpx_code* c, int K, ExactParams* P) {
   return BPX_OK;
 }
 
-WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision) {
+WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision, bool twod) {
   (void)M;
   WsLayout L{};
   size_t off = 0;
@@ -317,6 +318,14 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
   L.g_cell_src = take(E * i32);
   L.g_src_ptr = take((S + 1) * i32);
   L.g_src_cell = take(E * i32);
+  L.g_t2_ptr = take(c->t2_ptr.size() * i32);
+  L.g_t2_a = take(c->t2_a.size() * i32);
+  L.g_t2_b = take(c->t2_b.size() * i32);
+  L.g_a2_ptr = take(c->a2_ptr.size() * i32);
+  L.g_a2_blk = take(c->a2_blk.size() * i32);
+  L.g_b2_ptr = take(c->b2_ptr.size() * i32);
+  L.g_b2_blk = take(c->b2_blk.size() * i32);
+  L.g_t2_order = take(c->t2_order.size() * i32);
   L.p_info = take(BPX_INFO_LEN * i32);
   L.p_ctr = take(CTR_LEN * i32);
   L.p_cnt = take(C * i32);
@@ -336,6 +345,23 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision)
   L.p_pl_list = take(E * i32);
   L.plan_end = off;
   const size_t hN = static_cast<size_t>(h > 0 ? h : 0) * static_cast<size_t>(N > 0 ? N : 0);
+  if (twod) {
+    // products: h x w per cell (w = N / k); staging: every A operand (h rows
+    // each) and every B operand (w rows of B^T each), bf16 hi (+ lo)
+    const size_t w = static_cast<size_t>(N > 0 ? N / c->k : 0), hh = static_cast<size_t>(h > 0 ? h : 0);
+    const size_t Kq = static_cast<size_t>(K > 0 ? K : 0);
+    const size_t EA = c->a2_ptr.size() - 1, EB = c->b2_ptr.size() - 1;
+    L.products = take(C * hh * w * sizeof(float));
+    L.a_hi = take(EA * hh * Kq * 2);
+    L.b_hi = take(EB * w * Kq * 2);
+    L.a_lo = L.b_lo = L.a_scale = L.b_scale = L.ex_amax = L.ex_c64 = off;
+    if (precision == BPX_BF16X3) {
+      L.a_lo = take(EA * hh * Kq * 2);
+      L.b_lo = take(EB * w * Kq * 2);
+    }
+    L.total = off;
+    return L;
+  }
   if (precision == BPX_EXACT) {
     // Regions that depend on h and N only come first, so that the exact peel
     // (which does not know K) finds them at the same offsets.

@@ -16,7 +16,17 @@ struct DevGraph {
   const int32_t* cell_src;
   const int32_t* src_ptr;
   const int32_t* src_cell;
+  // two-dimensional scheme: cell terms, operand block lists, cell order
+  const int32_t* t2_ptr;
+  const int32_t* t2_a;
+  const int32_t* t2_b;
+  const int32_t* a2_ptr;
+  const int32_t* a2_blk;
+  const int32_t* b2_ptr;
+  const int32_t* b2_blk;
+  const int32_t* t2_order;
   int n, S, num_cells, num_edges, sigma;
+  int k, EA, EB;  // grid width (B blocks), A and B operand counts
 };
 
 // Peel plan written by the schedule kernel.
@@ -51,6 +61,17 @@ inline DevGraph make_graph(const bpx_code* c, const void* ws, const WsLayout& L)
   g.cell_src = reinterpret_cast<const int32_t*>(base + L.g_cell_src);
   g.src_ptr = reinterpret_cast<const int32_t*>(base + L.g_src_ptr);
   g.src_cell = reinterpret_cast<const int32_t*>(base + L.g_src_cell);
+  g.t2_ptr = reinterpret_cast<const int32_t*>(base + L.g_t2_ptr);
+  g.t2_a = reinterpret_cast<const int32_t*>(base + L.g_t2_a);
+  g.t2_b = reinterpret_cast<const int32_t*>(base + L.g_t2_b);
+  g.a2_ptr = reinterpret_cast<const int32_t*>(base + L.g_a2_ptr);
+  g.a2_blk = reinterpret_cast<const int32_t*>(base + L.g_a2_blk);
+  g.b2_ptr = reinterpret_cast<const int32_t*>(base + L.g_b2_ptr);
+  g.b2_blk = reinterpret_cast<const int32_t*>(base + L.g_b2_blk);
+  g.t2_order = reinterpret_cast<const int32_t*>(base + L.g_t2_order);
+  g.k = c->k;
+  g.EA = static_cast<int>(c->a2_ptr.size()) - 1;
+  g.EB = static_cast<int>(c->b2_ptr.size()) - 1;
   g.n = c->n;
   g.S = c->S;
   g.num_cells = c->num_cells;
@@ -201,6 +222,17 @@ cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void
 cudaError_t launch_peel_exact(const DevPlan& p, const ExactParams& P, const int32_t* planes, long long plane_stride,
                               long long* C64, float* C, const uint32_t* amax_a, const uint32_t* amax_b, int N,
                               int h, int ctas, cudaStream_t st);
+
+// Two-dimensional scheme: operand staging (summed A blocks, summed B^T
+// blocks, bf16 hi (+ lo)), products GEMM over each cell's terms, and the peel
+// over strided h x w blocks of C.
+cudaError_t launch_stage_2d(const DevGraph& g, const float* A, const float* B, int M, int N, int K, int h, int w,
+                            void* a_hi, void* a_lo, void* b_hi, void* b_lo, cudaStream_t st);
+cudaError_t launch_gemm_2d(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
+                           const void* b_lo, int N, int K, int h, int w, bool split3, float* products,
+                           float* C_direct, int config, int32_t* info_out, cudaStream_t st);
+cudaError_t launch_peel_2d(const DevGraph& g, const DevPlan& p, const float* P, float* C, int N, int h, int w,
+                           int first_wave, int ctas, cudaStream_t st);
 
 int num_sms();
 

@@ -194,6 +194,16 @@ struct __align__(64) TcJob {
   int32_t* planes;
   long long plane_stride;
   int ex_S, ex_Kp;
+  // two-dimensional scheme: every cell (in t2_order) is a list of terms (A
+  // operand, B operand) over h-row A operands and w-row B^T operands; N is the
+  // row stride of C; kc = the code's k (source s = z kc + l); cnt = -1 marks
+  // the cells of erased columns
+  const int32_t* t2_ptr;
+  const int32_t* t2_a;
+  const int32_t* t2_b;
+  const int32_t* t2_order;
+  const int32_t* cnt;
+  int w2, kc, ncells;
 };
 
 template <bool kSplit, int kBN, int kBK = BK>
@@ -226,8 +236,13 @@ struct TileRef {
   const TcJob* J;
   int m, n, Mc, k_blocks;
   int d, k_steps;  // exact slices: diagonal, and k-slices over its digit pairs
+  int cell, tp;    // two-dimensional scheme: the tile's cell and its first term
   bool live;
 };
+
+// Kernel modes: the coded GEMM of the one-dimensional scheme, its exact-slice
+// digit products, and the two-dimensional scheme's per-cell term products.
+enum { kModeRows = 0, kModeExact = 1, kMode2D = 2 };
 
 // live_mc >= 0: a single job whose surviving row count is already known; its
 // tile space then holds the live m-tiles only (no skipped tiles inside the
@@ -238,7 +253,29 @@ struct TileRef {
 // the tile then walks the d + 1 digit pairs (i, d - i), all k-slices of one
 // pair after the other.
 __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc,
-                                          bool pair, int bk, bool exact = false) {
+                                          bool pair, int bk, int mode = kModeRows) {
+  const bool exact = mode == kModeExact;
+  if (mode == kMode2D) {
+    // one job; tile space = cells (most terms first) x m-units x n-tiles,
+    // m fastest so that CTAs resident together share the B operand tile
+    const TcJob& J = jobs[0];
+    TileRef R;
+    R.J = &J;
+    const int m_units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
+    const int per_cell = m_units * J.n_tiles;
+    const int ci = static_cast<int>(t / per_cell);
+    const int r = static_cast<int>(t - static_cast<long long>(ci) * per_cell);
+    R.cell = J.t2_order[ci];
+    R.n = r / m_units;
+    R.m = r - R.n * m_units;
+    R.Mc = J.h;
+    R.d = 0;
+    R.tp = J.t2_ptr[R.cell];
+    R.k_blocks = (J.K + bk - 1) / bk;
+    R.k_steps = (J.t2_ptr[R.cell + 1] - R.tp) * R.k_blocks;
+    R.live = J.cnt[R.cell] >= 0;
+    return R;
+  }
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {  // last job with tile_base <= t
     const int mid = (lo + hi + 1) >> 1;
@@ -266,6 +303,7 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   R.n = r / rows_in_band;
   R.k_blocks = (J.K + bk - 1) / bk;
   R.d = d;
+  R.cell = R.tp = 0;
   R.k_steps = exact ? (d + 1) * R.k_blocks : R.k_blocks;
   R.live = (pair ? 2 * R.m : R.m) * BM < R.Mc;
   return R;
@@ -301,13 +339,17 @@ __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
 // with the same B tile; each CTA TMA-loads half of the B tile and multicasts
 // it into both CTAs' stage, and each MMA commit releases the stage in both
 // CTAs, so a stage is refilled only once both have consumed it.
-// kExact: exact-slice digit products (plain bf16 MMAs over the digit planes,
-// k-slices of the diagonal's digit pairs in sequence; FP32 segments exact by
-// construction, promoted to int32 and stored to the diagonal's plane).
-template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, bool kExact = false>
+// kMode == kModeExact: exact-slice digit products (plain bf16 MMAs over the
+// digit planes, k-slices of the diagonal's digit pairs in sequence; FP32
+// segments exact by construction, promoted to int32 and stored to the
+// diagonal's plane).  kMode == kMode2D: the two-dimensional scheme (k-slices
+// of the cell's terms in sequence; h x w output blocks).
+template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, int kMode = kModeRows>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ table, int njobs,
                long long total_tiles, int group, int seg_kb) {
+  constexpr bool kExact = kMode == kModeExact;
+  constexpr bool k2D = kMode == kMode2D;
   using St = Stage<kSplit, kBN, kBK>;
   constexpr int kTmemCols = 2 * kBN;  // two FP32 segment accumulators
   constexpr int kCols = kBN / 2;      // columns per epilogue warp
@@ -323,7 +365,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // A single job reads its surviving row count once and walks live tiles only.
   const int live_mc = grouped ? -1 : single.ctr[CTR_NSURV] * single.h;
-  if (!grouped) {
+  if (!grouped && !k2D) {
     int units = (live_mc + BM - 1) / BM;
     if (kPair) units = (units + 1) / 2;
     total_tiles = static_cast<long long>(units) * single.n_tiles * (kExact ? single.ex_S : 1);
@@ -364,7 +406,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       bool ok = true;
       const TcJob* fenced = nullptr;
       for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kExact);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
         if (!T.live) continue;
         if (grouped && T.J != fenced) {
           tensormap_acquire(&T.J->map_ahi);
@@ -375,6 +417,8 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           }
           fenced = T.J;
         }
+        const int m_cta = kPair ? 2 * T.m + static_cast<int>(rank) : T.m;
+        int ya = m_cta * BM, yb = T.n * kBN, cur_term = -1;
         for (int q = 0; q < T.k_steps; ++q, ++kb_all) {
           const int s = kb_all % kStages;
           int xa = q * kBK, xb = q * kBK;
@@ -382,6 +426,15 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
             const int pi = q / T.k_blocks, kb = q - pi * T.k_blocks;
             xa = pi * T.J->ex_Kp + kb * kBK;
             xb = (T.d - pi) * T.J->ex_Kp + kb * kBK;
+          }
+          if (k2D) {  // term ti of the cell, k-slice kb
+            const int ti = q / T.k_blocks, kb = q - ti * T.k_blocks;
+            if (ti != cur_term) {
+              cur_term = ti;
+              ya = T.J->t2_a[T.tp + ti] * T.J->h + m_cta * BM;
+              yb = T.J->t2_b[T.tp + ti] * T.J->w2 + T.n * kBN;
+            }
+            xa = xb = kb * kBK;
           }
           const uint32_t ph = static_cast<uint32_t>((kb_all / kStages) & 1) ^ 1u;
           if (!mbar_wait(smem_u32(&empty_bar[s]), ph, &abort_flag)) {
@@ -392,18 +445,17 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           const uint32_t base = smem_u32(smem + s * St::kBytes);
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, St::kBytes);
-          const int m_cta = kPair ? 2 * T.m + static_cast<int>(rank) : T.m;
-          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, xa, m_cta * BM);
-          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, xa, m_cta * BM);
+          tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, xa, ya);
+          if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, xa, ya);
           if (kPair) {
             // this CTA's half of the B tile, into both CTAs of the pair
             constexpr uint32_t kHalf = (kBN / 2) * kBK * 2;
-            const int yb = T.n * kBN + static_cast<int>(rank) * (kBN / 2);
-            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, xb, yb, 3);
-            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, xb, yb, 3);
+            const int yh = yb + static_cast<int>(rank) * (kBN / 2);
+            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, xb, yh, 3);
+            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, xb, yh, 3);
           } else {
-            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, xb, T.n * kBN);
-            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, xb, T.n * kBN);
+            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, xb, yb);
+            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, xb, yb);
           }
         }
       }
@@ -421,7 +473,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       int kb_all = 0, g = 0;
       bool ok = true;
       for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kExact);
+        const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
         if (!T.live) continue;
         const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
@@ -478,7 +530,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     int g = 0;
     bool ok = true;
     for (long long t = cid; t < total_tiles && ok; t += nclusters) {
-      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kExact);
+      const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
       if (!T.live) continue;
       const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
       float accum[kCols];
@@ -515,7 +567,26 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       if (!ok) break;
       const TcJob& J = *T.J;
       const int r = (kPair ? 2 * T.m + static_cast<int>(rank) : T.m) * BM + row;
-      if (r < T.Mc) {
+      if (k2D) {
+        if (r < J.h) {  // row r of the cell's h x w block
+          const int ds = J.C_direct ? J.direct[T.cell] : -1;
+          float* dst;
+          if (ds >= 0) {
+            const int z = ds / J.kc, l = ds - z * J.kc;
+            dst = J.C_direct + (static_cast<long long>(z) * J.h + r) * J.N + static_cast<long long>(l) * J.w2;
+          } else {
+            dst = J.products + (static_cast<long long>(T.cell) * J.h + r) * J.w2;
+          }
+          const int n0 = T.n * kBN + half * kCols;
+#pragma unroll
+          for (int q = 0; q < kCols / 4; ++q) {
+            const int n = n0 + 4 * q;
+            if (n < J.w2)
+              *reinterpret_cast<float4*>(dst + n) =
+                  make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+          }
+        }
+      } else if (r < T.Mc) {
         const int ci = r / J.h;
         const int j = r - ci * J.h;
         const int cell = J.surv[ci];
@@ -876,14 +947,14 @@ bool tile_pair(int config) {
 int tile_bk(int config) { return (config % 10) >= 5 ? 32 : 64; }
 
 // seg_kb: k-slices of kBK per TMEM accumulation segment.
-template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, bool kExact = false>
+template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, int kMode = kModeRows>
 cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, long long total_tiles,
                            int group, int seg_kb, cudaStream_t st) {
   // 32-wide slices: 32 KB of slack after the stages, so that the descriptors
   // of the 64-byte swizzled layout can never reach past the allocation.
   const size_t smem =
       static_cast<size_t>(kStages) * Stage<kSplit, kBN, kBK>::kBytes + 1024 + (kBK == 32 ? 32768 : 0);
-  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair, kBK, kExact>;
+  auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair, kBK, kMode>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (total_tiles <= 0) return cudaSuccess;
@@ -915,23 +986,20 @@ cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, l
   return cudaLaunchKernelEx(&cfg, kern, single, table, njobs, total_tiles, group, seg_kb);
 }
 
-template <int kBK>
+template <int kBK, int kMode = kModeRows>
 cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, const TcJob* table, int njobs,
                         long long total_tiles, int group, int seg_kb, cudaStream_t st) {
   constexpr int m = BK / kBK;  // stages scale up as slices shrink
   seg_kb *= m;                 // configs count segments in 64-wide k-blocks
+#define BPX_LV(SPLIT, STAGES, BN, PAIR) \
+  launch_variant<SPLIT, STAGES, BN, PAIR, kBK, kMode>(single, table, njobs, total_tiles, group, seg_kb, st)
   if (split3) {
-    if (bn == 128)
-      return pair ? launch_variant<true, 3 * m, 128, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
-                  : launch_variant<true, 3 * m, 128, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
-    return pair ? launch_variant<true, 2 * m, 256, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
-                : launch_variant<true, 2 * m, 256, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
+    if (bn == 128) return pair ? BPX_LV(true, 3 * m, 128, true) : BPX_LV(true, 3 * m, 128, false);
+    return pair ? BPX_LV(true, 2 * m, 256, true) : BPX_LV(true, 2 * m, 256, false);
   }
-  if (bn == 128)
-    return pair ? launch_variant<false, 6 * m, 128, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
-                : launch_variant<false, 6 * m, 128, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
-  return pair ? launch_variant<false, 4 * m, 256, true, kBK>(single, table, njobs, total_tiles, group, seg_kb, st)
-              : launch_variant<false, 4 * m, 256, false, kBK>(single, table, njobs, total_tiles, group, seg_kb, st);
+  if (bn == 128) return pair ? BPX_LV(false, 6 * m, 128, true) : BPX_LV(false, 6 * m, 128, false);
+  return pair ? BPX_LV(false, 4 * m, 256, true) : BPX_LV(false, 4 * m, 256, false);
+#undef BPX_LV
 }
 
 // Exact slices: the tile's width, pairing and k-slice (the padded K is a
@@ -942,10 +1010,10 @@ cudaError_t dispatch_exact_bk(int bn, bool pair, const TcJob& J, long long total
                               cudaStream_t st) {
   constexpr int m = BK / kBK;
   if (bn == 128)
-    return pair ? launch_variant<false, 6 * m, 128, true, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st)
-                : launch_variant<false, 6 * m, 128, false, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st);
-  return pair ? launch_variant<false, 4 * m, 256, true, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st)
-              : launch_variant<false, 4 * m, 256, false, kBK, true>(J, nullptr, 1, total_tiles, group, seg, st);
+    return pair ? launch_variant<false, 6 * m, 128, true, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st)
+                : launch_variant<false, 6 * m, 128, false, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
+  return pair ? launch_variant<false, 4 * m, 256, true, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st)
+              : launch_variant<false, 4 * m, 256, false, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
 }
 
 cudaError_t dispatch_exact(int bn, bool pair, int bk, const TcJob& J, long long total_tiles, int group, int seg,
@@ -955,7 +1023,12 @@ cudaError_t dispatch_exact(int bn, bool pair, int bk, const TcJob& J, long long 
 }
 
 cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single, const TcJob* table, int njobs,
-                     long long total_tiles, int group, int seg_kb, cudaStream_t st) {
+                     long long total_tiles, int group, int seg_kb, cudaStream_t st, bool twod = false) {
+  if (twod) {
+    if (bk == 32)
+      return dispatch_bk<32, kMode2D>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
+    return dispatch_bk<64, kMode2D>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
+  }
   if (bk == 32) return dispatch_bk<32>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
   return dispatch_bk<64>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
 }
@@ -1090,6 +1163,54 @@ cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void
   const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
   const long long tiles = static_cast<long long>(units) * J.n_tiles * P.S;
   return dispatch_exact(bn, pair, bk, J, tiles, group, P.seg, st);
+}
+
+// Two-dimensional scheme: A operands (EA x h rows) and B^T operands (EB x w
+// rows) staged as bf16; every tile of every cell (erased cells' tiles are
+// skipped) accumulates its cell's terms; h x w blocks go to products (cell c
+// at c h w, row stride w) or, for depth-1 resolvers, to C (row stride N).
+cudaError_t launch_gemm_2d(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
+                           const void* b_lo, int N, int K, int h, int w, bool split3, float* products,
+                           float* C_direct, int config, int32_t* info_out, cudaStream_t st) {
+  int group, seg_kb, bn, bk;
+  bool pair;
+  decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
+  TcJob J;
+  memset(&J, 0, sizeof J);
+  const int box_b = pair ? bn / 2 : bn;
+  const long long rows_a = static_cast<long long>(g.EA) * h, rows_b = static_cast<long long>(g.EB) * w;
+  if (!make_map(&J.map_ahi, a_hi, rows_a, K, BM, bk) || !make_map(&J.map_bhi, b_hi, rows_b, K, box_b, bk))
+    return cudaErrorInvalidValue;
+  if (split3) {
+    if (!make_map(&J.map_alo, a_lo, rows_a, K, BM, bk) || !make_map(&J.map_blo, b_lo, rows_b, K, box_b, bk))
+      return cudaErrorInvalidValue;
+  } else {
+    J.map_alo = J.map_ahi;
+    J.map_blo = J.map_bhi;
+  }
+  J.ctr = p.ctr;
+  J.surv = p.surv;
+  J.direct = p.direct;
+  J.info = p.info;
+  J.info_out = info_out;
+  J.products = products;
+  J.C_direct = C_direct;
+  J.N = N;
+  J.K = K;
+  J.h = h;
+  J.m_tiles_max = (h + BM - 1) / BM;
+  J.n_tiles = (w + bn - 1) / bn;
+  J.t2_ptr = g.t2_ptr;
+  J.t2_a = g.t2_a;
+  J.t2_b = g.t2_b;
+  J.t2_order = g.t2_order;
+  J.cnt = p.cnt;
+  J.w2 = w;
+  J.kc = g.k;
+  J.ncells = g.num_cells;
+  const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
+  const long long tiles = static_cast<long long>(units) * J.n_tiles * g.num_cells;
+  return dispatch(split3, bn, pair, bk, J, nullptr, 1, tiles, group, seg_kb, st, true);
 }
 
 // Grouped launch over a device table of jobs (tile_base set, maps encoded).

@@ -121,3 +121,28 @@ def test_exact_params_match_oracle(libbpx):
     S = 4
     assert need >= S * code.num_cells * 16 * 256 * 4 + (code.num_cells * 16 + 256) * S * 512 * 2 \
         + code.num_sources * 16 * 256 * 8
+
+
+def test_terms_2d_match_oracle(libbpx):
+    """The library's factoring of every cell for the two-dimensional scheme
+    (an independent C++ implementation) gives the oracle's product count per
+    cell, hence the paper's gray-cell counts for Tables I and III."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    cases = [(bpx.Code.table1(), o.table1()), (bpx.Code.table3(), o.table3()),
+             (bpx.Code.systematic(8, 3, 8), o.systematic_mojette(8, 3, 8)),
+             (bpx.Code.mojette_a(7, 4, 10), o.construction_a(7, 4, 10)),
+             (bpx.Code.mojette_b(6, 8, 4, 2), o.construction_b(6, 8, 4, 2))]
+    for code, ref in cases:
+        per, summ = bpx.terms_2d(code)
+        want = [len(o.terms_2d(ref, c)) for c in range(ref.num_cells)]
+        assert list(per) == want
+        assert summ["total"] == sum(want)
+        assert summ["gray"] == len(o.gray_cells_2d(ref))
+        A_ops = {Z for c in range(ref.num_cells) for Z, _L in o.terms_2d(ref, c)}
+        B_ops = {L for c in range(ref.num_cells) for _Z, L in o.terms_2d(ref, c)}
+        assert summ["a_operands"] == len(A_ops) and summ["b_operands"] == len(B_ops)
+    assert bpx.terms_2d(bpx.Code.table1())[1]["gray"] == 2
+    assert bpx.terms_2d(bpx.Code.table3())[1]["gray"] == 6
+    code = bpx.Code.systematic(8, 3, 8)
+    assert bpx.lib().bpx_workspace_bytes_2d(code.handle, 8192, 8192, 8192, 1024, bpx.BF16X3) > 0
