@@ -34,6 +34,8 @@ WORKLOAD = "sysmoj_8192"
 CODE_TEXT = {
     "sysmoj_8192": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, slopes 0,+1,-1)",
     "mojA_16384": "Mojette Construction A n=32 (k=24 x b=683 grid, q=1, p=-15..16), e=8",
+    "sysmoj_8192_2d": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, slopes 0,+1,-1) "
+                      "in the two-dimensional scheme (source (z, l) = A_z B_l, 1024 x 1024 blocks)",
     "batch512": "512 jobs: half array codes (Table I, Table III, systematic Mojette n=6..32, e=2..3), "
                 "half Construction A (n=6..32, e=n//4); each job its own seeded mask",
 }
@@ -655,6 +657,97 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_2d(args, wl):
+    """The paper's two-dimensional scheme on the benchmark code: C's 8 x 8
+    blocks of 1024 x 1024 are the sources, cells sum block products; one
+    step = schedule, operand staging, coded products, peel."""
+    import torch
+    from paper_1904_11563_gb300 import build as B_
+    B_.build()
+    from paper_1904_11563_gb300 import bpx
+    from paper_1904_11563_gb300 import workloads as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    code = _lib_code(bpx, wl)
+    M, N, K, h = wl["M"], wl["N"], wl["K"], wl["h"]
+    w = N // code.k
+    A, Bm = W.device_inputs(M, K, N, wl["dist"], wl["seed"], device=str(dev))
+    masks = torch.from_numpy(np.stack([_mask(W, wl, t) for t in range(wl["trials"])])).to(dev)
+    prec = args.precision if args.precision in ("bf16", "bf16x3") else "bf16x3"
+    P = bpx.PRECISIONS[prec]
+    ws = bpx.Workspace2D(code, M, N, K, h, P, device=dev)
+    C = torch.zeros((code.b * h, N), dtype=torch.float32, device=dev)
+    info = torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device=dev)
+    opts = bpx.default_opts(gemm_config=args.gemm_config)
+    warm, steps = max(args.warmup, 3), args.steps
+    for i in range(warm):
+        bpx.coded_matmul_2d(code, A, Bm, h, P, masks[i % wl["trials"]], ws, C=C, opts=opts, info=info)
+    torch.cuda.synchronize()
+    sev = StageEvents(bpx, steps)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for i in range(steps):
+        o_ = bpx.default_opts(gemm_config=args.gemm_config)
+        o_.stage_events = sev.ptr(i)
+        bpx.coded_matmul_2d(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o_, info=info)
+    t1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1) / steps
+    assert int(info[bpx.INFO_STATUS].item()) == bpx.OK
+    stage = {}
+    for si, nm in enumerate(bpx.STAGE_NAMES):
+        vals = [v for v in (sev.stage_ms(i, si) for i in range(steps)) if v]
+        if vals:
+            stage[nm] = sum(vals) / len(vals)
+    # executed MMA work: every surviving cell's products (T_c of them) of
+    # h x w x K, times 3 for split-BF16x3
+    per, summ = bpx.terms_2d(code)
+    col_of = np.repeat(np.arange(code.n), np.diff(code.col_ptr))
+    mult = 3 if prec == "bf16x3" else 1
+    mma = []
+    for i in range(steps):
+        mk = masks[(warm + i) % wl["trials"]].cpu().numpy()
+        mma.append(sum(int(per[c]) for c in range(code.num_cells) if not mk[col_of[c]]) * 2.0 * h * w * K * mult)
+    mma_mean = float(np.mean(mma))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = mma_mean / (stage["gemm"] * 1e-3) / 1e12
+    useful = 2.0 * M * N * K
+    # relative error of the deepest blocks and a direct one vs FP64 A_z B_l
+    last = masks[(warm + steps - 1) % wl["trials"]]
+    order, _r, _i = bpx.schedule(code, last, bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32, device=dev))
+    order = order.cpu().numpy()
+    depth = {int(s_): int(d_) for s_, _r2, d_ in order if s_ >= 0}
+    samples = sorted(depth, key=lambda s_: -depth[s_])[:2] + [s_ for s_ in sorted(depth) if depth[s_] == 1][:1]
+    Ah, Bh = A.cpu().numpy(), Bm.cpu().numpy()
+    errs = []
+    for s_ in samples:
+        z, l = divmod(s_, code.k)
+        r = Ah[z * h:(z + 1) * h].astype(np.float64) @ Bh[:, l * w:(l + 1) * w].astype(np.float64)
+        c = C[z * h:(z + 1) * h, l * w:(l + 1) * w].double().cpu().numpy()
+        errs.append(float(np.linalg.norm(c - r) / np.linalg.norm(r)))
+    line = {"metric": METRIC, "value": useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": wl["name"], "code": CODE_TEXT[wl["name"]], "M": M, "N": N, "K": K, "h": h, "w": w,
+                       "erasures": wl["e"], "trials": wl["trials"], "inputs": "A, B iid N(0,1) FP32, seeded",
+                       "l2": "inputs larger than L2 (A 268 MB; no flush)"},
+            "stages_ms": stage, "terms_2d": summ, "executed_over_useful": mma_mean / mult / useful,
+            "rel_err": {"sources": samples, "depths": [depth[s_] for s_ in samples], "errs": errs},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "tcgen05 GEMM over each cell's products (two-dimensional scheme)",
+                         "work_per_launch": "sum over surviving cells of T_c x 2 h w K x %d MMA flops" % mult},
+            "clocks": ck, "gpu_launches": 5 * steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     from paper_1904_11563_gb300 import workloads as W
@@ -664,7 +757,11 @@ def main():
         wl["M"], wl["N"], wl["K"] = (int(x) for x in args.shape.split(","))
     if args.workload == "batch512":
         run_batch(args)
+    elif wl.get("twod") and args.impl != "reference":
+        run_2d(args, wl)
     elif args.impl == "reference":
+        if wl.get("twod"):
+            raise SystemExit("--impl reference times the one-dimensional workloads only")
         run_reference(args, wl)
     else:
         run_ours(args, wl)

@@ -309,6 +309,14 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   return R;
 }
 
+// Tile of round j for CTA (or CTA pair) c of G: rounds alternate direction
+// (c, 2G-1-c, 2G+c, ...), so that over a tile space ordered from the longest
+// tiles to the shortest every CTA gets long and short ones alike.  The
+// sequence increases with j, so a CTA stops at its first tile past the end.
+__device__ __forceinline__ long long snake(long long j, int c, int G) {
+  return j * G + ((j & 1) ? (G - 1 - c) : c);
+}
+
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -405,7 +413,9 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       int kb_all = 0;
       bool ok = true;
       const TcJob* fenced = nullptr;
-      for (long long t = cid; t < total_tiles && ok; t += nclusters) {
+      for (long long j = 0; ok; ++j) {
+        const long long t = snake(j, cid, nclusters);
+        if (t >= total_tiles) break;
         const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
         if (!T.live) continue;
         if (grouped && T.J != fenced) {
@@ -472,7 +482,9 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     if (lane == 0) {
       int kb_all = 0, g = 0;
       bool ok = true;
-      for (long long t = cid; t < total_tiles && ok; t += nclusters) {
+      for (long long j = 0; ok; ++j) {
+        const long long t = snake(j, cid, nclusters);
+        if (t >= total_tiles) break;
         const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
         if (!T.live) continue;
         const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
@@ -529,7 +541,9 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     const int row = quarter * 32 + lane;
     int g = 0;
     bool ok = true;
-    for (long long t = cid; t < total_tiles && ok; t += nclusters) {
+    for (long long j = 0; ok; ++j) {
+      const long long t = snake(j, cid, nclusters);
+      if (t >= total_tiles) break;
       const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
       if (!T.live) continue;
       const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
