@@ -32,6 +32,11 @@ Matrix Multiplication"):
   decodable erasure pattern -- the exactness the paper's XOR over bits has
   (Section II) restored over the reals.  The digit representation is not in
   the paper; it is an Ozaki-style error-free splitting;
+* the straggler-time model of Section IV: processor (cell) task times
+  T_c = sigma_c X_c with X_c exponential of rate mu, and the parallel task
+  time min over decodable sets S of max_{c in S} T_c of Eq. (eqnTtotal),
+  both by brute force over subsets and as the first prefix of the arrival
+  order that peels completely;
 * the two-dimensional scheme of Section III-A (Examples 1 and 2): source
   (z, l) is the output block A_z B_l (row block z of A, column block l of
   B), a cell is the sum of its sources' block products, and the same peel
@@ -834,3 +839,45 @@ def coded_matmul_2d(code: Code, A: np.ndarray, B: np.ndarray, h: int, w: int, er
         z, l = source_zl(code, s)
         C[z * h:(z + 1) * h, l * w:(l + 1) * w] = blk
     return C, sched
+
+
+# --------------------------------------------------------------------------
+# Straggler-time model (Section IV, Eq. (eqnTtotal))
+# --------------------------------------------------------------------------
+
+
+def task_times(code: Code, mu: float, rng: np.random.Generator, scale_by_degree: bool = True) -> np.ndarray:
+    """T_c for every cell: a processor doing sigma_c long dot products has
+    the exponential cdf of rate mu stretched by sigma_c (Section IV-A), i.e.
+    T_c = sigma_c X_c with X_c ~ Exp(mu); sigma_c = 1 when not scaling."""
+    X = rng.exponential(1.0 / mu, size=code.num_cells)
+    deg = np.array([len(c) for c in code.cells], dtype=np.float64)
+    return X * (deg if scale_by_degree else 1.0)
+
+
+def decodes(code: Code, cell_subset) -> bool:
+    """Peeling over the given cells recovers every source (Section I-A)."""
+    return len(sequential_peel(code, list(cell_subset))) == code.num_sources
+
+
+def parallel_task_time_brute(code: Code, T) -> float:
+    """min over decodable cell sets S of max_{c in S} T_c, by enumerating
+    every subset (tiny codes only)."""
+    best = np.inf
+    cells = range(code.num_cells)
+    for r in range(1, code.num_cells + 1):
+        for S in itertools.combinations(cells, r):
+            t = max(T[c] for c in S)
+            if t < best and decodes(code, S):
+                best = t
+    return float(best)
+
+
+def first_decodable(code: Code, order) -> int:
+    """Number of arrivals after which the cells received so far (in the
+    given order) peel completely, or -1: the sink starts decoding as soon as
+    a decodable set has arrived."""
+    for i in range(1, len(order) + 1):
+        if decodes(code, order[:i]):
+            return i
+    return -1

@@ -773,3 +773,54 @@ def test_2d_example1_source_numbering():
     assert [o.source_zl(code, s) for s in range(4)] == [(0, 0), (0, 1), (1, 0), (1, 1)]
     c = code.cells.index((1, 2))
     assert o.terms_2d(code, c) == [((0,), (1,)), ((1,), (0,))]
+
+
+# ---------------------------------------------------------------- straggler-time model
+
+@pytest.mark.parametrize("maker", [o.table1, o.table3, lambda: o.systematic_mojette(3, 2, 2)])
+def test_parallel_task_time_is_first_decodable_prefix(maker):
+    """min over decodable sets of the latest arrival (Eq. (eqnTtotal), brute
+    force over every subset) equals the arrival time of the first prefix of
+    the arrival order that peels completely."""
+    code = maker()
+    rng = np.random.default_rng(8)
+    for _ in range(15):
+        T = o.task_times(code, 1.0, rng)
+        order = list(np.argsort(T, kind="stable"))
+        i = o.first_decodable(code, order)
+        assert i > 0
+        assert T[order[i - 1]] == o.parallel_task_time_brute(code, T)
+
+
+def test_table1_first_decodable_at_most_seven():
+    """Example 1: any 7 processor outputs suffice, so no arrival order needs
+    more than 7 cells; some order needs exactly 7."""
+    code = o.table1()
+    rng = np.random.default_rng(1)
+    worst = 0
+    for _ in range(400):
+        order = list(rng.permutation(code.num_cells))
+        worst = max(worst, o.first_decodable(code, order))
+    assert worst <= CLAIMS["table1_recovery_threshold"]
+    # an order that starts with a non-decodable 6-set
+    for S in itertools.combinations(range(10), 6):
+        if not o.decodes(code, S):
+            rest = [c for c in range(10) if c not in S]
+            assert o.first_decodable(code, list(S) + rest) == 7
+            break
+    else:
+        raise AssertionError("every 6-set decodes")
+
+
+def test_task_time_scaling():
+    """T_c = sigma_c X_c: mean of T_c / sigma_c is 1 / mu; the expected
+    maximum of b rate-mu exponentials is H_b / mu (Section IV-A order
+    statistics), checked by Monte Carlo on unscaled times."""
+    code = o.table1()
+    rng = np.random.default_rng(2)
+    deg = np.array([len(c) for c in code.cells])
+    Ts = np.stack([o.task_times(code, 2.0, rng) for _ in range(20000)])
+    assert abs((Ts / deg).mean() - 0.5) < 0.01
+    U = np.stack([o.task_times(code, 2.0, rng, scale_by_degree=False) for _ in range(20000)])
+    H = sum(1.0 / j for j in range(1, 11))
+    assert abs(U.max(axis=1).mean() - H / 2.0) < 0.03
