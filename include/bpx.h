@@ -121,6 +121,9 @@ typedef struct {
   void* const* stage_events; /* NULL, or cudaEvent_t[2 * BPX_NUM_STAGES] created by the caller:
                                 events 2i / 2i+1 are recorded on the stream right before / after
                                 stage i (enum bpx_stage).  Used to time kernels in place. */
+  int mask_cells;       /* 0 (default): erasure masks have one byte per code column (a node
+                           straggled); 1: one byte per cell (a single processor's output is
+                           missing, the straggler model of Section IV) */
 } bpx_opts;
 
 /* Stages of the hot path, in launch order (for bpx_opts.stage_events). */
@@ -181,6 +184,21 @@ int bpx_workspace_init(const bpx_code* code, void* d_ws, size_t ws_bytes, bpx_st
  * info array says BPX_ERR_UNDECODABLE and the partial plan stays usable. */
 int bpx_schedule(const bpx_code* code, const uint8_t* d_erasure_mask, void* d_ws, size_t ws_bytes,
                  int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, bpx_stream stream);
+
+/* a1 with a cell-level mask: d_cell_mask[num_cells], 1 = that processor's
+ * output is missing (Section IV: processors straggle individually).
+ * Otherwise as bpx_schedule. */
+int bpx_schedule_cells(const bpx_code* code, const uint8_t* d_cell_mask, void* d_ws, size_t ws_bytes,
+                       int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, bpx_stream stream);
+
+/* Straggler-time model (Section IV, Eq. (eqnTtotal)), host only: the cells'
+ * products arrive in order[0 .. n) (distinct cell ids); the sink peels online
+ * as they arrive.  recovered_after[i] (or NULL) = sources recovered once
+ * order[0..i] have arrived; *first = the number of arrivals after which every
+ * source is recovered -- so T_{order[*first - 1]} = min over decodable sets S
+ * of max_{c in S} T_c -- or -1 if the n arrivals never decode. */
+int bpx_first_decodable(const bpx_code* code, const int32_t* order, int n, int32_t* recovered_after,
+                        int32_t* first);
 
 /* a2. Worker-side encode, materialized (Section III-A, Example 1: the nodes
  * form the sums themselves): for the i-th surviving cell c (ascending id, as

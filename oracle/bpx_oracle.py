@@ -846,13 +846,30 @@ def coded_matmul_2d(code: Code, A: np.ndarray, B: np.ndarray, h: int, w: int, er
 # --------------------------------------------------------------------------
 
 
-def task_times(code: Code, mu: float, rng: np.random.Generator, scale_by_degree: bool = True) -> np.ndarray:
+def task_times(code: Code, mu: float, rng: np.random.Generator, scale_by_degree: bool = True, X=None) -> np.ndarray:
     """T_c for every cell: a processor doing sigma_c long dot products has
     the exponential cdf of rate mu stretched by sigma_c (Section IV-A), i.e.
-    T_c = sigma_c X_c with X_c ~ Exp(mu); sigma_c = 1 when not scaling."""
-    X = rng.exponential(1.0 / mu, size=code.num_cells)
+    T_c = sigma_c X_c with X_c ~ Exp(mu); sigma_c = 1 when not scaling.  X
+    (the unscaled draws) may be given instead of drawn."""
+    if X is None:
+        X = rng.exponential(1.0 / mu, size=code.num_cells)
     deg = np.array([len(c) for c in code.cells], dtype=np.float64)
-    return X * (deg if scale_by_degree else 1.0)
+    return np.asarray(X, dtype=np.float64) * (deg if scale_by_degree else 1.0)
+
+
+def coded_matmul_cells(code: Code, A: np.ndarray, B: np.ndarray, h: int, cells):
+    """The whole path when exactly the given cells' products arrived (a
+    processor-level erasure pattern).  Returns (C with unrecovered blocks
+    NaN, schedule)."""
+    sched = wave_schedule(code, sorted(cells))
+    N = B.shape[1]
+    used = sorted(set(r for _s, r, _d in sched.order))
+    P = coded_products(code, A, B, h, used)
+    Cd = peel_decode(code, P, sched, h, N)
+    C = np.full((code.num_sources * h, N), np.nan)
+    for s, blk in Cd.items():
+        C[s * h:(s + 1) * h] = blk
+    return C, sched
 
 
 def decodes(code: Code, cell_subset) -> bool:

@@ -47,7 +47,7 @@ class _CodeInfo(ct.Structure):
 class Opts(ct.Structure):
     _fields_ = [("direct_write", ct.c_int), ("compensate_depth", ct.c_int),
                 ("peel_ctas", ct.c_int), ("gemm_config", ct.c_int),
-                ("stage_events", ct.POINTER(ct.c_void_p))]
+                ("stage_events", ct.POINTER(ct.c_void_p)), ("mask_cells", ct.c_int)]
 
 
 STAGE_SCHEDULE, STAGE_B_PREP, STAGE_A_PREP, STAGE_GEMM, STAGE_PEEL = range(5)
@@ -95,6 +95,8 @@ def lib():
         "bpx_coded_matmul_host_async": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
                                             f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_schedule_noalloc": (i, [vp, vp, vp, vp, vp, vp]),
+        "bpx_schedule_cells": (i, [vp, vp, vp, sz, vp, vp, vp, vp]),
+        "bpx_first_decodable": (i, [vp, vp, i, vp, vp]),
         "bpx_terms_2d": (i, [vp, vp, vp]),
         "bpx_workspace_bytes_2d": (sz, [vp, i, i, i, i, i]),
         "bpx_coded_matmul_2d": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
@@ -233,15 +235,16 @@ class Workspace:
         return _ptr(self.t)
 
 
-def schedule(code: Code, mask, ws: Workspace):
-    """a1: returns (peel_order int32[S,3], recovered uint8[S], info int32[16]) on device."""
+def schedule(code: Code, mask, ws: Workspace, cells=False):
+    """a1: returns (peel_order int32[S,3], recovered uint8[S], info int32[16])
+    on device; cells=True: the mask has one byte per cell."""
     torch = _torch()
     S = code.num_sources
     order = torch.empty((S, 3), dtype=torch.int32, device=mask.device)
     rec = torch.empty(S, dtype=torch.uint8, device=mask.device)
     info = torch.empty(INFO_LEN, dtype=torch.int32, device=mask.device)
-    _check(lib().bpx_schedule(code.handle, _ptr(mask), ws.ptr, ws.nbytes, _ptr(order), _ptr(rec),
-                              _ptr(info), _stream()))
+    fn = lib().bpx_schedule_cells if cells else lib().bpx_schedule
+    _check(fn(code.handle, _ptr(mask), ws.ptr, ws.nbytes, _ptr(order), _ptr(rec), _ptr(info), _stream()))
     return order, rec, info
 
 
@@ -273,6 +276,18 @@ def peel_decode(code: Code, products, N, h, C, ws: Workspace, direct_written=Fal
     _check(lib().bpx_peel_decode(code.handle, _ptr(products), N, h, _ptr(C), int(direct_written),
                                  ct.byref(opts) if opts is not None else None, ws.ptr, _stream()))
     return C
+
+
+def first_decodable(code: Code, order):
+    """Online peel over cells arriving in `order` (host only): (number of
+    arrivals after which every source is recovered, or -1; sources recovered
+    after each arrival)."""
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    rec = np.zeros(len(order), dtype=np.int32)
+    first = ct.c_int32()
+    _check(lib().bpx_first_decodable(code.handle, order.ctypes.data_as(ct.c_void_p), len(order),
+                                     rec.ctypes.data_as(ct.c_void_p), ct.byref(first)))
+    return int(first.value), rec
 
 
 def exact_params(code: Code, K) -> dict:

@@ -112,19 +112,34 @@ extern "C" int bpx_workspace_init(const bpx_code* c, void* ws, size_t ws_bytes, 
   return BPX_OK;
 }
 
-extern "C" int bpx_schedule(const bpx_code* c, const uint8_t* d_mask, void* ws, size_t ws_bytes,
-                            int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info,
-                            bpx_stream stream) {
-  bpx::clear_error();
+namespace {
+
+int schedule_impl(const bpx_code* c, const uint8_t* d_mask, bool cell_mask, void* ws, size_t ws_bytes,
+                  int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, cudaStream_t st) {
   if (!c) return fail(BPX_ERR_INVAL, "bpx_schedule: code is NULL");
   const bpx::WsLayout L = bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32);
   if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
   if (!d_mask) return fail(BPX_ERR_INVAL, "bpx_schedule: erasure mask is NULL");
   const bpx::DevGraph g = bpx::make_graph(c, ws, L);
   const bpx::DevPlan p = bpx::make_plan(ws, L);
-  cudaError_t e = bpx::launch_schedule(g, p, d_mask, d_peel_order, d_recovered, d_info, S(stream));
+  cudaError_t e = bpx::launch_schedule(g, p, d_mask, d_peel_order, d_recovered, d_info, st, cell_mask);
   if (e != cudaSuccess) return cuda_fail(e, "bpx_schedule: launch");
   return BPX_OK;
+}
+
+}  // namespace
+
+extern "C" int bpx_schedule(const bpx_code* c, const uint8_t* d_mask, void* ws, size_t ws_bytes,
+                            int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info,
+                            bpx_stream stream) {
+  bpx::clear_error();
+  return schedule_impl(c, d_mask, false, ws, ws_bytes, d_peel_order, d_recovered, d_info, S(stream));
+}
+
+extern "C" int bpx_schedule_cells(const bpx_code* c, const uint8_t* d_cell_mask, void* ws, size_t ws_bytes,
+                                  int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, bpx_stream stream) {
+  bpx::clear_error();
+  return schedule_impl(c, d_cell_mask, true, ws, ws_bytes, d_peel_order, d_recovered, d_info, S(stream));
 }
 
 extern "C" int bpx_encode(const bpx_code* c, const float* d_A, int M, int K, int h,
@@ -340,7 +355,7 @@ extern "C" int bpx_coded_matmul_2d(const bpx_code* c, const float* d_A, const fl
   const bpx_opts o = opts ? *opts : bpx_default_opts();
   cudaStream_t st = S(stream);
   stage_mark(&o, BPX_STAGE_SCHEDULE, 0, st);
-  if (int rc = bpx_schedule(c, d_mask, ws, ws_bytes, nullptr, nullptr, d_info, stream)) return rc;
+  if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, st)) return rc;
   stage_mark(&o, BPX_STAGE_SCHEDULE, 1, st);
   const bpx::DevGraph g = bpx::make_graph(c, ws, L);
   const bpx::DevPlan p = bpx::make_plan(ws, L);
@@ -378,7 +393,8 @@ extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float
   const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
   if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
   stage_mark(&o, BPX_STAGE_SCHEDULE, 0, S(stream));
-  if (int rc = bpx_schedule(c, d_mask, ws, ws_bytes, nullptr, nullptr, d_info, stream)) return rc;
+  if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, S(stream)))
+    return rc;
   stage_mark(&o, BPX_STAGE_SCHEDULE, 1, S(stream));
   float* products = reinterpret_cast<float*>(static_cast<char*>(ws) + L.products);
   if (precision == BPX_EXACT) {
@@ -409,7 +425,8 @@ int host_impl(const bpx_code* c, const float* h_A, const float* h_B, int M, int 
   if ((e = cudaMemcpyAsync(d_B, h_B, sizeof(float) * K * static_cast<size_t>(N),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "copy B");
-  if ((e = cudaMemcpyAsync(d_mask, h_mask, c->n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  const size_t mask_bytes = (opts && opts->mask_cells) ? static_cast<size_t>(c->num_cells) : static_cast<size_t>(c->n);
+  if ((e = cudaMemcpyAsync(d_mask, h_mask, mask_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "copy mask");
   const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
   int32_t* d_info = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + L.p_info);

@@ -265,6 +265,7 @@ extern "C" bpx_opts bpx_default_opts(void) {
   o.peel_ctas = 0;
   o.gemm_config = 0;
   o.stage_events = nullptr;
+  o.mask_cells = 0;
   return o;
 }
 

@@ -51,10 +51,12 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
 // kSmem: the per-cell unknown counts and per-source depths (the state every
 // round reads and updates) live in shared memory when they fit, else in the
 // plan's global arrays.
+// cell_mask: the mask has one byte per cell (a processor whose output is
+// missing) instead of one per column (a node).
 template <bool kSmem>
 __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& p,
                                               const uint8_t* __restrict__ mask, int32_t* peel_order,
-                                              uint8_t* recovered, int32_t* info_out) {
+                                              uint8_t* recovered, int32_t* info_out, bool cell_mask = false) {
   extern __shared__ int32_t dyn_smem[];
   __shared__ int s_warp[32];
   __shared__ int s_nf, s_nnew, s_nnext;
@@ -64,7 +66,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   int32_t* depth = kSmem ? dyn_smem + g.num_cells : p.depth;
 
   for (int c = tid; c < g.num_cells; c += nt) {
-    const bool alive = mask[g.col_of_cell[c]] == 0;
+    const bool alive = (cell_mask ? mask[c] : mask[g.col_of_cell[c]]) == 0;
     cnt[c] = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
     p.direct[c] = -1;
   }
@@ -253,8 +255,8 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
 template <bool kSmem>
 __global__ void __launch_bounds__(kThreads, 1)
 schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
-                uint8_t* recovered, int32_t* info_out) {
-  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out);
+                uint8_t* recovered, int32_t* info_out, bool cell_mask) {
+  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out, cell_mask);
 }
 
 // Grouped launch: CTA j plans job j.
@@ -282,15 +284,15 @@ cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_stat
 
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool cell_mask) {
   const size_t smem = (static_cast<size_t>(g.num_cells) + g.S) * sizeof(int32_t);
   if (smem <= kSmemStateMax) {
     cudaError_t e = cudaFuncSetAttribute(schedule_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemStateMax));
     if (e != cudaSuccess) return e;
-    schedule_kernel<true><<<1, kThreads, smem, st>>>(g, p, mask, peel_order, recovered, info_out);
+    schedule_kernel<true><<<1, kThreads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask);
   } else {
-    schedule_kernel<false><<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out);
+    schedule_kernel<false><<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask);
   }
   return cudaGetLastError();
 }

@@ -64,6 +64,12 @@ def all_masks(n: int, max_e: int):
             yield mask_from_columns(n, cols)
 
 
+def exponential_draws(n: int, mu: float, seed: int) -> np.ndarray:
+    """n iid Exp(mu) draws (seeded): the unit-work task times of n processors
+    before the straggler model scales them."""
+    return rng(seed).exponential(1.0 / mu, size=n)
+
+
 def matrix(shape, dist: str, seed: int) -> np.ndarray:
     """FP32 matrix with iid entries: 'uniform' U(-1,1), 'normal' N(0,1),
     'loguniform' |x| log-uniform on [1e-3, 1e3] with random signs,

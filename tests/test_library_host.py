@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from oracle import bpx_oracle as o
@@ -146,3 +148,42 @@ def test_terms_2d_match_oracle(libbpx):
     assert bpx.terms_2d(bpx.Code.table3())[1]["gray"] == 6
     code = bpx.Code.systematic(8, 3, 8)
     assert bpx.lib().bpx_workspace_bytes_2d(code.handle, 8192, 8192, 8192, 1024, bpx.BF16X3) > 0
+
+
+def test_first_decodable_matches_oracle(libbpx):
+    """The library's online peel over arriving cells (C++) gives the oracle's
+    first decodable prefix and the same number of recovered sources after
+    every arrival."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    cases = [(bpx.Code.table1(), o.table1()), (bpx.Code.table3(), o.table3()),
+             (bpx.Code.systematic(6, 3, 4), o.systematic_mojette(6, 3, 4)),
+             (bpx.Code.mojette_a(7, 4, 5), o.construction_a(7, 4, 5))]
+    rng = np.random.default_rng(4)
+    for code, ref in cases:
+        for _ in range(10):
+            order = rng.permutation(code.num_cells).astype(np.int32)
+            first, rec = bpx.first_decodable(code, order)
+            assert first == o.first_decodable(ref, list(order))
+            for i in range(0, code.num_cells, max(1, code.num_cells // 7)):
+                assert rec[i] == len(o.sequential_peel(ref, list(order[:i + 1])))
+    with pytest.raises(bpx.BpxError):
+        bpx.first_decodable(bpx.Code.table1(), np.array([0, 0], dtype=np.int32))
+
+
+def test_straggler_arrivals_match_brute_force(libbpx):
+    """T_par from the emulator (task times sigma_c X_c, first decodable
+    arrival prefix) equals the oracle's brute-force min over decodable sets
+    of the latest arrival, for the same draws."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    from paper_1904_11563_gb300 import straggler as st
+    from paper_1904_11563_gb300 import workloads as W
+    for code, ref in [(bpx.Code.table1(), o.table1()), (bpx.Code.table3(), o.table3())]:
+        for seed in range(6):
+            X = W.exponential_draws(code.num_cells, 1.5, seed)
+            T = st.task_times(code, X)
+            _order, first, t_par, _rec = st.arrivals(code, T)
+            Tref = o.task_times(ref, 1.5, None, X=X)
+            assert np.array_equal(T, Tref)
+            assert t_par == o.parallel_task_time_brute(ref, Tref)
