@@ -36,6 +36,8 @@ CODE_TEXT = {
     "mojA_16384": "Mojette Construction A n=32 (k=24 x b=683 grid, q=1, p=-15..16), e=8",
     "sysmoj_8192_2d": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, slopes 0,+1,-1) "
                       "in the two-dimensional scheme (source (z, l) = A_z B_l, 1024 x 1024 blocks)",
+    "sysmoj_8192_straggler": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, "
+                             "slopes 0,+1,-1); processor-level stragglers, task times sigma_c X_c, X_c ~ Exp(1)",
     "batch512": "512 jobs: half array codes (Table I, Table III, systematic Mojette n=6..32, e=2..3), "
                 "half Construction A (n=6..32, e=n//4); each job its own seeded mask",
 }
@@ -748,6 +750,94 @@ def run_2d(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_straggler(args, wl):
+    """Processor-level stragglers (Section IV): every step draws the cells'
+    task times, finds the first decodable arrival set (online peel on the
+    host) and runs the whole GPU path on exactly those cells (cell-level
+    mask).  value = useful 2MNK / GPU step time; the model's parallel task
+    time T_par = min over decodable sets of the latest arrival is reported
+    beside it (units of 1 / mu)."""
+    import torch
+    from paper_1904_11563_gb300 import build as B_
+    B_.build()
+    from paper_1904_11563_gb300 import bpx
+    from paper_1904_11563_gb300 import straggler as st
+    from paper_1904_11563_gb300 import workloads as W
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    code = _lib_code(bpx, wl)
+    M, N, K, h = wl["M"], wl["N"], wl["K"], wl["h"]
+    A, Bm = W.device_inputs(M, K, N, wl["dist"], wl["seed"], device=str(dev))
+    prec = args.precision if args.precision in ("bf16", "bf16x3", "fp32", "exact") else "bf16x3"
+    P = bpx.PRECISIONS[prec]
+    ws = bpx.Workspace(code, M, N, K, h, P, device=dev)
+    C = bpx.alloc_C(code, h, N, dev)
+    info = torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device=dev)
+    warm, steps = max(args.warmup, 3), args.steps
+    plans = []
+    for i in range(warm + steps):
+        X = W.exponential_draws(code.num_cells, wl["mu"], wl["mask_seed_base"] + i)
+        T = st.task_times(code, X)
+        order, first, t_par, _rec = st.arrivals(code, T)
+        mask = np.ones(code.num_cells, dtype=np.uint8)
+        mask[order[:first]] = 0
+        plans.append(dict(mask=torch.from_numpy(mask).to(dev), first=first, t_par=t_par))
+    col_of = np.repeat(np.arange(code.n), np.diff(code.col_ptr))
+    o_ = bpx.default_opts(mask_cells=1)
+    for i in range(warm):
+        bpx.coded_matmul(code, A, Bm, h, P, plans[i]["mask"], ws, C=C, opts=o_, info=info)
+    torch.cuda.synchronize()
+    sev = StageEvents(bpx, steps)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for i in range(steps):
+        oi = bpx.default_opts(mask_cells=1)
+        oi.stage_events = sev.ptr(i)
+        bpx.coded_matmul(code, A, Bm, h, P, plans[warm + i]["mask"], ws, C=C, opts=oi, info=info)
+    t1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1) / steps
+    assert int(info[bpx.INFO_STATUS].item()) == bpx.OK
+    stage = {}
+    for si, nm in enumerate(bpx.STAGE_NAMES):
+        vals = [v for v in (sev.stage_ms(i, si) for i in range(steps)) if v]
+        if vals:
+            stage[nm] = sum(vals) / len(vals)
+    timed = plans[warm:]
+    useful = 2.0 * M * N * K
+    rows = [int((p_["mask"] == 0).sum().item()) * h for p_ in timed]
+    mult = {"bf16x3": 3, "bf16": 1, "fp32": 1}.get(prec)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    roof = None
+    if mult and prec != "fp32":
+        ach = 2.0 * float(np.mean(rows)) * N * K * mult / (stage["gemm"] * 1e-3) / 1e12
+        pk = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel": "coded tcgen05 GEMM"}
+    H = sum(1.0 / j for j in range(1, code.num_cells + 1))
+    line = {"metric": METRIC, "value": useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": wl["name"], "code": CODE_TEXT[wl["name"]], "M": M, "N": N, "K": K, "h": h,
+                       "mu": wl["mu"], "task_time_seeds": "%d + step" % wl["mask_seed_base"],
+                       "inputs": "A, B iid N(0,1) FP32, seeded", "l2": "inputs larger than L2"},
+            "stages_ms": stage,
+            "model": {"t_par_mean": float(np.mean([p_["t_par"] for p_ in timed])),
+                      "arrivals_to_decode_mean": float(np.mean([p_["first"] for p_ in timed])),
+                      "cells": code.num_cells,
+                      "t_all_cells_expected_unscaled": H / wl["mu"],
+                      "units": "1 / mu; T_c = sigma_c X_c"},
+            "computed_cells_mean": float(np.mean(rows)) / h,
+            "roofline": roof, "clocks": ck, "gpu_launches": 5 * steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     from paper_1904_11563_gb300 import workloads as W
@@ -759,6 +849,8 @@ def main():
         run_batch(args)
     elif wl.get("twod") and args.impl != "reference":
         run_2d(args, wl)
+    elif wl.get("straggler") and args.impl != "reference":
+        run_straggler(args, wl)
     elif args.impl == "reference":
         if wl.get("twod"):
             raise SystemExit("--impl reference times the one-dimensional workloads only")

@@ -32,6 +32,12 @@ WORKLOADS = {
     "table3_logu": dict(code=("table3",), h=64, M=576, K=256, N=128, dist="loguniform", seed=3, e=2),
     "mojA_16384": dict(code=("mojette_a", 32, 24, 683), h=1, M=16384, K=16384, N=8192,
                        dist="uniform", seed=4, e=8, mask_seed_base=4000),
+    # the benchmark workload with processor-level stragglers: every step draws
+    # each cell's task time sigma_c X_c, X_c ~ Exp(mu = 1) (seed 5000 + step),
+    # and decodes from the first decodable set of arrived products
+    "sysmoj_8192_straggler": dict(code=("systematic", 8, 3, 8), h=128, M=8192, K=8192, N=8192,
+                                  dist="normal", seed=2, e=0, trials=100, mask_seed_base=5000, mu=1.0,
+                                  straggler=True),
     # the benchmark code in the paper's two-dimensional scheme: 8 x 8 output
     # blocks of 1024 x 1024 (A in 8 row blocks, B in 8 column blocks)
     "sysmoj_8192_2d": dict(code=("systematic", 8, 3, 8), h=1024, M=8192, K=8192, N=8192,
