@@ -148,14 +148,24 @@ cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, flo
                         int first_wave, int compensate_depth, int ctas, cudaStream_t st) {
   const long long nv = static_cast<long long>(h) * N / 4;
   if (nv <= 0) return cudaSuccess;
-  const long long chunk = peel_chunk_for(nv, ctas);
-  const long long grid = (nv + chunk - 1) / chunk;
-  const unsigned gr = static_cast<unsigned>(grid);
-  const int ck = static_cast<int>(chunk);
+  // Every CTA walks every wave, so the grid never exceeds the CTAs that can
+  // be resident at once (a CTA waiting for a slot would repeat the chain).
+  auto launch = [&](auto kern) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPeelThreads, 0) != cudaSuccess || per_sm <= 0) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    long long chunk = peel_chunk_for(nv, ctas);
+    const long long slots = static_cast<long long>(per_sm) * num_sms();
+    if ((nv + chunk - 1) / chunk > slots) chunk = (nv + slots - 1) / slots;
+    const unsigned grid = static_cast<unsigned>((nv + chunk - 1) / chunk);
+    kern<<<grid, kPeelThreads, 0, st>>>(p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);
+  };
   switch (batch_for(g.sigma)) {
-    case 4: peel_kernel<4><<<gr, kPeelThreads, 0, st>>>(p, P, C, nv, ck, first_wave, compensate_depth); break;
-    case 8: peel_kernel<8><<<gr, kPeelThreads, 0, st>>>(p, P, C, nv, ck, first_wave, compensate_depth); break;
-    default: peel_kernel<16><<<gr, kPeelThreads, 0, st>>>(p, P, C, nv, ck, first_wave, compensate_depth);
+    case 4: launch(peel_kernel<4>); break;
+    case 8: launch(peel_kernel<8>); break;
+    default: launch(peel_kernel<16>);
   }
   return cudaGetLastError();
 }

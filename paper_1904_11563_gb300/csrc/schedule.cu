@@ -59,7 +59,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
                                               uint8_t* recovered, int32_t* info_out, bool cell_mask = false) {
   extern __shared__ int32_t dyn_smem[];
   __shared__ int s_warp[32];
-  __shared__ int s_nf, s_nnew, s_nnext;
+  __shared__ int s_nf, s_new[2], s_next[2];  // per-round counters, by round parity
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   int32_t* cnt = kSmem ? dyn_smem : p.cnt;
@@ -76,6 +76,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   }
   if (tid == 0) {
     s_nf = 0;
+    s_new[0] = s_new[1] = s_next[0] = s_next[1] = 0;
     p.wave_ptr[0] = 0;
   }
   __syncthreads();
@@ -98,12 +99,17 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   int32_t* fr = p.front0;
   int32_t* nx = p.front1;
   int round = 0, nrec = 0;
-  while (true) {
-    const int nf = s_nf;
-    if (nf == 0) break;
+  int nf = s_nf;
+  // Two barriers per round.  Counters of round r live at parity r & 1 and the
+  // other parity is cleared during round r, after every thread has read it.
+  while (nf > 0) {
     ++round;
-    // A: one warp per ready cell: the lanes scan its support together and
-    // the single unknown source is named; the lowest cell id wins it.
+    const int q = round & 1;
+    // A: one warp per ready cell (exactly one unknown source at the start of
+    // the round): the lanes scan its support together for that source -- one
+    // with depth 0, or depth == round if another cell of this round has
+    // already claimed it -- the lowest cell id becomes its resolver, and the
+    // first claim records it as recovered in this round.
     for (int i = warp; i < nf; i += nwarps) {
       const int c = fr[i];
       int found = -1;
@@ -112,37 +118,33 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
         for (int base = e0; base < e1; base += 32) {
           const int e = base + lane;
           const int t = e < e1 ? g.cell_src[e] : -1;
-          const unsigned m = __ballot_sync(0xffffffffu, t >= 0 && depth[t] == 0);
+          int dt = 0;
+          if (t >= 0) dt = depth[t];
+          const unsigned m = __ballot_sync(0xffffffffu, t >= 0 && (dt == 0 || dt == round));
           if (m) {
             found = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
             break;
           }
         }
       }
-      if (lane == 0) {
-        if (found >= 0) atomicMin(&p.resolver[found], c);
-        p.cand[i] = found;
+      if (lane == 0 && found >= 0) {
+        atomicMin(&p.resolver[found], c);
+        if (atomicCAS(&depth[found], 0, round) == 0) p.newsrc[atomicAdd(&s_new[q], 1)] = found;
       }
     }
-    if (tid == 0) {
-      s_nnew = 0;
-      s_nnext = 0;
-    }
     __syncthreads();
-    // B: mark the named sources recovered in this round (once each).
-    for (int i = tid; i < nf; i += nt) {
-      const int s = p.cand[i];
-      if (s >= 0 && atomicCAS(&depth[s], 0, round) == 0) p.newsrc[atomicAdd(&s_nnew, 1)] = s;
-    }
-    __syncthreads();
-    const int nnew = s_nnew;
+    const int nnew = s_new[q];
     if (nnew == 0) {
       --round;
       break;
     }
     nrec += nnew;
-    if (tid == 0) p.wave_ptr[round] = nrec;
-    // C: one warp per recovered source drops it from its cells; a cell whose
+    if (tid == 0) {
+      p.wave_ptr[round] = nrec;
+      s_new[q ^ 1] = 0;
+      s_next[q ^ 1] = 0;
+    }
+    // B: one warp per recovered source drops it from its cells; a cell whose
     // unknown count reaches one joins the next ready queue.
     for (int j = warp; j < nnew; j += nwarps) {
       const int s = p.newsrc[j];
@@ -151,16 +153,15 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
         const int c = g.src_cell[e];
         if (cnt[c] >= 0) {
           const int old = atomicSub(&cnt[c], 1);
-          if (old == 2) nx[atomicAdd(&s_nnext, 1)] = c;
+          if (old == 2) nx[atomicAdd(&s_next[q], 1)] = c;
         }
       }
     }
     __syncthreads();
-    if (tid == 0) s_nf = s_nnext;
+    nf = s_next[q];
     int32_t* tmp = fr;
     fr = nx;
     nx = tmp;
-    __syncthreads();
   }
 
   // Place the recovered sources in (depth, source) order: one warp walks the
