@@ -59,8 +59,9 @@ enum bpx_variant {
                          projection parities (q=1, slopes 0,+1,-1,+2,...), n = k + e */
   BPX_MOJETTE_A = 3,  /* Construction A (Cons33): n projections q=1,
                          p = -floor((n-1)/2)..ceil((n-1)/2) of the k x b grid; e = n - k */
-  BPX_MOJETTE_B = 4   /* Construction B (cons35): n projections q=2^q_e, p = n consecutive
+  BPX_MOJETTE_B = 4,  /* Construction B (cons35): n projections q=2^q_e, p = n consecutive
                          odd integers from ceil_odd(1-n); e = n - ceil(k / 2^q_e) */
+  BPX_LITERAL = 5     /* a code given by its cells (bpx_code_from_cells, bpx_code_search) */
 };
 
 /* Arithmetic of the coded products.  FP32 accumulation in every case. */
@@ -158,6 +159,43 @@ void bpx_code_free(bpx_code* code);
 
 /* Thread-local text of the last error raised on this thread. */
 const char* bpx_last_error(void);
+
+/* ---------------------------------------------------------------- code-parameter tooling
+ * Host only (no GPU needed). */
+
+/* Bounds on the number of columns n of an array BP-XOR code with k data
+ * columns, b rows and largest cell degree sigma (Section III-B):
+ *   bpx_bound_k_equals_sigma: n <= kb + 1 + max{k - 3, 0} when k = sigma
+ *     (quoted from Paterson et al.; Table I meets it with equality);
+ *   bpx_bound_paterson (k > sigma): n <= k + sigma - 1 + floor(sigma
+ *     (sigma - 1)(b - 1) / ((k - sigma) b + sigma - 1)) -- the straggler
+ *     count n - k the paper's Section V simulations use (Table III meets it);
+ *   bpx_bound_theorem31: Theorem 3.1 for an asymptotically MDS code with
+ *     worst-case overhead eps: n <= floor(((kb + sigma - 1)(k - 1) -
+ *     (sigma - 1)(sigma/2 - 1)) / (b (k - sigma') + sigma - 1)), sigma' =
+ *     sigma (1 + eps); BPX_ERR_INVAL when the denominator is not positive. */
+int bpx_bound_k_equals_sigma(int k, int b, int* n_max);
+int bpx_bound_paterson(int k, int b, int sigma, int* n_max);
+int bpx_bound_theorem31(int k, int b, int sigma, double eps, int* n_max);
+
+/* A code given by its cells (variant BPX_LITERAL): num_cells cells grouped by
+ * ascending column (col_of_cell[c] in [0, n)), cell c's support =
+ * cell_src[cell_ptr[c] .. cell_ptr[c+1]) ascending, source ids in [0, b k)
+ * (pixel (z, l) of the grid is z k + l).  e = the column erasures the code is
+ * meant to tolerate (recorded, not checked).  The arrays are copied. */
+int bpx_code_from_cells(int n, int k, int b, int num_cells, const int32_t* col_of_cell, const int32_t* cell_ptr,
+                        const int32_t* cell_src, int e, bpx_code** out);
+
+/* Searches for an equal-height array BP-XOR code: n columns of b cells, every
+ * cell the sum of at most sigma of the b k sources, decodable by peeling from
+ * every set of k columns (e = n - k).  Simulated annealing over the cells'
+ * supports (cost: the erasure patterns that do not peel, plus sources in fewer
+ * than n - k + 1 columns), at most `iters` moves from `seed`.  b k <= 64,
+ * n <= 30.  *out receives the code (BPX_LITERAL) or NULL with
+ * BPX_ERR_UNSUPPORTED when none was found; *iters_used (or NULL) the moves
+ * taken. */
+int bpx_code_search(int n, int k, int b, int sigma, long long iters, unsigned long long seed, bpx_code** out,
+                    long long* iters_used);
 
 /* ---------------------------------------------------------------- workspace */
 

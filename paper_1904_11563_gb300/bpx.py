@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbpx.so")
 
 # enums of bpx.h
-TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B = 0, 1, 2, 3, 4
+TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B, LITERAL = 0, 1, 2, 3, 4, 5
 FP32, BF16, BF16X3, MXFP8, EXACT = 0, 1, 2, 3, 4
 OK, ERR_INVAL, ERR_UNSUPPORTED, ERR_UNDECODABLE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(7)
 INFO_STATUS, INFO_RECOVERED, INFO_WAVES, INFO_SURVIVING, INFO_DIRECT, INFO_DEVICE_ERR = range(6)
@@ -97,6 +97,12 @@ def lib():
         "bpx_schedule_noalloc": (i, [vp, vp, vp, vp, vp, vp]),
         "bpx_schedule_cells": (i, [vp, vp, vp, sz, vp, vp, vp, vp]),
         "bpx_first_decodable": (i, [vp, vp, i, vp, vp]),
+        "bpx_bound_k_equals_sigma": (i, [i, i, ct.POINTER(ct.c_int)]),
+        "bpx_bound_paterson": (i, [i, i, i, ct.POINTER(ct.c_int)]),
+        "bpx_bound_theorem31": (i, [i, i, i, ct.c_double, ct.POINTER(ct.c_int)]),
+        "bpx_code_from_cells": (i, [i, i, i, i, vp, vp, vp, i, ct.POINTER(vp)]),
+        "bpx_code_search": (i, [i, i, i, i, ct.c_longlong, ct.c_ulonglong, ct.POINTER(vp),
+                                ct.POINTER(ct.c_longlong)]),
         "bpx_terms_2d": (i, [vp, vp, vp]),
         "bpx_workspace_bytes_2d": (sz, [vp, i, i, i, i, i]),
         "bpx_coded_matmul_2d": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
@@ -139,10 +145,13 @@ def default_opts(**kw) -> Opts:
 class Code:
     """A code graph built by the library (bpx_code_build)."""
 
-    def __init__(self, variant, n, k, b, e=-1, q_e=0):
+    def __init__(self, variant, n, k, b, e=-1, q_e=0, handle=None):
         self._h = None
         h = ct.c_void_p()
-        _check(lib().bpx_code_build(variant, n, k, e, b, q_e, ct.byref(h)))
+        if handle is not None:
+            h = handle
+        else:
+            _check(lib().bpx_code_build(variant, n, k, e, b, q_e, ct.byref(h)))
         self._h = h
         info = _CodeInfo()
         _check(lib().bpx_code_info_get(h, ct.byref(info)))
@@ -196,6 +205,37 @@ class Code:
     @classmethod
     def mojette_b(cls, n, k, b, q_e):
         return cls(MOJETTE_B, n, k, b, q_e=q_e)
+
+    @classmethod
+    def from_columns(cls, n, k, b, columns, e):
+        """A code given by its columns, each a list of cells (source tuples)."""
+        col_of, ptr, src = [], [0], []
+        for j, col in enumerate(columns):
+            for cell in col:
+                col_of.append(j)
+                src.extend(sorted(cell))
+                ptr.append(len(src))
+        a = [np.ascontiguousarray(x, dtype=np.int32) for x in (col_of, ptr, src)]
+        h = ct.c_void_p()
+        _check(lib().bpx_code_from_cells(n, k, b, len(col_of), *(x.ctypes.data_as(ct.c_void_p) for x in a), e,
+                                         ct.byref(h)))
+        return cls(LITERAL, n, k, b, handle=h)
+
+    @classmethod
+    def search(cls, n, k, b, sigma, iters=200000, seed=0):
+        """Equal-height array BP-XOR code search; (code or None, moves taken)."""
+        h = ct.c_void_p()
+        used = ct.c_longlong()
+        rc = lib().bpx_code_search(n, k, b, sigma, iters, seed, ct.byref(h), ct.byref(used))
+        if rc == ERR_UNSUPPORTED:
+            return None, used.value
+        _check(rc)
+        return cls(LITERAL, n, k, b, handle=h), used.value
+
+    def columns(self):
+        """Cells grouped by column (source tuples)."""
+        cells = self.cells
+        return [[cells[c] for c in range(self.col_ptr[j], self.col_ptr[j + 1])] for j in range(self.n)]
 
 
 def workspace_bytes(code: Code, M, N, K, h, precision) -> int:
@@ -276,6 +316,19 @@ def peel_decode(code: Code, products, N, h, C, ws: Workspace, direct_written=Fal
     _check(lib().bpx_peel_decode(code.handle, _ptr(products), N, h, _ptr(C), int(direct_written),
                                  ct.byref(opts) if opts is not None else None, ws.ptr, _stream()))
     return C
+
+
+def bound(kind, k, b, sigma=None, eps=0.0) -> int:
+    """Bounds on n (host only): kind 'k_equals_sigma', 'paterson' or
+    'theorem31'."""
+    out = ct.c_int()
+    if kind == "k_equals_sigma":
+        _check(lib().bpx_bound_k_equals_sigma(k, b, ct.byref(out)))
+    elif kind == "paterson":
+        _check(lib().bpx_bound_paterson(k, b, sigma, ct.byref(out)))
+    else:
+        _check(lib().bpx_bound_theorem31(k, b, sigma, eps, ct.byref(out)))
+    return out.value
 
 
 def first_decodable(code: Code, order):

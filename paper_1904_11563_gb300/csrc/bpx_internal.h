@@ -73,6 +73,14 @@ int exact_params(const bpx_code* c, int K, ExactParams* P);
 // staging holds the summed A and B operands of the code's factored cells).
 WsLayout ws_layout(const bpx_code* code, int M, int N, int K, int h, int precision, bool twod = false);
 
+// Completes a code from its cells (supports ascending) and the column of
+// each cell (grouped by ascending column): CSR views, source -> cells,
+// sigma, the worst-case overhead, the two-dimensional factoring.  c->n, k,
+// b, S and e must be set; col_ptr / heights / projections are derived when
+// empty.
+void finish_code(bpx_code* c, const std::vector<std::vector<int32_t>>& cells,
+                 const std::vector<int32_t>& col_of_cell);
+
 // Factors every cell for the two-dimensional scheme (fills the t2_* / a2_* /
 // b2_* arrays of the code).
 void build_terms_2d(bpx_code* c);

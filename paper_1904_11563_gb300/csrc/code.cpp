@@ -32,6 +32,54 @@ void clear_error() { g_last_error.clear(); }
 
 using bpx::fail;
 
+namespace bpx {
+
+void finish_code(bpx_code* c, const std::vector<std::vector<int32_t>>& cells,
+                 const std::vector<int32_t>& col_of_cell) {
+  c->col_of_cell = col_of_cell;
+  if (c->col_ptr.empty()) {  // columns given only through col_of_cell
+    c->col_ptr.assign(c->n + 1, 0);
+    for (int32_t j : col_of_cell) ++c->col_ptr[j + 1];
+    for (int j = 0; j < c->n; ++j) c->col_ptr[j + 1] += c->col_ptr[j];
+  }
+  if (c->heights.empty())
+    for (int j = 0; j < c->n; ++j) c->heights.push_back(c->col_ptr[j + 1] - c->col_ptr[j]);
+  if (c->proj_p.empty()) {
+    c->proj_p.assign(c->n, 0);
+    c->proj_q.assign(c->n, 0);
+  }
+  c->num_cells = static_cast<int>(cells.size());
+  c->cell_ptr.assign(1, 0);
+  c->cell_src.clear();
+  c->sigma = 0;
+  for (auto& s : cells) {
+    c->cell_src.insert(c->cell_src.end(), s.begin(), s.end());
+    c->cell_ptr.push_back(static_cast<int32_t>(c->cell_src.size()));
+    c->sigma = std::max(c->sigma, static_cast<int>(s.size()));
+  }
+  c->num_edges = static_cast<int>(c->cell_src.size());
+  // source -> cells, cells ascending
+  std::vector<int32_t> deg(c->S + 1, 0);
+  for (int32_t s : c->cell_src) ++deg[s + 1];
+  c->src_ptr.assign(c->S + 1, 0);
+  for (int s = 0; s < c->S; ++s) c->src_ptr[s + 1] = c->src_ptr[s] + deg[s + 1];
+  c->src_cell.assign(c->num_edges, 0);
+  std::vector<int32_t> fill(c->src_ptr.begin(), c->src_ptr.end() - 1);
+  for (int cell = 0; cell < c->num_cells; ++cell)
+    for (int i = c->cell_ptr[cell]; i < c->cell_ptr[cell + 1]; ++i)
+      c->src_cell[fill[c->cell_src[i]]++] = cell;
+  // Worst-case overhead (Section III-B): the tallest n - e columns, i.e.
+  // the tallest set of columns that still has to decode.
+  std::vector<int32_t> hs(c->heights);
+  std::sort(hs.begin(), hs.end(), [](int a, int b) { return a > b; });
+  long long tot = 0;
+  for (int j = 0; j < c->n - c->e; ++j) tot += hs[j];
+  c->eps = static_cast<double>(tot) / (static_cast<double>(c->k) * c->b) - 1.0;
+  build_terms_2d(c);
+}
+
+}  // namespace bpx
+
 namespace {
 
 constexpr int kMaxSources = 1 << 24;
@@ -94,32 +142,7 @@ struct Builder {
 
   void finish() {
     c->col_ptr.push_back(static_cast<int32_t>(cells.size()));
-    c->num_cells = static_cast<int>(cells.size());
-    c->cell_ptr.assign(1, 0);
-    c->sigma = 0;
-    for (auto& s : cells) {
-      c->cell_src.insert(c->cell_src.end(), s.begin(), s.end());
-      c->cell_ptr.push_back(static_cast<int32_t>(c->cell_src.size()));
-      c->sigma = std::max(c->sigma, static_cast<int>(s.size()));
-    }
-    c->num_edges = static_cast<int>(c->cell_src.size());
-    // source -> cells, cells ascending
-    std::vector<int32_t> deg(c->S + 1, 0);
-    for (int32_t s : c->cell_src) ++deg[s + 1];
-    c->src_ptr.assign(c->S + 1, 0);
-    for (int s = 0; s < c->S; ++s) c->src_ptr[s + 1] = c->src_ptr[s] + deg[s + 1];
-    c->src_cell.assign(c->num_edges, 0);
-    std::vector<int32_t> fill(c->src_ptr.begin(), c->src_ptr.end() - 1);
-    for (int cell = 0; cell < c->num_cells; ++cell)
-      for (int i = c->cell_ptr[cell]; i < c->cell_ptr[cell + 1]; ++i)
-        c->src_cell[fill[c->cell_src[i]]++] = cell;
-    // Worst-case overhead (Section III-B): the tallest n - e columns, i.e.
-    // the tallest set of columns that still has to decode.
-    std::vector<int32_t> hs(c->heights);
-    std::sort(hs.begin(), hs.end(), [](int a, int b) { return a > b; });
-    long long tot = 0;
-    for (int j = 0; j < c->n - c->e; ++j) tot += hs[j];
-    c->eps = static_cast<double>(tot) / (static_cast<double>(c->k) * c->b) - 1.0;
+    bpx::finish_code(c, cells, c->col_of_cell);
   }
 };
 
@@ -226,7 +249,6 @@ extern "C" int bpx_code_build(int variant, int n, int k, int e, int b, int q_e, 
   }
   c->e = derived_e;
   B.finish();
-  bpx::build_terms_2d(c);
   *out = c;
   return BPX_OK;
 }

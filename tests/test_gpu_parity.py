@@ -491,3 +491,28 @@ def test_mxfp8_many_tiles(libbpx):
     assert info[bpx.INFO_STATUS] == bpx.OK
     R, sch = _oracle_decode(ref, A, B, h, m)
     _check_blocks(C, R, ref, A, B, h, m, "mxfp8")
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "exact"])
+def test_searched_code_on_the_gpu(libbpx, prec):
+    """A code found by the library's search (a [5,3,2,4] array BP-XOR code
+    with sigma = 2, meeting the straggler bound) runs through the whole GPU
+    path: every pattern of two erased columns within tolerance of the
+    oracle (bit-exact for exact slices)."""
+    bpx = libbpx
+    code, _ = bpx.Code.search(5, 3, 4, 2, iters=2000000, seed=5)
+    assert code is not None
+    ref = o.code_from_columns("found", 3, 4, code.columns())
+    h, K, N = 24, 136, 68
+    M = ref.num_sources * h
+    A, B = W.inputs(M, K, N, "normal", 91)
+    for m in _masks(ref, 2):
+        er = list(np.nonzero(m)[0])
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        if prec == "exact":
+            R, _Q, _s = o.exact_slice_coded_matmul(ref, A, B, h, er)
+            assert np.array_equal(C[:M].view(np.uint32), R[:M].view(np.uint32))
+        else:
+            R, _s = _oracle_decode(ref, A, B, h, m)
+            _check_blocks(C, R, ref, A, B, h, m, prec)

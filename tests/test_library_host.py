@@ -187,3 +187,47 @@ def test_straggler_arrivals_match_brute_force(libbpx):
             Tref = o.task_times(ref, 1.5, None, X=X)
             assert np.array_equal(T, Tref)
             assert t_par == o.parallel_task_time_brute(ref, Tref)
+
+
+def test_bounds_match_oracle(libbpx):
+    """The library's bounds on n equal the oracle's, and Tables I / III meet
+    them with equality."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    for k in range(2, 12):
+        for b in (1, 2, 3, 8, 64):
+            assert bpx.bound("k_equals_sigma", k, b) == o.bound_k_equals_sigma(k, b)
+            for s in range(1, k):
+                assert bpx.bound("paterson", k, b, s) == o.bound_paterson(k, b, s)
+                for eps in (0.0, 0.1, 0.5):
+                    try:
+                        want = o.bound_theorem31(k, b, s, eps)
+                    except ValueError:
+                        with pytest.raises(bpx.BpxError):
+                            bpx.bound("theorem31", k, b, s, eps)
+                        continue
+                    assert bpx.bound("theorem31", k, b, s, eps) == want
+    assert bpx.bound("k_equals_sigma", 2, 2) == 5 == bpx.Code.table1().n
+    assert bpx.bound("paterson", 3, 3, 2) == 5 == bpx.Code.table3().n
+
+
+def test_code_from_columns_and_search(libbpx):
+    """A code given by its cells builds the same graph as the literal table;
+    the search finds array BP-XOR codes the oracle verifies by brute force
+    for parameters the bounds allow (incl. ones meeting them), and none where
+    the k = sigma bound rules them out."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    t1 = bpx.Code.table1()
+    c = bpx.Code.from_columns(5, 2, 2, t1.columns(), e=3)
+    assert c.cells == t1.cells and list(c.col_ptr) == list(t1.col_ptr) and c.sigma == 2
+    for n, k, b, s in [(5, 2, 2, 2), (5, 3, 3, 2), (5, 3, 4, 2), (4, 2, 4, 2)]:
+        code, used = bpx.Code.search(n, k, b, s, iters=2000000, seed=5)
+        assert code is not None, (n, k, b, s, used)
+        assert code.sigma <= s and code.e == n - k
+        assert o.is_array_bpxor(o.code_from_columns("found", k, b, code.columns()))
+    assert bpx.bound("k_equals_sigma", 2, 2) < 6
+    code, used = bpx.Code.search(6, 2, 2, 2, iters=200000, seed=1)
+    assert code is None and used == 200000
+    with pytest.raises(bpx.BpxError):
+        bpx.Code.from_columns(2, 1, 1, [[(0,)], [(1,)]], e=1)     # source 1 out of range
