@@ -176,11 +176,16 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
   const int config = opts ? opts->gemm_config : 0;
   cudaError_t e = cudaSuccess;
   switch (precision) {
-    case BPX_FP32:
+    case BPX_FP32: {
+      float* a_coded = reinterpret_cast<float*>(base + L.a_hi);
+      stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
+      e = bpx::launch_encode_f32(g, p, d_A, M, K, h, a_coded, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
       stage_mark(opts, BPX_STAGE_GEMM, 0, st);
-      e = bpx::launch_gemm_f32(g, p, d_A, d_B, M, N, K, h, d_products, d_C, st);
+      if (e == cudaSuccess) e = bpx::launch_gemm_f32(g, p, a_coded, d_B, N, K, h, d_products, d_C, st);
       stage_mark(opts, BPX_STAGE_GEMM, 1, st);
       break;
+    }
     case BPX_BF16:
     case BPX_BF16X3: {
       const bool split = precision == BPX_BF16X3;

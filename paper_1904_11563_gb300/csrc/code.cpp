@@ -395,7 +395,9 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision,
   const size_t rowsA = C * static_cast<size_t>(h > 0 ? h : 0);
   const size_t Kp = static_cast<size_t>(K > 0 ? K : 0), Np = static_cast<size_t>(N > 0 ? N : 0);
   L.a_hi = L.a_lo = L.b_hi = L.b_lo = L.a_scale = L.b_scale = off;
-  if (precision == BPX_BF16 || precision == BPX_BF16X3) {
+  if (precision == BPX_FP32) {
+    L.a_hi = take(rowsA * Kp * 4);  // FP32 coded rows for the CUDA-core GEMM
+  } else if (precision == BPX_BF16 || precision == BPX_BF16X3) {
     L.a_hi = take(rowsA * Kp * 2);
     L.b_hi = take(Np * Kp * 2);
     if (precision == BPX_BF16X3) {

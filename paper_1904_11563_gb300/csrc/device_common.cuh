@@ -202,9 +202,9 @@ cudaError_t launch_b_mx(const float* B, int K, int N, void* bt, void* sfb, cudaS
 cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, const void* b8, const void* sfb,
                            int num_cells, int N, int K, int h, float* products, float* C_direct, int config,
                            int32_t* info_out, cudaStream_t st);
-cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* A, const float* B,
-                            int M, int N, int K, int h, float* products, float* C_direct,
-                            cudaStream_t st);
+// Plain FP32 coded GEMM over the encode pass's FP32 coded rows.
+cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* a_coded, const float* B, int N, int K,
+                            int h, float* products, float* C_direct, cudaStream_t st);
 // Tensor-core coded GEMM over the staged bf16 operands (split or plain).
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
                            const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
