@@ -66,7 +66,7 @@ enum bpx_variant {
 
 /* Arithmetic of the coded products.  FP32 accumulation in every case. */
 enum bpx_precision {
-  BPX_FP32 = 0,   /* plain FP32 FFMA (CUDA cores), encode fused into the operand load */
+  BPX_FP32 = 0,   /* plain FP32 on the CUDA cores (FP32 encode pass, then an FFMA GEMM) */
   BPX_BF16 = 1,   /* coded A and B rounded to bf16, one tcgen05 MMA per k-step */
   BPX_BF16X3 = 2, /* split bf16: a = a_hi + a_lo; hi*hi + hi*lo + lo*hi on tcgen05 */
   BPX_MXFP8 = 3,  /* E4M3 with one UE8M0 scale per 32 K-elements (tcgen05 block-scaled) */
@@ -131,8 +131,8 @@ typedef struct {
 enum bpx_stage {
   BPX_STAGE_SCHEDULE = 0, /* a1 symbolic peel */
   BPX_STAGE_B_PREP = 1,   /* B split / quantize (tensor-core paths) */
-  BPX_STAGE_A_PREP = 2,   /* encode + split / quantize of the coded operand (tensor-core paths) */
-  BPX_STAGE_GEMM = 3,     /* coded products (FP32 path: encode fused here) */
+  BPX_STAGE_A_PREP = 2,   /* encode (+ split / quantize / digit planes) of the coded operand */
+  BPX_STAGE_GEMM = 3,     /* coded products */
   BPX_STAGE_PEEL = 4,     /* a4 numeric peel */
   BPX_NUM_STAGES = 5
 };
@@ -247,7 +247,7 @@ int bpx_encode(const bpx_code* code, const float* d_A, int M, int K, int h, cons
                float* d_A_coded, bpx_stream stream);
 
 /* a3. Coded products (Section III-A): P_c = A_c B for every surviving cell,
- * in the given precision, the encode sums formed on the way into the GEMM.
+ * in the given precision, the encode sums formed by a pass just before the GEMM.
  * P_c goes to d_products + c h N (d_products: num_cells h N floats, row-major
  * h x N per cell), except that with d_C non-NULL the product of each depth-1
  * resolver goes straight to its source block d_C + s h N.  Requires the plan
