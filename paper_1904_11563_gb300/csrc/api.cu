@@ -24,6 +24,11 @@ int num_sms() {
   return sms;
 }
 
+int& reserved_sms() {
+  thread_local int r = 0;
+  return r;
+}
+
 }  // namespace bpx
 
 namespace {
@@ -115,17 +120,57 @@ extern "C" int bpx_workspace_init(const bpx_code* c, void* ws, size_t ws_bytes, 
 namespace {
 
 int schedule_impl(const bpx_code* c, const uint8_t* d_mask, bool cell_mask, void* ws, size_t ws_bytes,
-                  int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, cudaStream_t st) {
+                  int32_t* d_peel_order, uint8_t* d_recovered, int32_t* d_info, cudaStream_t st, int part = 0) {
   if (!c) return fail(BPX_ERR_INVAL, "bpx_schedule: code is NULL");
   const bpx::WsLayout L = bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32);
   if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
   if (!d_mask) return fail(BPX_ERR_INVAL, "bpx_schedule: erasure mask is NULL");
   const bpx::DevGraph g = bpx::make_graph(c, ws, L);
   const bpx::DevPlan p = bpx::make_plan(ws, L);
-  cudaError_t e = bpx::launch_schedule(g, p, d_mask, d_peel_order, d_recovered, d_info, st, cell_mask);
+  cudaError_t e = bpx::launch_schedule(g, p, d_mask, d_peel_order, d_recovered, d_info, st, cell_mask, part);
   if (e != cudaSuccess) return cuda_fail(e, "bpx_schedule: launch");
   return BPX_OK;
 }
+
+// Codes with this many sources plan in hundreds of dependent rounds: the
+// rounds after the first then run on a second stream beside the products
+// (which need only the survivors and the depth-1 map), and the GEMMs leave
+// two SMs free for them.
+constexpr int kOverlapSources = 4096;
+
+// The second stream and the fork / join events of the calling thread.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int device = -1;
+};
+
+SideStream* side_stream() {
+  thread_local SideStream ss;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (ss.s && ss.device == dev) return &ss;
+  if (ss.s) {
+    cudaStreamDestroy(ss.s);
+    cudaEventDestroy(ss.fork);
+    cudaEventDestroy(ss.join);
+    ss.s = nullptr;
+  }
+  if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ss.s = nullptr;
+    return nullptr;
+  }
+  ss.device = dev;
+  return &ss;
+}
+
+struct ReserveGuard {
+  explicit ReserveGuard(int n) { bpx::reserved_sms() = n; }
+  ~ReserveGuard() { bpx::reserved_sms() = 0; }
+};
 
 }  // namespace
 
@@ -397,20 +442,42 @@ extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float
   const bpx_opts o = opts ? *opts : bpx_default_opts();
   const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
   if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
+  SideStream* side = c->S >= kOverlapSources ? side_stream() : nullptr;
   stage_mark(&o, BPX_STAGE_SCHEDULE, 0, S(stream));
-  if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, S(stream)))
-    return rc;
-  stage_mark(&o, BPX_STAGE_SCHEDULE, 1, S(stream));
+  if (!side) {
+    if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, S(stream)))
+      return rc;
+    stage_mark(&o, BPX_STAGE_SCHEDULE, 1, S(stream));
+  } else {
+    // survivors + depth-1 map now; the remaining rounds beside the products
+    if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, S(stream), 1))
+      return rc;
+    cudaError_t e = cudaEventRecord(side->fork, S(stream));
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side->s, side->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "bpx_coded_matmul: fork");
+    if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, side->s, 2))
+      return rc;
+    stage_mark(&o, BPX_STAGE_SCHEDULE, 1, side->s);
+    if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return cuda_fail(e, "bpx_coded_matmul: join");
+  }
   float* products = reinterpret_cast<float*>(static_cast<char*>(ws) + L.products);
+  ReserveGuard reserve(side ? 2 : 0);
+  auto join = [&]() -> int {
+    if (!side) return BPX_OK;
+    const cudaError_t e = cudaStreamWaitEvent(S(stream), side->join, 0);
+    return e == cudaSuccess ? BPX_OK : cuda_fail(e, "bpx_coded_matmul: join");
+  };
   if (precision == BPX_EXACT) {
     if (int rc = products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, products, nullptr, &o, d_info,
                                S(stream)))
       return rc;
+    if (int rc = join()) return rc;
     return peel_exact_impl(c, reinterpret_cast<const int32_t*>(products), N, h, d_C, &o, ws, ws_bytes, S(stream));
   }
   if (int rc = products_impl(c, d_A, d_B, M, N, K, h, precision, ws, ws_bytes, products,
                              o.direct_write ? d_C : nullptr, &o, d_info, S(stream)))
     return rc;
+  if (int rc = join()) return rc;
   return peel_impl(c, products, N, h, d_C, o.direct_write, &o, ws, S(stream));
 }
 

@@ -185,9 +185,14 @@ struct TcSpec {
 cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
                            long long* total_tiles, cudaStream_t st);
 // cell_mask: the mask has one byte per cell instead of one per column.
+// part: 0 = whole plan, 1 = survivors + depth-1 direct map, 2 = the rest.
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
-                            cudaStream_t st, bool cell_mask = false);
+                            cudaStream_t st, bool cell_mask = false, int part = 0);
+
+// SMs the persistent GEMMs leave free (for a schedule running beside them);
+// set by the entry points for the duration of a launch.
+int& reserved_sms();
 cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, float* C, int N, int h,
                         int first_wave, int compensate_depth, int ctas, cudaStream_t st);
 cudaError_t launch_encode_f32(const DevGraph& g, const DevPlan& p, const float* A, int M, int K,

@@ -1021,7 +1021,7 @@ cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, l
   if (e != cudaSuccess) return e;
   if (total_tiles <= 0) return cudaSuccess;
   if (!kPair) {
-    const int grid = static_cast<int>(std::min<long long>(total_tiles, num_sms()));
+    const int grid = static_cast<int>(std::min<long long>(total_tiles, std::max(1, num_sms() - reserved_sms())));
     kern<<<grid, kThreads, smem, st>>>(single, table, njobs, total_tiles, group, seg_kb);
     return cudaGetLastError();
   }
@@ -1043,6 +1043,7 @@ cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, l
     cudaGetLastError();
     resident = num_sms() / 2;
   }
+  resident = std::max(1, resident - (reserved_sms() + 1) / 2);
   const int clusters = static_cast<int>(std::min<long long>(total_tiles, resident));
   cfg.gridDim = dim3(2 * clusters);
   return cudaLaunchKernelEx(&cfg, kern, single, table, njobs, total_tiles, group, seg_kb);
@@ -1338,7 +1339,7 @@ cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, co
     cudaError_t e = cudaFuncSetAttribute(gemm_mx_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    const int grid = static_cast<int>(std::min<long long>(tiles, num_sms()));
+    const int grid = static_cast<int>(std::min<long long>(tiles, std::max(1, num_sms() - reserved_sms())));
     if (grid <= 0) return cudaSuccess;
     gemm_mx_kernel<false><<<grid, kThreads, smem, st>>>(ma, mb, P);
     return cudaGetLastError();
@@ -1364,6 +1365,7 @@ cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, co
     cudaGetLastError();
     resident = num_sms() / 2;
   }
+  resident = std::max(1, resident - (reserved_sms() + 1) / 2);
   const long long pairs = ((P.m_tiles_max + 1) / 2) * static_cast<long long>(P.n_tiles);
   const int clusters = static_cast<int>(std::min<long long>(pairs, resident));
   cfg.gridDim = dim3(2 * clusters);

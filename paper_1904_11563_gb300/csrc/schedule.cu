@@ -53,10 +53,15 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
 // plan's global arrays.
 // cell_mask: the mask has one byte per cell (a processor whose output is
 // missing) instead of one per column (a node).
+// part: 0 = the whole plan; 1 = what the products need (surviving cells,
+// their count and the depth-1 direct map, from the first round alone);
+// 2 = the rest of the plan after a part-1 launch, leaving the arrays part 1
+// wrote untouched (so that it may run while the products read them).
 template <bool kSmem>
 __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& p,
                                               const uint8_t* __restrict__ mask, int32_t* peel_order,
-                                              uint8_t* recovered, int32_t* info_out, bool cell_mask = false) {
+                                              uint8_t* recovered, int32_t* info_out, bool cell_mask = false,
+                                              int part = 0) {
   extern __shared__ int32_t dyn_smem[];
   __shared__ int s_warp[32];
   __shared__ int s_nf, s_new[2], s_next[2];  // per-round counters, by round parity
@@ -67,8 +72,10 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
 
   for (int c = tid; c < g.num_cells; c += nt) {
     const bool alive = (cell_mask ? mask[c] : mask[g.col_of_cell[c]]) == 0;
-    cnt[c] = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
-    p.direct[c] = -1;
+    const int v = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
+    cnt[c] = v;
+    if (kSmem) p.cnt[c] = v;  // the sign (erased column) is read by the two-dimensional GEMM
+    if (part != 2) p.direct[c] = -1;
   }
   for (int s = tid; s < g.S; s += nt) {
     depth[s] = 0;
@@ -89,7 +96,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
     int total;
     const int ex = block_exclusive_scan(f, s_warp, &total);
     if (f) {
-      p.surv[nsurv + ex] = c;
+      if (part != 2) p.surv[nsurv + ex] = c;
       if (cnt[c] == 1) p.front0[atomicAdd(&s_nf, 1)] = c;
     }
     nsurv += total;
@@ -102,7 +109,8 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   int nf = s_nf;
   // Two barriers per round.  Counters of round r live at parity r & 1 and the
   // other parity is cleared during round r, after every thread has read it.
-  while (nf > 0) {
+  const int max_rounds = part == 1 ? 1 : INT_MAX;
+  while (nf > 0 && round < max_rounds) {
     ++round;
     const int q = round & 1;
     // A: one warp per ready cell (exactly one unknown source at the start of
@@ -164,6 +172,18 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
     nx = tmp;
   }
 
+  if (part == 1) {
+    // what the products need: the depth-1 direct map and the survivor count
+    __syncthreads();
+    for (int s = tid; s < g.S; s += nt)
+      if (depth[s] == 1) p.direct[p.resolver[s]] = s;
+    if (tid == 0) {
+      p.ctr[CTR_NSURV] = nsurv;
+      p.info[BPX_INFO_DEVICE_ERR] = 0;  // cleared before the products run
+    }
+    return;
+  }
+
   // Place the recovered sources in (depth, source) order: one warp walks the
   // sources in ascending id; lanes of equal depth share one cursor bump.
   for (int d = 1 + tid; d <= round; d += nt) p.cursor[d] = p.wave_ptr[d - 1];
@@ -189,7 +209,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   for (int s = tid; s < g.S; s += nt) {
     const int d = depth[s];
     if (kSmem) p.depth[s] = d;
-    if (d == 1) p.direct[p.resolver[s]] = s;
+    if (d == 1 && part != 2) p.direct[p.resolver[s]] = s;
     if (recovered) recovered[s] = d > 0 ? 1 : 0;
   }
   // Peel list: for order position i, the resolver and the other sources of
@@ -241,12 +261,18 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
     p.ctr[CTR_ERR] = 0;
     int32_t inf[BPX_INFO_LEN];
     for (int i = 0; i < BPX_INFO_LEN; ++i) inf[i] = 0;
-    inf[BPX_INFO_STATUS] = (nrec == g.S) ? BPX_OK : BPX_ERR_UNDECODABLE;
+    // part 2 runs beside the products: keep a self-check error they raised
+    const int32_t dev_err = part == 2 ? atomicAdd(&p.info[BPX_INFO_DEVICE_ERR], 0) : 0;
+    inf[BPX_INFO_STATUS] = dev_err ? dev_err : ((nrec == g.S) ? BPX_OK : BPX_ERR_UNDECODABLE);
+    inf[BPX_INFO_DEVICE_ERR] = dev_err;
     inf[BPX_INFO_RECOVERED] = nrec;
     inf[BPX_INFO_WAVES] = round;
     inf[BPX_INFO_SURVIVING] = nsurv;
     inf[BPX_INFO_DIRECT] = round >= 1 ? p.wave_ptr[1] : 0;
     for (int i = 0; i < BPX_INFO_LEN; ++i) {
+      if (i == BPX_INFO_DEVICE_ERR || i == BPX_INFO_STATUS) {
+        if (dev_err) continue;  // left as the products' atomic writes set them
+      }
       p.info[i] = inf[i];
       if (info_out) info_out[i] = inf[i];
     }
@@ -256,8 +282,8 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
 template <bool kSmem>
 __global__ void __launch_bounds__(kThreads, 1)
 schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
-                uint8_t* recovered, int32_t* info_out, bool cell_mask) {
-  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out, cell_mask);
+                uint8_t* recovered, int32_t* info_out, bool cell_mask, int part) {
+  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
 }
 
 // Grouped launch: CTA j plans job j.
@@ -285,15 +311,15 @@ cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_stat
 
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
-                            cudaStream_t st, bool cell_mask) {
+                            cudaStream_t st, bool cell_mask, int part) {
   const size_t smem = (static_cast<size_t>(g.num_cells) + g.S) * sizeof(int32_t);
   if (smem <= kSmemStateMax) {
     cudaError_t e = cudaFuncSetAttribute(schedule_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemStateMax));
     if (e != cudaSuccess) return e;
-    schedule_kernel<true><<<1, kThreads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask);
+    schedule_kernel<true><<<1, kThreads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
   } else {
-    schedule_kernel<false><<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask);
+    schedule_kernel<false><<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
   }
   return cudaGetLastError();
 }
