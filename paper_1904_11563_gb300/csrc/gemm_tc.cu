@@ -264,9 +264,10 @@ enum { kModeRows = 0, kModeExact = 1, kMode2D = 2 };
 // rasterisation bands).  pair: the tile space counts pairs of vertically
 // adjacent m-tiles (two CTAs of a cluster share the B tile); m is then the
 // pair index and `live` tells whether the pair covers surviving rows.
-// exact: a single job's tile space repeats once per diagonal d (outermost);
-// the tile then walks the d + 1 digit pairs (i, d - i), all k-slices of one
-// pair after the other.
+// exact: a single job's tile space holds every tile once per diagonal d
+// (innermost, so that a tile's diagonals run close together); the tile then
+// walks the d + 1 digit pairs (i, d - i), all k-slices of one pair after the
+// other.
 __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long long t, int group, int live_mc,
                                           bool pair, int bk, int mode = kModeRows) {
   const bool exact = mode == kModeExact;
@@ -305,10 +306,9 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   int m_units = live_mc >= 0 ? (live_mc + BM - 1) / BM : J.m_tiles_max;
   if (pair) m_units = (m_units + 1) / 2;
   int d = 0, lt = lt0;
-  if (exact) {
-    const int per = m_units * J.n_tiles;
-    d = lt / per;
-    lt -= d * per;
+  if (exact) {  // the diagonals of a tile are adjacent: they reuse its digit planes from L2
+    d = lt % J.ex_S;
+    lt /= J.ex_S;
   }
   const int band_tiles = group * J.n_tiles;
   const int band = lt / band_tiles;
