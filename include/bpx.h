@@ -442,11 +442,15 @@ int bpx_group_autotune(bpx_group* group, const int* configs, int nconfigs, bpx_s
  * whole path once, then times the GEMM under each candidate configuration.
  * gemm_config = band * 1000 + seg_kb * 10 + tile, tile 1 = 128x256 and
  * 2 = 128x128 output tiles, 3 / 4 = the same in clusters of two CTAs that
- * share (multicast) each B tile; seg_kb = k-blocks of 64 per TMEM
+ * share (multicast) each B tile, 5..8 = tiles 1..4 with 32-wide instead of
+ * 64-wide k-slices, 0 / 9 = 256x256 tiles computed by CTA-pair MMAs
+ * (cta_group::2; each CTA of the cluster holds 128 rows of A and half of
+ * the B tile) with 64- / 32-wide k-slices; seg_kb = k-blocks of 64 per TMEM
  * accumulation segment, band = m-tiles (or m-tile pairs) per rasterisation
- * band.  Precisions BPX_BF16, BPX_BF16X3 and BPX_EXACT (which uses the tile
- * width, pairing and band, with 32-wide k-slices and its own exact segment
- * length).  Synchronizes. */
+ * band.  gemm_config 0 = the default, 8080.  Precisions BPX_BF16,
+ * BPX_BF16X3 and BPX_EXACT (which uses the tile shape, pairing, k-slice and
+ * band, with its own exact segment length; its default is also 8080).
+ * Synchronizes. */
 int bpx_autotune(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
                  int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
                  const int* configs, int nconfigs, bpx_stream stream, int* best_config, float* best_ms);

@@ -358,22 +358,78 @@ __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
       : "memory");
 }
 
+// ---- CTA-pair MMA (cta_group::2) ----------------------------------------
+// The two CTAs of a cluster compute one 256 x kBN tile: each holds its 128
+// rows of A and half of the B tile (kBN / 2 rows of B^T) in its own shared
+// memory, and its 128 rows of the accumulator in its own tensor memory.  The
+// even CTA issues the MMAs for both; both CTAs' copies complete on the even
+// CTA's stage barrier, and its commits arrive on the barriers of both.
+
+// Address of the same shared variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on a
+// barrier of either CTA of the pair.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t cluster_bar, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(cluster_bar)
+      : "memory");
+}
+
+// kind::f16, M = 256 (128 rows in each CTA of the pair), N = kBN.
+template <int kBN>
+__host__ __device__ constexpr uint32_t idesc_bf16_pair() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kBN >> 3) << 17) |
+         (static_cast<uint32_t>((2 * BM) >> 4) << 24);
+}
+
+template <int kBN>
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc_bf16_pair<kBN>()), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(static_cast<uint16_t>(3))
+      : "memory");
+}
+
 // kPair: launched in clusters of two CTAs that take the two m-tiles of a pair
 // with the same B tile; each CTA TMA-loads half of the B tile and multicasts
 // it into both CTAs' stage, and each MMA commit releases the stage in both
 // CTAs, so a stage is refilled only once both have consumed it.
+// kPair == 2: the same pairs of m-tiles, computed by CTA-pair MMAs
+// (cta_group::2, M = 256): each CTA loads only its own A rows and its half of
+// the B tile, so a CTA's shared memory takes a third less traffic per MMA.
 // kMode == kModeExact: exact-slice digit products (plain bf16 MMAs over the
 // digit planes, k-slices of the diagonal's digit pairs in sequence; FP32
 // segments exact by construction, promoted to int32 and stored to the
 // diagonal's plane).  kMode == kMode2D: the two-dimensional scheme (k-slices
 // of the cell's terms in sequence; h x w output blocks).
-template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, int kMode = kModeRows>
+template <bool kSplit, int kStages, int kBN, int kPair, int kBK, int kMode = kModeRows>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ table, int njobs,
                long long total_tiles, int group, int seg_kb) {
   constexpr bool kExact = kMode == kModeExact;
   constexpr bool k2D = kMode == kMode2D;
-  using St = Stage<kSplit, kBN, kBK>;
+  constexpr bool k2Sm = kPair == 2;
+  using St = Stage<kSplit, k2Sm ? kBN / 2 : kBN, kBK>;  // a CTA pair holds half the B tile each
   constexpr int kTmemCols = 2 * kBN;  // two FP32 segment accumulators
   constexpr int kCols = kBN / 2;      // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
@@ -401,21 +457,29 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), kPair ? 2 : 1);
+      mbar_init(smem_u32(&empty_bar[s]), kPair == 1 ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&sfull_bar[a]), 1);
-      mbar_init(smem_u32(&sempty_bar[a]), 8);
+      mbar_init(smem_u32(&sempty_bar[a]), k2Sm ? 16 : 8);  // CTA pair: both CTAs' epilogue warps
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base_sh)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (k2Sm) {  // both CTAs of the pair allocate together
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(&tmem_base_sh)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(&tmem_base_sh)),
+                   "r"(kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   fence_before();
   __syncthreads();
@@ -469,6 +533,18 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           }
           const uint32_t base = smem_u32(smem + s * St::kBytes);
           const uint32_t fb = smem_u32(&full_bar[s]);
+          if constexpr (k2Sm) {
+            // both CTAs' copies count on the even CTA's barrier, armed there
+            // for the two stages' bytes
+            const uint32_t fb0 = mapa_rank(fb, 0);
+            if (rank == 0) mbar_expect_tx(fb, 2 * St::kBytes);
+            const int yh = yb + static_cast<int>(rank) * (kBN / 2);
+            tma_load_2d_pair(base + St::kAhi, &T.J->map_ahi, fb0, xa, ya);
+            if (kSplit) tma_load_2d_pair(base + St::kAlo, &T.J->map_alo, fb0, xa, ya);
+            tma_load_2d_pair(base + St::kBhi, &T.J->map_bhi, fb0, xb, yh);
+            if (kSplit) tma_load_2d_pair(base + St::kBlo, &T.J->map_blo, fb0, xb, yh);
+            continue;
+          }
           mbar_expect_tx(fb, St::kBytes);
           tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, xa, ya);
           if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, xa, ya);
@@ -484,9 +560,10 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           }
         }
       }
-      if (!ok || abort_flag) {
+      if ((!ok || abort_flag) && !(k2Sm && rank != 0)) {
         // Stopping early: let the copies this CTA still has in flight land
         // (bounded waits, abort ignored) before its shared memory goes away.
+        // (A CTA pair's copies all complete on the even CTA's barriers.)
         for (int i = 0; i < kStages && i < kb_all; ++i) {
           const int kb = kb_all - 1 - i;
           mbar_wait(smem_u32(&full_bar[kb % kStages]), static_cast<uint32_t>((kb / kStages) & 1), nullptr);
@@ -494,7 +571,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && (!k2Sm || rank == 0)) {  // a CTA pair's MMAs issue from the even CTA
       int kb_all = 0, g = 0;
       bool ok = true;
       for (long long j = 0; ok; ++j) {
@@ -532,19 +609,32 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
             for (int kk = 0; kk < kBK / 16; ++kk) {
               const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
-              umma_bf16<kBN>(d_tmem, ahi + adv, bhi + adv, first);
-              if (kSplit) {
-                umma_bf16<kBN>(d_tmem, ahi + adv, blo + adv, 1u);
-                umma_bf16<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
+              if constexpr (k2Sm) {
+                umma_bf16_pair<kBN>(d_tmem, ahi + adv, bhi + adv, first);
+                if (kSplit) {
+                  umma_bf16_pair<kBN>(d_tmem, ahi + adv, blo + adv, 1u);
+                  umma_bf16_pair<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
+                }
+              } else {
+                umma_bf16<kBN>(d_tmem, ahi + adv, bhi + adv, first);
+                if (kSplit) {
+                  umma_bf16<kBN>(d_tmem, ahi + adv, blo + adv, 1u);
+                  umma_bf16<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
+                }
               }
             }
-            if (kPair)
+            if (k2Sm)
+              umma_commit_pair(smem_u32(&empty_bar[s]));
+            else if (kPair)
               umma_commit_mc(smem_u32(&empty_bar[s]), 3);
             else
               umma_commit(smem_u32(&empty_bar[s]));
           }
           if (!ok) break;
-          umma_commit(smem_u32(&sfull_bar[buf]));
+          if (k2Sm)
+            umma_commit_pair(smem_u32(&sfull_bar[buf]));
+          else
+            umma_commit(smem_u32(&sfull_bar[buf]));
         }
       }
     }
@@ -591,7 +681,12 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
         }
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&sempty_bar[buf]));
+        if (lane == 0) {
+          if (k2Sm)  // the even CTA's MMA thread waits for both CTAs' drains
+            mbar_arrive_cluster(mapa_rank(smem_u32(&sempty_bar[buf]), 0));
+          else
+            mbar_arrive(smem_u32(&sempty_bar[buf]));
+        }
       }
       if (!ok) break;
       const TcJob& J = *T.J;
@@ -649,9 +744,14 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   if (kPair) cluster_sync();  // no CTA leaves while its peer may still write into it
   if (warp == 1) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(kTmemCols)
-                 : "memory");
+    if constexpr (k2Sm)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(kTmemCols)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(kTmemCols)
+                   : "memory");
   }
 }
 
@@ -997,25 +1097,30 @@ bool make_map_u8(CUtensorMap* map, const void* base, long long rows, int K, int 
 // Tile configurations the autotuner chooses among (gemm_config % 10):
 // 1 = 128x256, 2 = 128x128, 3 = 128x256 paired (B multicast), 4 = 128x128
 // paired; 5..8 = the same with 32-wide k-slices (64-byte swizzle, twice the
-// stages of half the size).
+// stages of half the size); 9 / 0 = 256x256 tiles of CTA-pair MMAs (128x256
+// per CTA) with 32- / 64-wide k-slices.
 int tile_bn(int config) {
   const int t = config % 10;
   return (t == 2 || t == 4 || t == 6 || t == 8) ? 128 : 256;
 }
-bool tile_pair(int config) {
+// 0: one CTA per tile; 1: CTA pairs sharing the B tile by multicast; 2: CTA
+// pairs computing one tile with cta_group::2 MMAs.
+int tile_pair(int config) {
   const int t = config % 10;
-  return t == 3 || t == 4 || t == 7 || t == 8;
+  if (t == 9 || t == 0) return 2;
+  return (t == 3 || t == 4 || t == 7 || t == 8) ? 1 : 0;
 }
 int tile_bk(int config) { return (config % 10) >= 5 ? 32 : 64; }
 
 // seg_kb: k-slices of kBK per TMEM accumulation segment.
-template <bool kSplit, int kStages, int kBN, bool kPair, int kBK, int kMode = kModeRows>
+template <bool kSplit, int kStages, int kBN, int kPair, int kBK, int kMode = kModeRows>
 cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, long long total_tiles,
                            int group, int seg_kb, cudaStream_t st) {
   // 32-wide slices: 32 KB of slack after the stages, so that the descriptors
   // of the 64-byte swizzled layout can never reach past the allocation.
-  const size_t smem =
-      static_cast<size_t>(kStages) * Stage<kSplit, kBN, kBK>::kBytes + 1024 + (kBK == 32 ? 32768 : 0);
+  // (a CTA of a cta_group::2 pair stages half the B tile)
+  using St = Stage<kSplit, kPair == 2 ? kBN / 2 : kBN, kBK>;
+  const size_t smem = static_cast<size_t>(kStages) * St::kBytes + 1024 + (kBK == 32 ? 32768 : 0);
   auto kern = gemm_tc_kernel<kSplit, kStages, kBN, kPair, kBK, kMode>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -1050,12 +1155,14 @@ cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, l
 }
 
 template <int kBK, int kMode = kModeRows>
-cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, const TcJob* table, int njobs,
+cudaError_t dispatch_bk(bool split3, int bn, int pair, const TcJob& single, const TcJob* table, int njobs,
                         long long total_tiles, int group, int seg_kb, cudaStream_t st) {
   constexpr int m = BK / kBK;  // stages scale up as slices shrink
   seg_kb *= m;                 // configs count segments in 64-wide k-blocks
 #define BPX_LV(SPLIT, STAGES, BN, PAIR) \
   launch_variant<SPLIT, STAGES, BN, PAIR, kBK, kMode>(single, table, njobs, total_tiles, group, seg_kb, st)
+  // CTA-pair MMAs: a stage holds the CTA's A rows and half the B tile
+  if (pair == 2 && bn == 256) return split3 ? BPX_LV(true, 3 * m, 256, 2) : BPX_LV(false, 6 * m, 256, 2);
   if (split3) {
     if (bn == 128) return pair ? BPX_LV(true, 3 * m, 128, true) : BPX_LV(true, 3 * m, 128, false);
     return pair ? BPX_LV(true, 2 * m, 256, true) : BPX_LV(true, 2 * m, 256, false);
@@ -1069,9 +1176,11 @@ cudaError_t dispatch_bk(bool split3, int bn, bool pair, const TcJob& single, con
 // multiple of 64, so a 64-wide slice never straddles two digit planes);
 // seg in k-slices.
 template <int kBK>
-cudaError_t dispatch_exact_bk(int bn, bool pair, const TcJob& J, long long total_tiles, int group, int seg,
+cudaError_t dispatch_exact_bk(int bn, int pair, const TcJob& J, long long total_tiles, int group, int seg,
                               cudaStream_t st) {
   constexpr int m = BK / kBK;
+  if (pair == 2 && bn == 256)
+    return launch_variant<false, 6 * m, 256, 2, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
   if (bn == 128)
     return pair ? launch_variant<false, 6 * m, 128, true, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st)
                 : launch_variant<false, 6 * m, 128, false, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
@@ -1079,13 +1188,13 @@ cudaError_t dispatch_exact_bk(int bn, bool pair, const TcJob& J, long long total
               : launch_variant<false, 4 * m, 256, false, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
 }
 
-cudaError_t dispatch_exact(int bn, bool pair, int bk, const TcJob& J, long long total_tiles, int group, int seg,
+cudaError_t dispatch_exact(int bn, int pair, int bk, const TcJob& J, long long total_tiles, int group, int seg,
                            cudaStream_t st) {
   if (bk == 64) return dispatch_exact_bk<64>(bn, pair, J, total_tiles, group, seg / 64, st);
   return dispatch_exact_bk<32>(bn, pair, J, total_tiles, group, seg / 32, st);
 }
 
-cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single, const TcJob* table, int njobs,
+cudaError_t dispatch(bool split3, int bn, int pair, int bk, const TcJob& single, const TcJob* table, int njobs,
                      long long total_tiles, int group, int seg_kb, cudaStream_t st, bool twod = false) {
   if (twod) {
     if (bk == 32)
@@ -1096,15 +1205,15 @@ cudaError_t dispatch(bool split3, int bn, bool pair, int bk, const TcJob& single
   return dispatch_bk<64>(split3, bn, pair, single, table, njobs, total_tiles, group, seg_kb, st);
 }
 
-// gemm_config: 0 = defaults (the fastest measured on the benchmark: 128x256
-// tiles in CTA pairs, 32-wide k-slices, band 8, 512-wide K segments), else
-// band * 1000 + seg_kb * 10 + tile (see tile_bn / tile_pair / tile_bk).
-void decode_config(int config, int* group, int* seg_kb, int* bn, bool* pair, int* bk) {
+// gemm_config: 0 = defaults (the fastest measured on the benchmark: 256x256
+// tiles of CTA-pair MMAs, 64-wide k-slices, band 8, 512-wide K segments),
+// else band * 1000 + seg_kb * 10 + tile (see tile_bn / tile_pair / tile_bk).
+void decode_config(int config, int* group, int* seg_kb, int* bn, int* pair, int* bk) {
   *group = 8;
   *seg_kb = 8;
   *bn = 256;
-  *pair = true;
-  *bk = 32;
+  *pair = 2;
+  *bk = 64;
   if (config > 0) {
     *group = 16;
     *seg_kb = 4;
@@ -1161,7 +1270,7 @@ bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo,
 cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
                            long long* total_tiles, cudaStream_t st) {
   int group, seg_kb, bn, bk;
-  bool pair;
+  int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
@@ -1191,7 +1300,7 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
                            int32_t* info_out, cudaStream_t st) {
   (void)g;
   int group, seg_kb, bn, bk;
-  bool pair;
+  int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   TcJob J;
   if (!tc_fill_job(&J, p, a_hi, split3 ? a_lo : nullptr, b_hi, split3 ? b_lo : nullptr, num_cells, N, K, h,
@@ -1209,11 +1318,11 @@ cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void
                               int K, int h, const ExactParams& P, int32_t* planes, int config, int32_t* info_out,
                               cudaStream_t st) {
   int group, seg_kb, bn, bk;
-  bool pair;
-  // Default: 128x256 paired tiles, 64-wide k-slices, bands of 8 (fastest
-  // measured; one MMA per k-slice and digit pair, so the wider slice halves
-  // the stage hand-offs per MMA).
-  decode_config(config > 0 ? config : 8083, &group, &seg_kb, &bn, &pair, &bk);
+  int pair;
+  // Default: 256x256 tiles of CTA-pair MMAs, 64-wide k-slices, bands of 8
+  // (fastest measured; one MMA per k-slice and digit pair, so the wider
+  // slice halves the stage hand-offs per MMA).
+  decode_config(config > 0 ? config : 8080, &group, &seg_kb, &bn, &pair, &bk);
   TcJob J;
   if (!tc_fill_job(&J, p, a_planes, nullptr, b_planes, nullptr, num_cells, N, P.S * P.Kp, h, bn, pair, bk,
                    nullptr, nullptr, info_out))
@@ -1236,7 +1345,7 @@ cudaError_t launch_gemm_2d(const DevGraph& g, const DevPlan& p, const void* a_hi
                            const void* b_lo, int N, int K, int h, int w, bool split3, float* products,
                            float* C_direct, int config, int32_t* info_out, cudaStream_t st) {
   int group, seg_kb, bn, bk;
-  bool pair;
+  int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   TcJob J;
   memset(&J, 0, sizeof J);
@@ -1280,7 +1389,7 @@ cudaError_t launch_gemm_2d(const DevGraph& g, const DevPlan& p, const void* a_hi
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st) {
   int group, seg_kb, bn, bk;
-  bool pair;
+  int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
   TcJob dummy;
   memset(&dummy, 0, sizeof dummy);

@@ -46,7 +46,7 @@ void mark(const bpx_opts* o, int stage, int end, cudaStream_t st) {
 }
 
 // The device GEMM table depends on the tile shape and pairing (gemm_config % 10).
-int tile_of(int config) { return (config % 10) == 0 ? 7 : config % 10; }
+int tile_of(int config) { return config % 10; }  // the default (0) is tile 0
 
 // (Re)builds the device GEMM table when the tile width changes.
 int ensure_table(bpx_group* G, int config, cudaStream_t st) {
@@ -248,7 +248,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
 
 namespace {
 
-const int kDefaultConfigs[] = {8087, 16087, 4087, 8085, 16085, 8047, 8045, 16041, 8086, 8088, 8046, 16042};
+const int kDefaultConfigs[] = {8080, 16080, 4080, 8089, 16089, 8087, 16087, 8085, 8047, 16041, 8086, 8088};
 
 // Times `launch` on each config (one warm-up, then the best of three) and
 // returns the fastest.
@@ -342,7 +342,7 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
   if (precision == BPX_EXACT) {
     bpx::ExactParams P;
     if (int rc = bpx::exact_params(c, K, &P)) return rc;
-    static const int kExactConfigs[] = {8083, 8081, 4083, 16083, 8084, 8082, 8087, 8085};
+    static const int kExactConfigs[] = {8080, 16080, 8089, 8083, 8081, 4083, 16083, 8084, 8082, 8087};
     if (!configs || nconfigs <= 0) {
       configs = kExactConfigs;
       nconfigs = static_cast<int>(sizeof(kExactConfigs) / sizeof(kExactConfigs[0]));

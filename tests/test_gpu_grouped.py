@@ -118,7 +118,7 @@ def test_autotune_replans_and_stays_exact(libbpx):
     torch.cuda.synchronize()
     _check_exact(bpx, jobs, refs)
     # every other tile shape, re-planned, stays exact
-    for cfg in (16041, 16042, 16043, 16044, 16045, 16048):
+    for cfg in (16041, 16042, 16043, 16044, 16045, 16048, 16049, 16040):
         G.set_config(cfg)
         for j in jobs:
             j["C"].zero_()
@@ -139,7 +139,7 @@ def test_single_job_autotune_and_tile_configs(libbpx):
     best, ms = bpx.autotune(code, dA, dB, h, bpx.BF16X3, m, ws, configs=[16041, 16022, 4012, 32082, 16043, 8024])
     assert best in (16041, 16022, 4012, 32082, 16043, 8024)
     refC = o.reference_product(A, B)
-    for cfg in (16041, 16022, 4012, 32082, 16043, 8024, best):
+    for cfg in (16041, 16022, 4012, 32082, 16043, 8024, 8089, 4019, best):
         C, info = bpx.coded_matmul(code, dA, dB, h, bpx.BF16X3, m, ws, opts=bpx.default_opts(gemm_config=cfg))
         torch.cuda.synchronize()
         assert np.array_equal(C[:M].cpu().numpy(), refC), cfg

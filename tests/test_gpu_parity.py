@@ -345,7 +345,8 @@ def test_async_host_calls_in_flight(libbpx, prec):
 
 @pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16043), ("bf16x3", 8044),
                                       ("bf16", 16043), ("bf16x3", 16022), ("bf16x3", 16045), ("bf16x3", 8047),
-                                      ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8048)])
+                                      ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8048), ("bf16x3", 8089),
+                                      ("bf16", 16089), ("bf16x3", 8080), ("bf16", 4080)])
 def test_many_tiles_per_cta(libbpx, prec, cfg):
     """Bench-shaped code and block height at reduced N, K: ~600 output tiles
     of 128 x 256, so every persistent CTA runs several tiles and both TMEM
