@@ -517,3 +517,28 @@ def test_searched_code_on_the_gpu(libbpx, prec):
         else:
             R, _s = _oracle_decode(ref, A, B, h, m)
             _check_blocks(C, R, ref, A, B, h, m, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("peel_ctas,comp", [(0, -1), (16, -1), (0, 0), (16, 0)])
+def test_gathered_peel_waves(libbpx, prec, peel_ctas, comp):
+    """A tall code (Construction A n=12, k=9, b=120: 1080 sources, ~118
+    narrow waves), whose peel gathers each wave's blocks into shared memory.
+    Integer inputs keep every product and every peeled row exact, so C must
+    equal A B bit for bit: on the default grid (every wave fits the gather
+    buffer), on a 16-CTA grid whose wide column slices send the wider waves
+    down the register path (both paths in one launch), plain and with the
+    FP64-compensated subtraction on every wave."""
+    bpx = libbpx
+    code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
+    h, K, N = 2, 64, 4096
+    M = ref.num_sources * h - 3  # ragged: the last source block is partly padding
+    A = W.matrix((M, K), "int", 91)
+    B = W.matrix((K, N), "int", 92)
+    exact = o.reference_product(A, B)
+    opts = bpx.default_opts(peel_ctas=peel_ctas, compensate_depth=comp)
+    for t in range(2):
+        m = W.erasure_mask(12, 3, 5 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=opts)
+        assert info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] > 50
+        assert np.array_equal(C[:M], exact), (prec, peel_ctas, comp, t)
