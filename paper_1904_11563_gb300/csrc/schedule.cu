@@ -313,13 +313,17 @@ cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* 
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
                             cudaStream_t st, bool cell_mask, int part) {
   const size_t smem = (static_cast<size_t>(g.num_cells) + g.S) * sizeof(int32_t);
+  // Small codes take a 256-thread block: it fits beside a resident GEMM CTA
+  // (registers), so the schedule of one multiplication can run while the
+  // GEMM of another still holds every SM.
+  const int threads = g.num_cells + g.S <= 4096 ? 256 : kThreads;
   if (smem <= kSmemStateMax) {
     cudaError_t e = cudaFuncSetAttribute(schedule_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemStateMax));
     if (e != cudaSuccess) return e;
-    schedule_kernel<true><<<1, kThreads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
+    schedule_kernel<true><<<1, threads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
   } else {
-    schedule_kernel<false><<<1, kThreads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
+    schedule_kernel<false><<<1, threads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
   }
   return cudaGetLastError();
 }
