@@ -98,6 +98,8 @@ def _parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "mxfp8", "fp32", "exact"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-inflight", type=int, default=3,
+                    help="end-to-end steps in flight (each on its own stream with its own device buffers)")
     ap.add_argument("--inflight", type=int, default=2,
                     help="steps in flight in the timed region of `value` (each on its own stream with its own "
                          "workspace, C and info words); 1 = one step at a time")
@@ -578,7 +580,7 @@ def run_ours(args, wl):
                 r_["ws"] = r_["C"] = None
         torch.cuda.empty_cache()
         e2e_steps = max(10, steps)
-        nflight = 3
+        nflight = max(1, args.e2e_inflight)
         sets = []
         for j in range(nflight):
             sets.append(dict(
@@ -588,6 +590,7 @@ def run_ours(args, wl):
                 ws=ws0 if j == 0 else bpx.Workspace(code, M, N, K, h, P, device=dev),
                 hC=torch.empty((M, N), dtype=torch.float32).pin_memory(),
                 hinfo=torch.zeros(bpx.INFO_LEN, dtype=torch.int32).pin_memory(),
+                dinfo=torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device=dev),
                 stream=torch.cuda.Stream(device=dev)))
 
         def _enqueue(i):
@@ -616,6 +619,29 @@ def run_ours(args, wl):
                        "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
                        "api": "bpx_coded_matmul_host_async, %d steps in flight (separate streams, buffers, "
                               "workspaces)" % nflight, "steps": e2e_steps}
+        # The same host-link traffic without the computation: each step's
+        # copies (A, B and the mask in, C and the info words out) on the
+        # same streams and buffers -- the floor the link puts under "e2e".
+        def _copies(i):
+            S_ = sets[i % nflight]
+            with torch.cuda.stream(S_["stream"]):
+                S_["dA"].copy_(hA, non_blocking=True)
+                S_["dB"].copy_(hB, non_blocking=True)
+                S_["dmask"].copy_(hmasks[i % wl["trials"]], non_blocking=True)
+                S_["hC"].copy_(S_["dC"][:M], non_blocking=True)
+                S_["hinfo"].copy_(S_["dinfo"], non_blocking=True)
+
+        for i in range(nflight):
+            _copies(i)
+        torch.cuda.synchronize()
+        t_s = time.perf_counter()
+        for i in range(e2e_steps):
+            _copies(i)
+        torch.cuda.synchronize()
+        dtc = (time.perf_counter() - t_s) / e2e_steps
+        line["e2e"]["link_only_ms_per_step"] = dtc * 1e3
+        line["e2e"]["link_only_note"] = ("the same copies without the computation, same streams and buffers: "
+                                         "the host link's floor under the end-to-end step")
         S0 = sets[0]
         with torch.cuda.stream(S0["stream"]):
             for i in range(2):
