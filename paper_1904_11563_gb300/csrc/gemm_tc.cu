@@ -7,12 +7,16 @@
 // accumulator (the lo*lo term is below FP32 rounding); plain BF16 issues the
 // hi*hi MMA only.
 //
-// Persistent warp-specialised kernel, one 128 x 256 output tile at a time:
+// Persistent warp-specialised kernel, one 128 x 256 output tile per CTA at
+// a time:
 //   warp 0     TMA producer: 128B-swizzled 64-wide k-slices of A (hi, lo)
 //              and B (hi, lo) into a ring of shared-memory stages
 //   warp 1     TMEM owner + MMA issuer (one thread): tcgen05.mma kind::f16,
 //              M=128 N=256 K=16, commit -> "stage empty" / "segment full"
 //   warps 2-9  epilogue: two warps per TMEM lane quarter, 128 columns each.
+// The default configuration runs the CTAs in clusters of two whose MMAs are
+// CTA-pair MMAs (cta_group::2, M=256): each CTA stages its own 128 A rows and
+// half of the B tile, and the even CTA's MMA thread issues for both.
 //
 // The tensor core adds each MMA's products into its FP32 accumulator with
 // truncation, so the error of a long K sum grows with K.  The K range of a
