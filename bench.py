@@ -252,6 +252,43 @@ def cpu_baseline(A, B, wl, budget_s=12.0):
                       f"trial mask seed {wl['mask_seed_base']}, {total_t:.1f} s"}
 
 
+# ------------------------------------------------------------ replicas (N > 1)
+# One process per GPU under torchrun, each an independent replica of the
+# whole path (no data-path collective): the ranks meet only at the barriers
+# around the timed region, and rank 0 reports the slowest rank's time.
+
+def _world():
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
+
+
+def _dist_init(backend):
+    """Joins the replicas' process group (rendezvous from the MASTER_* env)."""
+    world, _rank = _world()
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+    return world
+
+
+def _barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def _max_over_ranks(values, device="cpu"):
+    """The element-wise maximum of `values` over all ranks (identity for one
+    process): the timed region ends when the slowest replica does."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -289,13 +326,10 @@ def run_ours(args, wl):
     from paper_1904_11563_gb300 import bpx
     from paper_1904_11563_gb300 import workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank = _world()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    _dist_init("nccl")
     dev = torch.device("cuda", local)
     M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
     code = _lib_code(bpx, wl)
@@ -355,8 +389,7 @@ def run_ours(args, wl):
         clocks = ClockSampler(gpu_index)
         clocks.start()
         time.sleep(0.3)
-        if world > 1:
-            torch.distributed.barrier()
+        _barrier()
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -367,8 +400,7 @@ def run_ours(args, wl):
             bpx.coded_matmul(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o, info=info)
         t1.record()
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        _barrier()
         ms_serial = t0.elapsed_time(t1)
         inf = info.cpu().numpy()
         assert inf[bpx.INFO_STATUS] == bpx.OK, inf
@@ -401,25 +433,20 @@ def run_ours(args, wl):
 
             _pipelined(0, max(warm, nf))
             torch.cuda.synchronize()
-            if world > 1:
-                torch.distributed.barrier()
+            _barrier()
             torch.cuda.synchronize()
             t0.record()
             _pipelined(warm, steps)
             t1.record()
             torch.cuda.synchronize()
-            if world > 1:
-                torch.distributed.barrier()
+            _barrier()
             ms = t0.elapsed_time(t1)
             for sl in slots:
                 si = sl["info"].cpu().numpy()
                 assert si[bpx.INFO_STATUS] == bpx.OK and si[bpx.INFO_DEVICE_ERR] == 0, si
             C_last = slots[(steps - 1) % nf]["C"]  # the last timed step's output (error report)
             del slots
-        if world > 1:
-            tt = torch.tensor([ms, ms_serial], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms, ms_serial = float(tt[0].item()), float(tt[1].item())
+        ms, ms_serial = _max_over_ranks([ms, ms_serial], device=dev)
         stage = {}
         recorded = ["schedule", "a_prep", "gemm", "peel"] + (["b_prep"] if prec != "fp32" else [])
         # (the autotuner covers the bf16 tensor-core kernels only)
