@@ -189,13 +189,27 @@ int bpx_code_from_cells(int n, int k, int b, int num_cells, const int32_t* col_o
 /* Searches for an equal-height array BP-XOR code: n columns of b cells, every
  * cell the sum of at most sigma of the b k sources, decodable by peeling from
  * every set of k columns (e = n - k).  Simulated annealing over the cells'
- * supports (cost: the erasure patterns that do not peel, plus sources in fewer
- * than n - k + 1 columns), at most `iters` moves from `seed`.  b k <= 64,
- * n <= 30.  *out receives the code (BPX_LITERAL) or NULL with
- * BPX_ERR_UNSUPPORTED when none was found; *iters_used (or NULL) the moves
- * taken. */
+ * supports (cost: the sources left unknown, summed over the erasure patterns,
+ * plus sources in fewer than n - k + 1 columns), at most `iters` moves from
+ * `seed`.  b k <= 64, n <= 30.  *out receives the code (BPX_LITERAL) or NULL
+ * with BPX_ERR_UNSUPPORTED when none was found; *iters_used (or NULL) the
+ * moves taken.  Equivalent to bpx_code_search_ex with flags 0, threads 1. */
 int bpx_code_search(int n, int k, int b, int sigma, long long iters, unsigned long long seed, bpx_code** out,
                     long long* iters_used);
+
+/* Search flags. */
+enum bpx_search_flags {
+  BPX_SEARCH_SYSTEMATIC = 1 /* the first k columns hold the b k sources one per cell (column l,
+                               cell z = source z k + l); only the parity columns are searched */
+};
+
+/* bpx_code_search with options: `threads` (1..256) independent annealing
+ * chains run on host threads, chain t from seed + t with up to `iters` moves
+ * each; the code returned is the one of the lowest t that found one, so the
+ * result does not depend on the threads' timing.  *iters_used = the moves of
+ * all chains.  flags: BPX_SEARCH_SYSTEMATIC or 0. */
+int bpx_code_search_ex(int n, int k, int b, int sigma, long long iters, unsigned long long seed, int flags,
+                       int threads, bpx_code** out, long long* iters_used);
 
 /* ---------------------------------------------------------------- workspace */
 

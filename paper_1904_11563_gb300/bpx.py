@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libbpx.so")
 
 # enums of bpx.h
 TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B, LITERAL = 0, 1, 2, 3, 4, 5
+SEARCH_SYSTEMATIC = 1  # bpx_code_search_ex flag
 FP32, BF16, BF16X3, MXFP8, EXACT = 0, 1, 2, 3, 4
 OK, ERR_INVAL, ERR_UNSUPPORTED, ERR_UNDECODABLE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(7)
 INFO_STATUS, INFO_RECOVERED, INFO_WAVES, INFO_SURVIVING, INFO_DIRECT, INFO_DEVICE_ERR = range(6)
@@ -103,6 +104,8 @@ def lib():
         "bpx_code_from_cells": (i, [i, i, i, i, vp, vp, vp, i, ct.POINTER(vp)]),
         "bpx_code_search": (i, [i, i, i, i, ct.c_longlong, ct.c_ulonglong, ct.POINTER(vp),
                                 ct.POINTER(ct.c_longlong)]),
+        "bpx_code_search_ex": (i, [i, i, i, i, ct.c_longlong, ct.c_ulonglong, i, i, ct.POINTER(vp),
+                                   ct.POINTER(ct.c_longlong)]),
         "bpx_terms_2d": (i, [vp, vp, vp]),
         "bpx_workspace_bytes_2d": (sz, [vp, i, i, i, i, i]),
         "bpx_coded_matmul_2d": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
@@ -222,11 +225,15 @@ class Code:
         return cls(LITERAL, n, k, b, handle=h)
 
     @classmethod
-    def search(cls, n, k, b, sigma, iters=200000, seed=0):
-        """Equal-height array BP-XOR code search; (code or None, moves taken)."""
+    def search(cls, n, k, b, sigma, iters=200000, seed=0, systematic=False, threads=1):
+        """Equal-height array BP-XOR code search; (code or None, moves taken).
+        systematic: the first k columns fixed to single sources; threads:
+        independent chains (seeds seed .. seed + threads - 1, iters moves
+        each; the lowest chain that found a code wins)."""
         h = ct.c_void_p()
         used = ct.c_longlong()
-        rc = lib().bpx_code_search(n, k, b, sigma, iters, seed, ct.byref(h), ct.byref(used))
+        rc = lib().bpx_code_search_ex(n, k, b, sigma, iters, seed, SEARCH_SYSTEMATIC if systematic else 0,
+                                      threads, ct.byref(h), ct.byref(used))
         if rc == ERR_UNSUPPORTED:
             return None, used.value
         _check(rc)

@@ -5,14 +5,17 @@
 //     every cell the XOR (here: sum) of at most sigma of the b k sources,
 //     decodable by peeling from any k columns.
 // The search is simulated annealing over the cells' supports with cost =
-// the number of (n - k)-column erasure patterns that do not peel plus a
-// penalty for sources in fewer than n - k + 1 columns (the appearance count
-// Theorem 3.1 starts from).  Supports are bit masks (b k <= 64), so one peel
-// is a few passes of mask operations.
+// the sources that the (n - k)-column erasure patterns leave unknown, summed
+// over the patterns, plus a penalty for sources in fewer than n - k + 1
+// columns (the appearance count Theorem 3.1 starts from).  Supports are bit
+// masks (b k <= 64), so one peel is a few passes of mask operations.
+// Optionally systematic (the first k columns fixed to single sources), and
+// run as independent chains on host threads.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <random>
+#include <thread>
 #include <vector>
 
 #include "bpx_internal.h"
@@ -23,45 +26,11 @@ using Mask = uint64_t;
 
 int popc(Mask m) { return __builtin_popcountll(m); }
 
-// Peels the cells of the columns not in `erased` (bitmask over columns).
-bool peels(const std::vector<Mask>& cells, const std::vector<int>& col, uint32_t erased, Mask all) {
-  Mask known = 0;
-  bool progress = true;
-  while (progress && known != all) {
-    progress = false;
-    for (size_t c = 0; c < cells.size(); ++c) {
-      if ((erased >> col[c]) & 1u) continue;
-      const Mask u = cells[c] & ~known;
-      if (u && !(u & (u - 1))) {
-        known |= u;
-        progress = true;
-      }
-    }
-  }
-  return known == all;
-}
-
 struct Problem {
   int n, k, b, sigma, S;
   std::vector<uint32_t> patterns;  // every set of n - k erased columns
   Mask all;
 };
-
-long long cost(const Problem& P, const std::vector<Mask>& cells, const std::vector<int>& col) {
-  long long bad = 0;
-  for (uint32_t er : P.patterns)
-    if (!peels(cells, col, er, P.all)) ++bad;
-  // sources must appear in at least n - k + 1 columns
-  long long short_by = 0;
-  for (int s = 0; s < P.S; ++s) {
-    uint32_t cols = 0;
-    for (size_t c = 0; c < cells.size(); ++c)
-      if ((cells[c] >> s) & 1u) cols |= 1u << col[c];
-    const int have = __builtin_popcount(cols);
-    if (have < P.n - P.k + 1) short_by += P.n - P.k + 1 - have;
-  }
-  return bad * 4 + short_by;
-}
 
 }  // namespace
 
@@ -125,46 +94,89 @@ extern "C" int bpx_code_from_cells(int n, int k, int b, int num_cells, const int
   return BPX_OK;
 }
 
-extern "C" int bpx_code_search(int n, int k, int b, int sigma, long long iters, unsigned long long seed,
-                               bpx_code** out, long long* iters_used) {
-  bpx::clear_error();
-  if (!out) return bpx::fail(BPX_ERR_INVAL, "bpx_code_search: out is NULL");
-  *out = nullptr;
-  if (n < 2 || k < 1 || k >= n || b < 1 || sigma < 1 || k * b > 64 || n > 30 || iters < 1)
-    return bpx::fail(BPX_ERR_INVAL, "bpx_code_search: needs 1 <= k < n <= 30, b k <= 64, sigma >= 1");
-  Problem P{n, k, b, sigma, k * b, {}, 0};
-  P.all = P.S == 64 ? ~Mask(0) : ((Mask(1) << P.S) - 1);
-  const int e = n - k;
-  for (uint32_t m = 0; m < (1u << n); ++m)
-    if (__builtin_popcount(m) == e) P.patterns.push_back(m);
+namespace {
+
+// Sources left unknown after peeling the cells of the columns not in
+// `erased`.
+int unrecovered(const std::vector<Mask>& cells, const std::vector<int>& col, uint32_t erased, Mask all) {
+  Mask known = 0;
+  bool progress = true;
+  while (progress && known != all) {
+    progress = false;
+    for (size_t c = 0; c < cells.size(); ++c) {
+      if ((erased >> col[c]) & 1u) continue;
+      const Mask u = cells[c] & ~known;
+      if (u && !(u & (u - 1))) {
+        known |= u;
+        progress = true;
+      }
+    }
+  }
+  return popc(all & ~known);
+}
+
+// Annealing cost: the sources every erasure pattern leaves unknown (a
+// smoother signal than the count of failing patterns), plus the shortfall of
+// sources appearing in fewer than n - k + 1 columns.  Zero iff every pattern
+// peels.
+long long cost_smooth(const Problem& P, const std::vector<Mask>& cells, const std::vector<int>& col) {
+  long long left = 0;
+  for (uint32_t er : P.patterns) left += unrecovered(cells, col, er, P.all);
+  long long short_by = 0;
+  for (int s = 0; s < P.S; ++s) {
+    uint32_t cols = 0;
+    for (size_t c = 0; c < cells.size(); ++c)
+      if ((cells[c] >> s) & 1u) cols |= 1u << col[c];
+    const int have = __builtin_popcount(cols);
+    if (have < P.n - P.k + 1) short_by += P.n - P.k + 1 - have;
+  }
+  return left + short_by;
+}
+
+struct Chain {
+  bool found = false;
+  long long moves = 0;
+  std::vector<Mask> cells;
+};
+
+// One annealing chain from `seed`.  systematic: the first k columns are
+// fixed single-source cells (column l, cell z = source z k + l) and only the
+// parity columns' cells move.
+Chain anneal(const Problem& P, int sigma, long long iters, unsigned long long seed, bool systematic) {
+  Chain out;
   std::mt19937_64 rng(seed);
+  const int n = P.n, k = P.k, b = P.b;
   std::vector<int> col(n * b);
   std::vector<Mask> cells(n * b);
   for (int c = 0; c < n * b; ++c) col[c] = c / b;
+  const int first_free = systematic ? k * b : 0;
+  if (systematic)
+    for (int l = 0; l < k; ++l)
+      for (int z = 0; z < b; ++z) cells[l * b + z] = Mask(1) << (z * k + l);
   auto rand_src = [&]() { return static_cast<int>(rng() % P.S); };
-  auto restart = [&]() {  // every cell a random support of 1 .. sigma sources
-    for (auto& m : cells) {
-      m = 0;
+  auto restart = [&]() {  // every free cell a random support of 1 .. sigma sources
+    for (int c = first_free; c < n * b; ++c) {
+      Mask m = 0;
       const int d = 1 + static_cast<int>(rng() % sigma);
       while (popc(m) < d) m |= Mask(1) << rand_src();
+      cells[c] = m;
     }
   };
   restart();
-  long long cur = cost(P, cells, col);
-  // Restarts every `epoch` moves without an improvement of the best cost of
-  // the epoch; the temperature falls geometrically within an epoch.
+  long long cur = cost_smooth(P, cells, col);
   const long long epoch = std::max<long long>(20000, iters / 20);
   long long since = 0, best = cur;
   double T = 1.0;
   long long it = 0;
+  const int nfree = n * b - first_free;
   for (; it < iters && cur > 0; ++it) {
     if (++since > epoch) {
       restart();
-      cur = best = cost(P, cells, col);
+      cur = best = cost_smooth(P, cells, col);
       since = 0;
       T = 1.0;
     }
-    const int c = static_cast<int>(rng() % cells.size());
+    const int c = first_free + static_cast<int>(rng() % nfree);
     const Mask old = cells[c];
     Mask m = old;
     const int r = static_cast<int>(rng() % 3);
@@ -183,7 +195,7 @@ extern "C" int bpx_code_search(int n, int k, int b, int sigma, long long iters, 
     }
     if (m == old) continue;
     cells[c] = m;
-    const long long nc = cost(P, cells, col);
+    const long long nc = cost_smooth(P, cells, col);
     if (nc <= cur || std::exp((cur - nc) / T) > std::uniform_real_distribution<double>(0, 1)(rng)) {
       cur = nc;
       if (cur < best) {
@@ -195,8 +207,51 @@ extern "C" int bpx_code_search(int n, int k, int b, int sigma, long long iters, 
     }
     T = std::max(0.02, T * (1.0 - 4.0 / epoch));
   }
-  if (iters_used) *iters_used = it;
-  if (cur != 0) return bpx::fail(BPX_ERR_UNSUPPORTED, "bpx_code_search: no code found in %lld iterations", iters);
+  out.found = cur == 0;
+  out.moves = it;
+  out.cells = cells;
+  return out;
+}
+
+}  // namespace
+
+extern "C" int bpx_code_search_ex(int n, int k, int b, int sigma, long long iters, unsigned long long seed,
+                                  int flags, int threads, bpx_code** out, long long* iters_used) {
+  bpx::clear_error();
+  if (!out) return bpx::fail(BPX_ERR_INVAL, "bpx_code_search: out is NULL");
+  *out = nullptr;
+  if (n < 2 || k < 1 || k >= n || b < 1 || sigma < 1 || k * b > 64 || n > 30 || iters < 1)
+    return bpx::fail(BPX_ERR_INVAL, "bpx_code_search: needs 1 <= k < n <= 30, b k <= 64, sigma >= 1");
+  if (threads < 1 || threads > 256) return bpx::fail(BPX_ERR_INVAL, "bpx_code_search: threads must be 1..256");
+  if (flags & ~BPX_SEARCH_SYSTEMATIC) return bpx::fail(BPX_ERR_INVAL, "bpx_code_search: unknown flags %d", flags);
+  Problem P{n, k, b, sigma, k * b, {}, 0};
+  P.all = P.S == 64 ? ~Mask(0) : ((Mask(1) << P.S) - 1);
+  const int e = n - k;
+  for (uint32_t m = 0; m < (1u << n); ++m)
+    if (__builtin_popcount(m) == e) P.patterns.push_back(m);
+  const bool systematic = (flags & BPX_SEARCH_SYSTEMATIC) != 0;
+  // Independent chains, chain t from seed + t; the result is the lowest t
+  // that found a code, so it does not depend on the threads' timing.
+  std::vector<Chain> chains(threads);
+  {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t)
+      pool.emplace_back([&, t] { chains[t] = anneal(P, sigma, iters, seed + t, systematic); });
+    chains[0] = anneal(P, sigma, iters, seed, systematic);
+    for (auto& th : pool) th.join();
+  }
+  long long used = 0;
+  int win = -1;
+  for (int t = 0; t < threads; ++t) {
+    used += chains[t].moves;
+    if (win < 0 && chains[t].found) win = t;
+  }
+  if (iters_used) *iters_used = used;
+  if (win < 0)
+    return bpx::fail(BPX_ERR_UNSUPPORTED, "bpx_code_search: no code found in %lld moves", used);
+  const std::vector<Mask>& cells = chains[win].cells;
+  std::vector<int> col(n * b);
+  for (int c = 0; c < n * b; ++c) col[c] = c / b;
   std::vector<std::vector<int32_t>> supp(cells.size());
   for (size_t c = 0; c < cells.size(); ++c)
     for (int s = 0; s < P.S; ++s)
@@ -211,4 +266,9 @@ extern "C" int bpx_code_search(int n, int k, int b, int sigma, long long iters, 
   bpx::finish_code(code, supp, col);
   *out = code;
   return BPX_OK;
+}
+
+extern "C" int bpx_code_search(int n, int k, int b, int sigma, long long iters, unsigned long long seed,
+                               bpx_code** out, long long* iters_used) {
+  return bpx_code_search_ex(n, k, b, sigma, iters, seed, 0, 1, out, iters_used);
 }

@@ -231,3 +231,32 @@ def test_code_from_columns_and_search(libbpx):
     assert code is None and used == 200000
     with pytest.raises(bpx.BpxError):
         bpx.Code.from_columns(2, 1, 1, [[(0,)], [(1,)]], e=1)     # source 1 out of range
+
+
+def test_code_search_ex_threads_and_flags(libbpx):
+    """The multi-chain search: a [7, 2] code with b = 3 (n meets the k = sigma
+    bound 2 b + 1) is found and verified by brute force; the result does not
+    depend on the threads' timing (same seed, same code twice); the
+    systematic flag keeps the data columns' single-source cells; bad
+    arguments are rejected."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    assert bpx.bound("k_equals_sigma", 2, 3) == 7
+    code, used = bpx.Code.search(7, 2, 3, 2, iters=2000000, seed=3, threads=1)
+    assert code is not None, used
+    assert code.sigma <= 2 and code.e == 5
+    assert o.is_array_bpxor(o.code_from_columns("found", 2, 3, code.columns()))
+    a, _ = bpx.Code.search(7, 2, 3, 2, iters=300000, seed=11, threads=4)
+    b, _ = bpx.Code.search(7, 2, 3, 2, iters=300000, seed=11, threads=4)
+    assert (a is None) == (b is None)
+    if a is not None:
+        assert a.cells == b.cells and list(a.col_ptr) == list(b.col_ptr)
+    s, used = bpx.Code.search(5, 2, 2, 2, iters=20000, seed=0, systematic=True, threads=2)
+    assert used <= 2 * 20000
+    if s is not None:  # data columns: column l, cell z holds source z k + l alone
+        cols = s.columns()
+        assert cols[0] == [(0,), (2,)] and cols[1] == [(1,), (3,)]
+    h = ctypes.c_void_p()
+    used = ctypes.c_longlong()
+    assert bpx.lib().bpx_code_search_ex(5, 2, 2, 2, 10, 0, 0, 0, ctypes.byref(h), ctypes.byref(used)) == bpx.ERR_INVAL
+    assert bpx.lib().bpx_code_search_ex(5, 2, 2, 2, 10, 0, 4, 1, ctypes.byref(h), ctypes.byref(used)) == bpx.ERR_INVAL
