@@ -720,6 +720,7 @@ def run_batch(args):
     useful = sum(2.0 * sp["M"] * sp["N"] * sp["K"] for sp in specs)
     G = bpx.Group(jobs, bpx.BF16X3, device=dev)
     best, best_ms = G.autotune()
+    peel_target, peel_tuned_ms = G.autotune_peel()
     stream = torch.cuda.Stream(device=dev)
     warm = max(args.warmup, 3)
     steps = args.steps
@@ -781,6 +782,7 @@ def run_batch(args):
                        "dims": "M, N, K = 128 * round(x / 128), x log-uniform on [256, 4096], seeded",
                        "inputs": "A, B iid U(-1,1) FP32, seeded", "useful_tflop_per_batch": useful / 1e12,
                        "launch": "one grouped run per step replayed from a CUDA graph",
+                       "peel_ctas_per_job": peel_target,
                        "gemm_config": best, "l2": "inputs larger than L2"},
             "all_ok": ok, "stages_ms": stage,
             "per_job_fp32_ms": base["fp32"], "per_job_bf16x3_ms": base["bf16x3"],

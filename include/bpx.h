@@ -469,6 +469,25 @@ int bpx_autotune(const bpx_code* code, const float* d_A, const float* d_B, int M
                  int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
                  const int* configs, int nconfigs, bpx_stream stream, int* best_config, float* best_ms);
 
+/* Peel-schedule autotuner of a group: times the grouped numeric peel (a4)
+ * with each job's float4 columns cut so that the job gets about `targets[i]`
+ * CTAs (NULL / 0 = a built-in list from 1/8 to 8 x the SM count; the default
+ * plan aims at 4 x the SM count), on the group's own plans and products (one full
+ * run first), keeps the fastest plan for later runs and graph launches, and
+ * reports it.  Synchronizes; not capturable. */
+int bpx_group_autotune_peel(bpx_group* group, const int* targets, int ntargets, bpx_stream stream,
+                            int* best_target, float* best_ms);
+
+/* Peel-schedule autotuner for one coded multiplication: runs the whole path
+ * once, then times the numeric peel (a4, bpx_peel_decode over the staged
+ * products) with opts->peel_ctas = each of `ctas` (NULL / 0 = a built-in list
+ * from half to 8 x the SM count) and returns the fastest count (pass it as
+ * bpx_opts.peel_ctas).  Precisions BPX_FP32, BPX_BF16, BPX_BF16X3, BPX_MXFP8.
+ * d_C holds the decoded C afterwards.  Synchronizes. */
+int bpx_autotune_peel(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
+                      int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
+                      const int* ctas, int nctas, bpx_stream stream, int* best_ctas, float* best_ms);
+
 void bpx_group_free(bpx_group* group);
 
 /* a1 without any device allocation by the caller or the library (the paper has

@@ -119,6 +119,10 @@ def lib():
                                    ct.POINTER(ct.c_float)]),
         "bpx_autotune": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, vp, sz, ct.POINTER(ct.c_int), i, vp,
                              ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
+        "bpx_group_autotune_peel": (i, [vp, ct.POINTER(ct.c_int), i, vp, ct.POINTER(ct.c_int),
+                                        ct.POINTER(ct.c_float)]),
+        "bpx_autotune_peel": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, vp, sz, ct.POINTER(ct.c_int), i, vp,
+                                  ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
         "bpx_group_free": (None, [vp]),
         "bpx_selftest_wait_timeout": (i, [ct.c_longlong, vp, vp]),
         "bpx_default_opts": (Opts, []),
@@ -486,6 +490,21 @@ def autotune(code: Code, A, B, h, precision, mask, ws: Workspace, C=None, config
     return best.value, ms.value
 
 
+def autotune_peel(code: Code, A, B, h, precision, mask, ws: Workspace, C=None, ctas=None):
+    """Peel-schedule autotuner for one job: returns (peel_ctas, ms) for
+    bpx_opts.peel_ctas."""
+    M, K = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = alloc_C(code, h, N, A.device)
+    best, ms = ct.c_int(), ct.c_float()
+    arr = (ct.c_int * len(ctas))(*ctas) if ctas else None
+    _check(lib().bpx_autotune_peel(code.handle, _ptr(A), _ptr(B), M, N, K, h, precision, _ptr(mask), _ptr(C),
+                                   ws.ptr, ws.nbytes, arr, len(ctas) if ctas else 0, _stream(),
+                                   ct.byref(best), ct.byref(ms)))
+    return best.value, ms.value
+
+
 class Group:
     """A batch of coded multiplications run together (bpx_group_*).
 
@@ -526,6 +545,14 @@ class Group:
         arr = (ct.c_int * len(configs))(*configs) if configs else None
         _check(lib().bpx_group_autotune(self._h, arr, len(configs) if configs else 0, _stream(),
                                         ct.byref(best), ct.byref(ms)))
+        return best.value, ms.value
+
+    def autotune_peel(self, targets=None):
+        """Peel-schedule autotuner: (CTAs per job aimed at, ms of the grouped peel)."""
+        best, ms = ct.c_int(), ct.c_float()
+        arr = (ct.c_int * len(targets))(*targets) if targets else None
+        _check(lib().bpx_group_autotune_peel(self._h, arr, len(targets) if targets else 0, _stream(),
+                                             ct.byref(best), ct.byref(ms)))
         return best.value, ms.value
 
     def __del__(self):

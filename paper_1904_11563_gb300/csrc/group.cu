@@ -28,7 +28,9 @@ struct bpx_group {
   std::vector<bpx::TcSpec> specs;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int graph_key[4] = {0, 0, 0, 0};
+  int graph_key[5] = {0, 0, 0, 0, 0};
+  int peel_target = 0;                // peel CTAs aimed at per job (0 = 4 x the SM count)
+  std::vector<bpx::GJob> host_jobs;   // the device job table's host copy (re-planned peels)
 };
 
 namespace {
@@ -58,6 +60,20 @@ int ensure_table(bpx_group* G, int config, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_fail(e, "grouped GEMM table");
   G->table_config = config;
   return BPX_OK;
+}
+
+// The grouped peel's launch plan: each job's float4 columns cut into chunks
+// so that the job gets about G->peel_target CTAs (0: 4 x the SM count), and
+// the jobs' CTA ranges laid end to end.
+void plan_peel(bpx_group* G) {
+  long long pe = 0;
+  for (auto& g : G->host_jobs) {
+    const long long nv = static_cast<long long>(g.h) * g.N / 4;
+    g.peel_chunk = bpx::peel_chunk_for(nv, G->peel_target);
+    g.peel_base = pe;
+    pe += (nv + g.peel_chunk - 1) / g.peel_chunk;
+  }
+  G->peel_total = pe;
 }
 
 int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
@@ -142,7 +158,7 @@ extern "C" int bpx_group_init(bpx_group* G, void* ws, size_t ws_bytes, bpx_strea
   const int njobs = static_cast<int>(G->jobs.size());
   std::vector<bpx::GJob> gj(njobs);
   G->specs.assign(njobs, bpx::TcSpec{});
-  long long bs = 0, en = 0, pe = 0;
+  long long bs = 0, en = 0;
   for (int j = 0; j < njobs; ++j) {
     const bpx_job& J = G->jobs[j];
     const bpx_code* c = J.code;
@@ -170,10 +186,6 @@ extern "C" int bpx_group_init(bpx_group* G, void* ws, size_t ws_bytes, bpx_strea
     bs += bpx::bsplit_ctas(J.N, J.K);
     g.enc_base = en;
     en += bpx::encode_ctas(static_cast<long long>(c->num_cells) * J.h, J.K);
-    const long long nv = static_cast<long long>(J.h) * J.N / 4;
-    g.peel_chunk = bpx::peel_chunk_for(nv, 0);
-    g.peel_base = pe;
-    pe += (nv + g.peel_chunk - 1) / g.peel_chunk;
     bpx::TcSpec& sp = G->specs[j];
     sp.p = g.p;
     sp.a_hi = g.a_hi;
@@ -190,9 +202,10 @@ extern "C" int bpx_group_init(bpx_group* G, void* ws, size_t ws_bytes, bpx_strea
   }
   G->bsplit_total = bs;
   G->enc_total = en;
-  G->peel_total = pe;
-  cudaError_t e = cudaMemcpyAsync(static_cast<char*>(ws) + G->gjob_off, gj.data(), sizeof(bpx::GJob) * njobs,
-                                  cudaMemcpyHostToDevice, st);
+  G->host_jobs = gj;
+  plan_peel(G);
+  cudaError_t e = cudaMemcpyAsync(static_cast<char*>(ws) + G->gjob_off, G->host_jobs.data(),
+                                  sizeof(bpx::GJob) * njobs, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "bpx_group_init: job table");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bpx_group_init: sync");
   G->table_config = -1;
@@ -222,8 +235,8 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
   cudaStream_t st = S(stream);
   if (!st) return fail(BPX_ERR_INVAL, "bpx_group_graph_launch needs a non-default stream");
   const int config = (opts && opts->gemm_config) ? opts->gemm_config : G->tuned_config;
-  const int key[4] = {config, opts ? opts->direct_write : 1, opts ? opts->compensate_depth : -1, 1};
-  const bool same = G->exec && std::equal(key, key + 4, G->graph_key);
+  const int key[5] = {config, opts ? opts->direct_write : 1, opts ? opts->compensate_depth : -1, 1, G->peel_target};
+  const bool same = G->exec && std::equal(key, key + 5, G->graph_key);
   if (!same) {
     if (int rc = ensure_table(G, config, st)) return rc;
     if (G->exec) cudaGraphExecDestroy(G->exec);
@@ -239,7 +252,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "end capture");
     if ((e = cudaGraphInstantiate(&G->exec, G->graph, 0)) != cudaSuccess) return cuda_fail(e, "instantiate");
-    std::copy(key, key + 4, G->graph_key);
+    std::copy(key, key + 5, G->graph_key);
   }
   cudaError_t e = cudaGraphLaunch(G->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
@@ -364,6 +377,78 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
                 return e == cudaSuccess ? BPX_OK : cuda_fail(e, "autotune launch");
               },
               best_config, best_ms);
+}
+
+extern "C" int bpx_group_autotune_peel(bpx_group* G, const int* targets, int ntargets, bpx_stream stream,
+                                       int* best_target, float* best_ms) {
+  bpx::clear_error();
+  if (!G || !G->ws) return fail(BPX_ERR_INVAL, "bpx_group_autotune_peel: group not initialised");
+  cudaStream_t st = S(stream);
+  const int sms = bpx::num_sms();
+  const int defaults[] = {std::max(1, sms / 8), std::max(1, sms / 4), std::max(1, sms / 2), sms, 2 * sms, 4 * sms,
+                          8 * sms};
+  if (!targets || ntargets <= 0) {
+    targets = defaults;
+    ntargets = static_cast<int>(sizeof(defaults) / sizeof(defaults[0]));
+  }
+  for (int i = 0; i < ntargets; ++i)
+    if (targets[i] < 1) return fail(BPX_ERR_INVAL, "bpx_group_autotune_peel: targets must be >= 1");
+  // one full run so that every job's plan, products and direct blocks exist;
+  // re-running the peel alone then recomputes the same C
+  if (int rc = run_group(G, nullptr, G->tuned_config, st)) return rc;
+  const int njobs = static_cast<int>(G->jobs.size());
+  const auto* gj = reinterpret_cast<const bpx::GJob*>(static_cast<char*>(G->ws) + G->gjob_off);
+  auto upload = [&](int target) -> int {
+    G->peel_target = target;
+    plan_peel(G);
+    cudaError_t e = cudaMemcpyAsync(static_cast<char*>(G->ws) + G->gjob_off, G->host_jobs.data(),
+                                    sizeof(bpx::GJob) * njobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? BPX_OK : cuda_fail(e, "bpx_group_autotune_peel: job table");
+  };
+  int best = targets[0];
+  int rc = tune(targets, ntargets, st,
+                [&](int target) -> int {
+                  if (G->peel_target != target || G->peel_total == 0)
+                    if (int r = upload(target)) return r;
+                  cudaError_t e = bpx::launch_peel_group(gj, njobs, G->peel_total, 2, -1, G->max_sigma, st);
+                  return e == cudaSuccess ? BPX_OK : cuda_fail(e, "autotune launch");
+                },
+                &best, best_ms);
+  if (rc) return rc;
+  if (best_target) *best_target = best;
+  return upload(best);  // also retires a captured graph (the key holds the target)
+}
+
+extern "C" int bpx_autotune_peel(const bpx_code* c, const float* d_A, const float* d_B, int M, int N, int K, int h,
+                                 int precision, const uint8_t* d_mask, float* d_C, void* ws, size_t ws_bytes,
+                                 const int* ctas, int nctas, bpx_stream stream, int* best_ctas, float* best_ms) {
+  bpx::clear_error();
+  if (precision == BPX_EXACT)
+    return fail(BPX_ERR_UNSUPPORTED, "bpx_autotune_peel tunes the floating-point peel (not BPX_EXACT)");
+  const int sms = bpx::num_sms();
+  const int defaults[] = {sms / 2, sms, 2 * sms, 3 * sms, 4 * sms, 8 * sms};
+  if (!ctas || nctas <= 0) {
+    ctas = defaults;
+    nctas = static_cast<int>(sizeof(defaults) / sizeof(defaults[0]));
+  }
+  for (int i = 0; i < nctas; ++i)
+    if (ctas[i] < 1) return fail(BPX_ERR_INVAL, "bpx_autotune_peel: CTA counts must be >= 1");
+  // one full run: plan, products, direct blocks; the peel alone then
+  // recomputes the same C from them
+  if (int rc = bpx_coded_matmul(c, d_A, d_B, M, N, K, h, precision, d_mask, d_C, nullptr, ws, ws_bytes,
+                                nullptr, stream))
+    return rc;
+  const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
+  const float* products = reinterpret_cast<const float*>(static_cast<char*>(ws) + L.products);
+  bpx_opts o = bpx_default_opts();
+  cudaStream_t st = S(stream);
+  return tune(ctas, nctas, st,
+              [&](int n_ctas) -> int {
+                o.peel_ctas = n_ctas;
+                return bpx_peel_decode(c, products, N, h, d_C, 1, &o, ws, stream);
+              },
+              best_ctas, best_ms);
 }
 
 extern "C" void bpx_group_free(bpx_group* G) {

@@ -143,3 +143,55 @@ def test_single_job_autotune_and_tile_configs(libbpx):
         C, info = bpx.coded_matmul(code, dA, dB, h, bpx.BF16X3, m, ws, opts=bpx.default_opts(gemm_config=cfg))
         torch.cuda.synchronize()
         assert np.array_equal(C[:M].cpu().numpy(), refC), cfg
+
+
+def test_peel_autotune_replans_and_stays_exact(libbpx):
+    """The grouped peel-schedule autotuner: the chosen plan (CTAs per job) is
+    one of the candidates, and runs and graph replays under it -- and under
+    every other candidate -- stay bit-exact."""
+    bpx = libbpx
+    jobs, refs = _build(bpx, SPECS, "int", 500)
+    G = bpx.Group(jobs, bpx.BF16X3)
+    cands = [19, 152, 608, 2432]
+    best, ms = G.autotune_peel(cands)
+    assert best in cands and ms > 0
+    for j in jobs:
+        j["C"].zero_()
+    G.run()
+    torch.cuda.synchronize()
+    _check_exact(bpx, jobs, refs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for t in cands:
+            G.autotune_peel([t])           # re-plan to this one target
+            for j in jobs:
+                j["C"].zero_()
+            G.graph_launch()               # the graph is captured again for the new plan
+            stream.synchronize()
+            _check_exact(bpx, jobs, refs)
+
+
+def test_single_job_peel_autotune(libbpx):
+    """bpx_autotune_peel: the fastest peel CTA count among the candidates;
+    the tuned run and the runs under each candidate stay bit-exact."""
+    bpx = libbpx
+    code = bpx.Code.systematic(8, 3, 8)
+    h, M, K, N = 128, 8192, 256, 1000
+    A = W.matrix((M, K), "int", 61)
+    B = W.matrix((K, N), "int", 62)
+    refC = o.reference_product(A, B)
+    m = torch.from_numpy(W.erasure_mask(11, 3, 7)).cuda()
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    for prec in (bpx.BF16X3, bpx.FP32):
+        ws = bpx.Workspace(code, M, N, K, h, prec)
+        C = bpx.alloc_C(code, h, N)
+        cands = [8, 76, 152, 1216]
+        best, ms = bpx.autotune_peel(code, dA, dB, h, prec, m, ws, C=C, ctas=cands)
+        torch.cuda.synchronize()
+        assert best in cands and ms > 0
+        assert np.array_equal(C[:M].cpu().numpy(), refC)
+        for c in cands + [best]:
+            C2, info = bpx.coded_matmul(code, dA, dB, h, prec, m, ws, opts=bpx.default_opts(peel_ctas=c))
+            torch.cuda.synchronize()
+            assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+            assert np.array_equal(C2[:M].cpu().numpy(), refC), (prec, c)
