@@ -127,7 +127,10 @@ def _config(wl):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    """nvidia-smi clock / throttle sampling (every 25 ms) while the timed
+    region runs.  Each sample is stamped with the host time it arrived;
+    begin() / end() bracket the timed loops, and the record keeps the samples
+    inside that window (all samples only when none fell inside)."""
 
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
               "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
@@ -137,12 +140,13 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.window = [None, None]
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -151,33 +155,52 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def begin(self):
+        if self.window[0] is None:
+            self.window[0] = time.time()
+
+    def end(self):
+        self.window[1] = time.time()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)  # the sample that covers the window's end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) != len(self.FIELDS):
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[3:]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+
+        def parse(rows):
+            sm, smax, reasons = [], [], set()
+            for _t, ln in rows:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) != len(self.FIELDS):
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            return sm, smax, reasons
+
+        t0, t1 = self.window
+        inside = [r for r in self.lines if t0 is not None and t1 is not None and t0 <= r[0] <= t1 + 0.03]
+        sm, smax, reasons = parse(inside)
+        in_window = bool(sm)
+        if not sm:
+            sm, smax, reasons = parse(self.lines)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "in_timed_region": in_window,
+                "period_ms": 25}
 
 
 class StageEvents:
@@ -393,6 +416,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        clocks.begin()
         t0.record()
         for i in range(steps):
             o = bpx.default_opts(gemm_config=cfg)
@@ -446,6 +470,7 @@ def run_ours(args, wl):
                 assert si[bpx.INFO_STATUS] == bpx.OK and si[bpx.INFO_DEVICE_ERR] == 0, si
             C_last = slots[(steps - 1) % nf]["C"]  # the last timed step's output (error report)
             del slots
+        clocks.end()
         ms, ms_serial = _max_over_ranks([ms, ms_serial], device=dev)
         stage = {}
         recorded = ["schedule", "a_prep", "gemm", "peel"] + (["b_prep"] if prec != "fp32" else [])
@@ -733,11 +758,13 @@ def run_batch(args):
         time.sleep(0.3)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        clocks.begin()
         t0.record(stream)
         for _ in range(steps):
             G.graph_launch()
         t1.record(stream)
         stream.synchronize()
+        clocks.end()
         ck = clocks.stop()
     ms = t0.elapsed_time(t1) / steps
     ok = all(int(j["info"][bpx.INFO_STATUS].item()) == bpx.OK for j in jobs)
@@ -827,6 +854,7 @@ def run_2d(args, wl):
     time.sleep(0.3)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    clocks.begin()
     t0.record()
     for i in range(steps):
         o_ = bpx.default_opts(gemm_config=args.gemm_config)
@@ -834,6 +862,7 @@ def run_2d(args, wl):
         bpx.coded_matmul_2d(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o_, info=info)
     t1.record()
     torch.cuda.synchronize()
+    clocks.end()
     ck = clocks.stop()
     ms = t0.elapsed_time(t1) / steps
     assert int(info[bpx.INFO_STATUS].item()) == bpx.OK
@@ -929,6 +958,7 @@ def run_straggler(args, wl):
     time.sleep(0.3)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    clocks.begin()
     t0.record()
     for i in range(steps):
         oi = bpx.default_opts(mask_cells=1)
@@ -936,6 +966,7 @@ def run_straggler(args, wl):
         bpx.coded_matmul(code, A, Bm, h, P, plans[warm + i]["mask"], ws, C=C, opts=oi, info=info)
     t1.record()
     torch.cuda.synchronize()
+    clocks.end()
     ck = clocks.stop()
     ms = t0.elapsed_time(t1) / steps
     assert int(info[bpx.INFO_STATUS].item()) == bpx.OK
