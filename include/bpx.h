@@ -328,7 +328,9 @@ int bpx_peel_decode_exact(const bpx_code* code, const int32_t* d_planes, int N, 
 
 /* The whole path for one erasure pattern: schedule, encode + products, peel.
  * The products live in the workspace.  d_info as in bpx_schedule.  With
- * BPX_EXACT, direct_write and compensate_depth are ignored. */
+ * BPX_EXACT, direct_write and compensate_depth are ignored.  0 <= M <= S h:
+ * rows M .. S h - 1 of the source blocks are zero padding (d_A may be NULL
+ * when M = 0; C is then zero). */
 int bpx_coded_matmul(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K,
                      int h, int precision, const uint8_t* d_erasure_mask, float* d_C,
                      const bpx_opts* opts, void* d_ws, size_t ws_bytes, int32_t* d_info,

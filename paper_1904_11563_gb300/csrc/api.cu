@@ -190,7 +190,8 @@ extern "C" int bpx_schedule_cells(const bpx_code* c, const uint8_t* d_cell_mask,
 extern "C" int bpx_encode(const bpx_code* c, const float* d_A, int M, int K, int h,
                           const void* ws, float* d_A_coded, bpx_stream stream) {
   bpx::clear_error();
-  if (!c || !d_A || !d_A_coded || !ws) return fail(BPX_ERR_INVAL, "bpx_encode: NULL argument");
+  // (A may be NULL when M = 0: every source block is then zero padding)
+  if (!c || (!d_A && M > 0) || !d_A_coded || !ws) return fail(BPX_ERR_INVAL, "bpx_encode: NULL argument");
   if (int rc = check_shapes(c, M, 4, K, h)) return rc;
   if (!aligned(d_A, 16) || !aligned(d_A_coded, 16))
     return fail(BPX_ERR_INVAL, "bpx_encode: buffers must be 16-byte aligned");
@@ -207,7 +208,7 @@ namespace {
 int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, int N, int K,
                   int h, int precision, void* ws, size_t ws_bytes, float* d_products, float* d_C,
                   const bpx_opts* opts, int32_t* d_info, cudaStream_t st) {
-  if (!c || !d_A || !d_B || !ws || !d_products)
+  if (!c || (!d_A && M > 0) || !d_B || !ws || !d_products)  // A unused when M = 0
     return fail(BPX_ERR_INVAL, "bpx_coded_products: NULL argument");
   if (int rc = check_shapes(c, M, N, K, h)) return rc;
   if (!aligned(d_A, 16) || !aligned(d_B, 16) || !aligned(d_products, 16) ||

@@ -542,3 +542,39 @@ def test_gathered_peel_waves(libbpx, prec, peel_ctas, comp):
         C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=opts)
         assert info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] > 50
         assert np.array_equal(C[:M], exact), (prec, peel_ctas, comp, t)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "mxfp8", "exact"])
+def test_degenerate_shapes(libbpx, prec):
+    """Edge cases of the path: M = 0 (every source block is zero padding, A
+    empty: C must be zero), the smallest blocks (h = 1, N = 4, the smallest K
+    the precision takes), and no erasure at all on a systematic code (the
+    decode is a copy of the data cells' products) -- each bit for bit on
+    small integers, with the plan's status OK."""
+    bpx = libbpx
+    P = bpx.PRECISIONS[prec]
+    kmin = 128 if prec == "mxfp8" else 8
+    # M = 0
+    code = bpx.Code.table1()
+    A = torch.empty((0, kmin), device="cuda")
+    B = torch.from_numpy(W.matrix((kmin, 4), "int", 71)).cuda()
+    ws = bpx.Workspace(code, 0, 4, kmin, 1, P)
+    C, info = bpx.coded_matmul(code, A, B, 1, P, torch.from_numpy(W.erasure_mask(5, 3, 1)).cuda(), ws)
+    torch.cuda.synchronize()
+    assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+    assert C.shape == (4, 4) and not C.abs().sum().item()
+    # the smallest blocks: h = 1, N = 4
+    An = W.matrix((4, kmin), "int", 72)
+    Bn = W.matrix((kmin, 4), "int", 73)
+    for t in range(3):
+        m = W.erasure_mask(5, 3, 10 + t)
+        Cn, inf = _run(bpx, code, An, Bn, 1, P, m)
+        assert inf[bpx.INFO_STATUS] == bpx.OK
+        assert np.array_equal(Cn, o.reference_product(An, Bn)), (prec, t)
+    # no erasure on a systematic code
+    code_s = bpx.Code.systematic(4, 2, 3)
+    As = W.matrix((24, 2 * kmin), "int", 74)
+    Bs = W.matrix((2 * kmin, 8), "int", 75)
+    Cs, inf = _run(bpx, code_s, As, Bs, 2, P, np.zeros(6, dtype=np.uint8))
+    assert inf[bpx.INFO_STATUS] == bpx.OK and inf[bpx.INFO_WAVES] == 1
+    assert np.array_equal(Cs, o.reference_product(As, Bs))
