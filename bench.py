@@ -610,6 +610,21 @@ def run_ours(args, wl):
                       "gbs": peel_b / (peel_ms * 1e-3) / 1e9 if peel_ms > 0 else None,
                       "frac_hbm": (peel_b / (peel_ms * 1e-3) / 1e9) / hbm if peel_ms > 0 else None,
                       "bytes_def": "sum over non-direct sources of (deg(resolver)+1) h N 4"}
+    # the HBM-bound staging stages against their compulsory bytes: the
+    # encode reads A once and writes the coded rows (bf16 hi + lo: 4 B per
+    # element, or FP32: 4 B), the B split reads B and writes B^T hi + lo
+    def _hbm(nbytes, ms, what):
+        gbs = nbytes / (ms * 1e-3) / 1e9 if ms and ms > 0 else None
+        return {"bytes_per_step": nbytes, "ms": ms, "gbs": gbs, "frac_hbm": gbs / hbm if gbs else None,
+                "bytes_def": what}
+    st_ = R["stage"]
+    if head in ("bf16x3", "bf16", "fp32"):
+        out_b = 4 if head in ("bf16x3", "fp32") else 2
+        line["encode"] = _hbm(4.0 * M * K + out_b * rows_mean * K, st_.get("a_prep", 0.0),
+                              "read A once (4 M K) + write the coded rows (%d B per element)" % out_b)
+    if head in ("bf16x3", "bf16"):
+        line["b_split"] = _hbm(4.0 * K * N + (4 if head == "bf16x3" else 2) * K * N, st_.get("b_prep", 0.0),
+                               "read B (4 K N) + write B^T hi (+ lo) bf16")
     line["clocks"] = R["clocks"]
     per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 4, "exact": 7}[head]
     line["gpu_launches"] = per_step * steps
