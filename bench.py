@@ -111,6 +111,8 @@ def _parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(CODE_TEXT))
     ap.add_argument("--shape", default="",
                     help="M,N,K override of the workload (profiling of reduced cases only)")
+    ap.add_argument("--jobs", type=int, default=512,
+                    help="jobs of the batch512 workload (fewer: profiling of reduced cases only)")
     return ap.parse_args()
 
 
@@ -744,7 +746,7 @@ def run_batch(args):
     from paper_1904_11563_gb300 import workloads as W
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    specs = W.batch_specs(512, 5)
+    specs = W.batch_specs(args.jobs, 5)
     g = torch.Generator(device=dev)
     g.manual_seed(5)
     jobs = []
@@ -820,7 +822,7 @@ def run_batch(args):
     line = {"metric": METRIC, "value": useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
             "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
-            "config": {"workload": "batch512", "code": CODE_TEXT["batch512"], "jobs": 512,
+            "config": {"workload": "batch512", "code": CODE_TEXT["batch512"], "jobs": args.jobs,
                        "dims": "M, N, K = 128 * round(x / 128), x log-uniform on [256, 4096], seeded",
                        "inputs": "A, B iid U(-1,1) FP32, seeded", "useful_tflop_per_batch": useful / 1e12,
                        "launch": "one grouped run per step replayed from a CUDA graph",
