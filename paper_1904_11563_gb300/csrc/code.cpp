@@ -422,7 +422,7 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision,
     const size_t ks = (Kp + 127) / 128;
     L.a_hi = take(rowsA * Kp);
     L.b_hi = take(Np * Kp);
-    L.a_scale = take(((rowsA + 127) / 128) * ks * 512);
+    L.a_scale = take(((rowsA + 255) / 256) * 2 * ks * 512);  // an even tile count: CTA pairs read whole pairs
     L.b_scale = take(((Np + 255) / 256) * ks * 1024);
   }
   L.total = off;

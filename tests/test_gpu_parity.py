@@ -451,11 +451,12 @@ TOL["mxfp8"] = 6e-2
     ("table3", 8, 70, 384, 200),
     ("table1", 130, 520, 128, 260),
 ])
-def test_mxfp8_exact_on_small_integers(libbpx, name, h, M, K, N):
+@pytest.mark.parametrize("cfg", [0, 8001])
+def test_mxfp8_exact_on_small_integers(libbpx, name, h, M, K, N, cfg):
     """MXFP8 (E4M3 with one UE8M0 scale per 32 K-elements): with degree-two
     codes and integers in [-2, 2] every coded 32-run scales onto E4M3 values
     exactly (|x| <= 4 becomes a multiple of 64 or 128 not above 448), so the
-    decode is bit-exact."""
+    decode is bit-exact -- with CTA-pair MMAs (0, the default) and 1-CTA MMAs (8001)."""
     bpx = libbpx
     code, ref = _pair(bpx, name)
     A = W.matrix((M, K), "int", 71)
@@ -463,9 +464,9 @@ def test_mxfp8_exact_on_small_integers(libbpx, name, h, M, K, N):
     ref_C = o.reference_product(A, B)
     for t in range(5):
         m = W.erasure_mask(code.n, t % (code.e + 1), 300 + t)
-        C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m)
+        C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m, opts=bpx.default_opts(gemm_config=cfg))
         assert info[bpx.INFO_STATUS] == bpx.OK
-        assert np.array_equal(C[:M], ref_C), (name, m, np.abs(C[:M] - ref_C).max())
+        assert np.array_equal(C[:M], ref_C), (name, m, cfg, np.abs(C[:M] - ref_C).max())
 
 
 def test_mxfp8_table1_all_masks(libbpx):
@@ -480,15 +481,17 @@ def test_mxfp8_table1_all_masks(libbpx):
         _check_blocks(C, R, ref, A, B, wl["h"], m, "mxfp8")
 
 
-def test_mxfp8_many_tiles(libbpx):
+@pytest.mark.parametrize("cfg", [0, 8001, 4003])
+def test_mxfp8_many_tiles(libbpx, cfg):
     """~600 tiles of 128 x 256 on the benchmark code: the single TMEM
-    accumulator is drained and refilled on every tile of every CTA."""
+    accumulator is drained and refilled on every tile of every CTA (1-CTA,
+    CTA-pair and multicast-pair forms)."""
     bpx = libbpx
     code, ref = _pair(bpx, "sys8_3_8")
     h, M, K, N = 128, 8192, 512, 2048
     A, B = W.inputs(M, K, N, "uniform", 91)
     m = W.erasure_mask(11, 3, 2001)
-    C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m)
+    C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m, opts=bpx.default_opts(gemm_config=cfg))
     assert info[bpx.INFO_STATUS] == bpx.OK
     R, sch = _oracle_decode(ref, A, B, h, m)
     _check_blocks(C, R, ref, A, B, h, m, "mxfp8")
