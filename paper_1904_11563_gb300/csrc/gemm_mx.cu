@@ -302,9 +302,8 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 // (tcgen05.cp.cta_group::2) and issues the M = 256 block-scaled MMAs for the
 // pair; its commits arrive on both CTAs' barriers, and the odd CTA's
 // epilogue warps arrive on the even CTA's accumulator-drained barrier.
-// A CTA's shared memory takes a third less operand traffic per MMA than in
-// the 1-CTA kernel, whose 128 x 256 fp8 tile needs more than an SM's shared
-// memory bandwidth at full MMA rate.
+// A CTA stages a third less operand data per MMA than in the 1-CTA kernel,
+// and the pair shares each B tile's L2 reads.
 constexpr int kMxpStages = 6;
 constexpr uint32_t kMxpA = BM * kMxBK;                 // 16 KB
 constexpr uint32_t kMxpB = (kMxBN / 2) * kMxBK;        // 16 KB: half of the B tile
