@@ -118,7 +118,9 @@ typedef struct {
   int compensate_depth; /* sources deeper than this are peeled in FP64 before one rounding;
                            < 0 (default -1): never */
   int peel_ctas;        /* 0 = auto (a multiple of the SM count) */
-  int gemm_config;      /* 0 = defaults; otherwise band * 1000 + seg_kb * 10 + tile (bpx_autotune) */
+  int gemm_config;      /* 0 = defaults; otherwise band * 1000 + seg_kb * 10 + tile (bpx_autotune).
+                           BPX_MXFP8 reads band * 1000 + tile: tiles 9 / 0 = CTA-pair MMAs (the
+                           default, 16009), 3 / 4 / 7 / 8 = B multicast pairs, others 1-CTA */
   void* const* stage_events; /* NULL, or cudaEvent_t[2 * BPX_NUM_STAGES] created by the caller:
                                 events 2i / 2i+1 are recorded on the stream right before / after
                                 stage i (enum bpx_stage).  Used to time kernels in place. */
