@@ -370,7 +370,7 @@ def run_ours(args, wl):
     if args.precisions:
         precs = [x for x in args.precisions.split(",") if x]
     elif args.precision == "auto":
-        precs = ["bf16x3", "fp32", "mxfp8", "exact"]
+        precs = ["bf16x3", "fp32", "bf16", "mxfp8", "exact"]
     else:
         precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
     results = {}
