@@ -541,15 +541,24 @@ def run_ours(args, wl):
     gemm_ms = R["stage"]["gemm"]
     rows_mean = sum(R["rows"]) / len(R["rows"])
     clk = R["clocks"].get("sm_mhz") or 0
-    if head in ("bf16x3", "bf16"):
-        mult = 3 if head == "bf16x3" else 1
+    if head != "fp32":
+        # tensor-core paths: MMA flops executed per launch (split terms, or
+        # the exact path's digit-pair products) against the measured bf16
+        # peak (FP8: times the nominal fp8 / bf16 ratio of 2)
+        if head == "exact":
+            S_ex = bpx.exact_params(code, K)["S"]
+            mult = S_ex * (S_ex + 1) // 2
+        else:
+            mult = {"bf16x3": 3, "bf16": 1, "mxfp8": 1}[head]
         flops = 2.0 * rows_mean * N * K * mult
         achieved = flops / (gemm_ms * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops", 1900.0)
+        peak = peaks.get("bf16_tflops", 1900.0) * (2.0 if head == "mxfp8" else 1.0)
+        src = "measured bf16 burst (MEASURED_PEAKS.json)" if peaks else "fallback"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _traffic(wl["name"], head, tuned.get(head)),
-                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if peaks else "fallback",
-                "kernel": "coded tcgen05 GEMM", "work_per_launch": "2 x coded rows x N x K x %d MMA flops" % mult}
+                "peak_source": src + (" x 2 (nominal fp8/bf16)" if head == "mxfp8" else ""),
+                "kernel": "coded tcgen05 GEMM" + (" (block-scaled MXFP8)" if head == "mxfp8" else ""),
+                "work_per_launch": "2 x coded rows x N x K x %d MMA flops" % mult}
     else:
         flops = 2.0 * rows_mean * N * K
         achieved = flops / (gemm_ms * 1e-3) / 1e12

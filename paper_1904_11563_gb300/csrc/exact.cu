@@ -40,6 +40,37 @@ __device__ __forceinline__ int exponent_of(uint32_t amax_bits) {
   return e;
 }
 
+// RN_fp32(q 2^e) for an exact integer q, in integer arithmetic: keep the top
+// 24 bits of |q| (fewer where the result is subnormal: its last bit is worth
+// 2^-149), round the dropped bits to nearest even, and assemble the float's
+// bits; a carry out of the significand moves into the exponent field, and a
+// result past the largest float becomes infinity.  One rounding of the exact
+// value, so the same bits as rounding the exact FP64 product q 2^e
+// (|q| < 2^53) to FP32, without the FP64 pipe.
+__device__ __forceinline__ float rn_float_scaled(long long q, int e) {
+  if (q == 0) return 0.f;
+  const uint32_t sign = q < 0 ? 0x80000000u : 0u;
+  const unsigned long long m = q < 0 ? 0ull - static_cast<unsigned long long>(q) : static_cast<unsigned long long>(q);
+  const int top = 63 - __clzll(static_cast<long long>(m));  // m in [2^top, 2^(top + 1))
+  const int E = top + e;                                     // result in [2^E, 2^(E + 1))
+  const int keep = E >= -126 ? 24 : E + 150;                 // significand bits the float holds
+  if (keep < 0) return __uint_as_float(sign);                // below half the smallest subnormal
+  const int drop = top + 1 - keep;
+  unsigned long long mant;
+  if (drop <= 0) {
+    mant = m << -drop;
+  } else {
+    mant = drop >= 64 ? 0ull : m >> drop;
+    const unsigned long long rem = drop >= 64 ? m : m & ((1ull << drop) - 1ull);
+    const unsigned long long half = 1ull << (drop - 1);
+    mant += (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
+  }
+  // normal: ((E + 126) << 23) + mant, mant in [2^23, 2^24]; subnormal: mant
+  const long long bits = E >= -126 ? (static_cast<long long>(E + 126) << 23) + static_cast<long long>(mant)
+                                                 : static_cast<long long>(mant);
+  return __uint_as_float(sign | static_cast<uint32_t>(bits >= 0x7F800000LL ? 0x7F800000LL : bits));
+}
+
 // rint(x 2^shift): exact power-of-two scaling (|result| <= 2^24), then round
 // to nearest even.
 __device__ __forceinline__ int to_fixed(float x, int shift) { return __float2int_rn(ldexpf(x, shift)); }
@@ -224,14 +255,29 @@ exact_peel_kernel(DevPlan p, const int32_t* __restrict__ planes, long long plane
         q[2] += pv.z * sc;
         q[3] += pv.w * sc;
       }
-      for (int e = p.pl_ptr[i], e1 = p.pl_ptr[i + 1]; e < e1; ++e) {
-        const longlong2* src = reinterpret_cast<const longlong2*>(C64 + static_cast<long long>(p.pl_list[e]) * hN) +
-                               2 * v;
-        const longlong2 a = src[0], b = src[1];
-        q[0] -= a.x;
-        q[1] -= a.y;
-        q[2] -= b.x;
-        q[3] -= b.y;
+      // subtrahends four at a time: their loads in flight together (exact
+      // integers, so the order of the subtractions does not matter)
+      for (int e = p.pl_ptr[i], e1 = p.pl_ptr[i + 1]; e < e1; e += 4) {
+        int t[4];
+        longlong2 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = e + u < e1 ? p.pl_list[e + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = b[u] = make_longlong2(0, 0);
+          if (t[u] >= 0) {
+            const longlong2* src = reinterpret_cast<const longlong2*>(C64 + static_cast<long long>(t[u]) * hN) + 2 * v;
+            a[u] = src[0];
+            b[u] = src[1];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          q[0] -= a[u].x;
+          q[1] -= a[u].y;
+          q[2] -= b[u].x;
+          q[3] -= b[u].y;
+        }
       }
       longlong2* dst = reinterpret_cast<longlong2*>(C64 + static_cast<long long>(s) * hN) + 2 * v;
       dst[0] = make_longlong2(q[0], q[1]);
@@ -242,7 +288,7 @@ exact_peel_kernel(DevPlan p, const int32_t* __restrict__ planes, long long plane
       float out[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        out[u] = __double2float_rn(ldexp(__ll2double_rn(q[u]), ej + exponent_of(amax_b[n + u])));
+        out[u] = rn_float_scaled(q[u], ej + exponent_of(amax_b[n + u]));
       *reinterpret_cast<float4*>(C + static_cast<long long>(s) * hN + el) = make_float4(out[0], out[1], out[2], out[3]);
     }
     __syncthreads();
