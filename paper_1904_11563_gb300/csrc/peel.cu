@@ -78,22 +78,28 @@ __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, fl
   }
 }
 
-// Gathered waves: when a wave's blocks over the CTA's columns fit in shared
-// memory (the deep, narrow waves of tall codes with thin blocks), the CTA
-// copies every block element the wave reads -- each position's product and
-// all its subtrahends -- with cp.async into shared memory at once, so that
-// the wave costs one global round trip instead of one per batch of kB
-// subtrahends, with no registers held for the loads in flight.  The wave's
-// descriptors (list offsets, resolvers, sources, subtrahend lists) were
-// staged in shared memory while the previous wave's copies were in flight
-// (two descriptor buffers), so they are off the chain from wave to wave.
-// Thread t works on column t % clen of the CTA's slice for every position
-// and list entry congruent to t / clen.  Wider waves take the register path.
-constexpr int kTermCap = 3840;  // float4 block elements of one wave
+// Gathered waves (tall codes with thin blocks: hundreds of deep, narrow
+// waves).  The CTA copies every block element a wave reads -- each
+// position's product and all its subtrahends over the CTA's columns -- with
+// cp.async into shared memory at once, so that the wave costs one global
+// round trip instead of one per batch of kB subtrahends, with no registers
+// held for the loads in flight.  A wave whose rows exceed the term buffer
+// runs in rounds over runs of its positions (positions of one wave never
+// read each other).  The descriptors of the next wave (list offsets,
+// resolvers, sources, subtrahend lists) are copied into the second of two
+// descriptor buffers with cp.async along with the current wave's first
+// round, and the two scalars that bound them (its first order position and
+// first list entry) are loaded one wave earlier still, so no dependent load
+// sits on the chain from wave to wave.  Thread t works on column t % clen of
+// the CTA's slice for every position and list entry congruent to t / clen.
+// Waves with more positions or list entries than the descriptor buffers hold
+// take the register path.
+constexpr int kTermCap = 5632;  // float4 block elements of one round (88 KB)
 constexpr int kListCap = 2048;  // subtrahend list entries of one wave
-constexpr int kPosCap = 512;    // order positions of one wave
+constexpr int kPosCap = 256;    // order positions of one wave
 constexpr int kGatherMinSources = 1024;  // codes this tall peel in hundreds of waves
 constexpr int kDescInts = kListCap + 3 * kPosCap + 1;  // one descriptor buffer
+// 110 KB: two CTAs of kPeelThreads per SM
 constexpr size_t kGatherSmem = static_cast<size_t>(kTermCap) * 16 + 2 * static_cast<size_t>(kDescInts) * 4;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -101,9 +107,14 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
 struct WaveDesc {
-  int* list;  // subtrahend sources, relative to the wave's first entry
-  int* ptr;   // per position: first list entry (np + 1 values)
+  int* list;  // subtrahend sources, from the wave's first list entry on
+  int* ptr;   // per position: first list entry, absolute (np + 1 values)
   int* res;   // per position: resolving cell
   int* src;   // per position: recovered source
   __device__ WaveDesc(uint8_t* base) {
@@ -114,18 +125,20 @@ struct WaveDesc {
   }
 };
 
-// Stages the descriptors of order positions [o0, o1) (list entries [l0, l1)).
+// Starts the copies of the descriptors of order positions [o0, o1) (list
+// entries [l0, l1)); they land with the caller's next cp.async.wait_all.
 __device__ __forceinline__ void stage_wave(const DevPlan& p, const WaveDesc& w, int o0, int o1, int l0, int l1) {
   const int np = o1 - o0, nl = l1 - l0;
-  for (int t = threadIdx.x; t <= np; t += blockDim.x) w.ptr[t] = p.pl_ptr[o0 + t] - l0;
+  for (int t = threadIdx.x; t <= np; t += blockDim.x) cp_async4(w.ptr + t, p.pl_ptr + o0 + t);
   for (int t = threadIdx.x; t < np; t += blockDim.x) {
-    w.res[t] = p.pl_res[o0 + t];
-    w.src[t] = p.order[o0 + t];
+    cp_async4(w.res + t, p.pl_res + o0 + t);
+    cp_async4(w.src + t, p.order + o0 + t);
   }
-  for (int t = threadIdx.x; t < nl; t += blockDim.x) w.list[t] = p.pl_list[l0 + t];
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) cp_async4(w.list + t, p.pl_list + l0 + t);
 }
 
-// kGather: the launch provides kGatherSmem bytes of dynamic shared memory.
+// kGather: the launch provides kGatherSmem bytes of dynamic shared memory, and
+// sigma * chunk <= kTermCap (one position's rows fit a round).
 template <int kB, bool kGather>
 __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restrict__ P, float* C,
                                           long long nv, int chunk, int first_wave,
@@ -159,68 +172,77 @@ __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restr
   // this thread's column and its first position / entry (stride G)
   const int col = threadIdx.x % clen, g0 = threadIdx.x / clen;
   const int G = static_cast<int>(blockDim.x) / clen;
+  const int cap = kTermCap / clen;  // block rows of one round
   auto fits = [&](int np, int nl) {
-    return kGather && clen <= static_cast<int>(blockDim.x) && np <= kPosCap && nl <= kListCap &&
-           (np + nl) * clen <= kTermCap;
+    return clen <= static_cast<int>(blockDim.x) && np <= kPosCap && nl <= kListCap;
   };
 
+  // wave d spans order positions [o0, o1) and list entries [l0, l1); wave
+  // d + 1 ends at (o2, l2)
   int o0 = p.wave_ptr[first_wave - 1], o1 = p.wave_ptr[first_wave];
   int l0 = p.pl_ptr[o0], l1 = p.pl_ptr[o1];
+  int o2 = first_wave < nwaves ? p.wave_ptr[first_wave + 1] : o1;
+  int l2 = p.pl_ptr[o2];
   bool fit = fits(o1 - o0, l1 - l0);
   int buf = 0;
   if (fit) stage_wave(p, desc(0), o0, o1, l0, l1);
+  asm volatile("cp.async.wait_all;" ::: "memory");  // commit + wait for every copy issued
   __syncthreads();
 
   for (int d = first_wave; d <= nwaves; ++d) {
     const bool comp = compensate_depth >= 0 && d > compensate_depth;
     const bool more = d < nwaves;
-    const int o2 = more ? p.wave_ptr[d + 1] : o1;
-    int l2 = l1;
-    bool nfit = false;
+    const int o3 = d + 1 < nwaves ? p.wave_ptr[d + 2] : o2;  // wave d + 2, consumed after this wave
+    const bool nfit = more && fits(o2 - o1, l2 - l1);
     if (fit) {
       const WaveDesc w = desc(buf);
-      const int np = o1 - o0, nl = l1 - l0, tp = np * clen;
-      // terms [0, np clen): products; list entry e at tp + e clen + column
-      if (g0 < G) {
-        for (int j = g0; j < np; j += G)
-          cp_async16(s_term + j * clen + col, P4 + static_cast<long long>(w.res[j]) * nv + v0 + col);
-        for (int e = g0; e < nl; e += G)
-          cp_async16(s_term + tp + e * clen + col, C4 + static_cast<long long>(w.list[e]) * nv + v0 + col);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      if (more) {  // the next wave's descriptors, while the copies fly
-        l2 = p.pl_ptr[o2];
-        nfit = fits(o2 - o1, l2 - l1);
-        if (nfit) stage_wave(p, desc(buf ^ 1), o1, o2, l1, l2);
-      }
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncthreads();
-      if (g0 < G) {
-        for (int j = g0; j < np; j += G) {
-          const int e0 = w.ptr[j], e1 = w.ptr[j + 1];
-          const float4* t = s_term + tp + col;
-          float4 r;
-          if (!comp) {
-            r = s_term[j * clen + col];
-            for (int e = e0; e < e1; ++e) sub4(r, t[e * clen]);
-          } else {
-            const float4 pr = s_term[j * clen + col];
-            double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
-            for (int e = e0; e < e1; ++e) {
-              const float4 x = t[e * clen];
-              ax -= x.x;
-              ay -= x.y;
-              az -= x.z;
-              aw -= x.w;
-            }
-            r = make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
-                            static_cast<float>(aw));
-          }
-          C4[static_cast<long long>(w.src[j]) * nv + v0 + col] = r;
+      const int np = o1 - o0;
+      // Rounds over runs of positions [j0, j1) whose product and subtrahend
+      // rows fit the term buffer; one round when the whole wave fits.
+      for (int j0 = 0, round = 0; round == 0 || j0 < np; ++round) {
+        int j1 = min(j0 + 1, np);
+        while (j1 < np && (j1 + 1 - j0) + (w.ptr[j1 + 1] - w.ptr[j0]) <= cap) ++j1;
+        const int e0 = w.ptr[j0], e1 = w.ptr[j1], tp = (j1 - j0) * clen;
+        // terms [0, tp): products; list entry e at tp + (e - e0) clen + column
+        if (g0 < G) {
+          for (int j = j0 + g0; j < j1; j += G)
+            cp_async16(s_term + (j - j0) * clen + col, P4 + static_cast<long long>(w.res[j]) * nv + v0 + col);
+          for (int e = e0 + g0; e < e1; e += G)
+            cp_async16(s_term + tp + (e - e0) * clen + col,
+                       C4 + static_cast<long long>(w.list[e - l0]) * nv + v0 + col);
         }
+        if (round == 0 && nfit) stage_wave(p, desc(buf ^ 1), o1, o2, l1, l2);  // with the copies
+        asm volatile("cp.async.wait_all;" ::: "memory");  // commit + wait for every copy issued
+        __syncthreads();
+        if (g0 < G) {
+          const float4* t = s_term + tp + col;
+          for (int j = j0 + g0; j < j1; j += G) {
+            const int f0 = w.ptr[j] - e0, f1 = w.ptr[j + 1] - e0;
+            float4 r;
+            if (!comp) {
+              r = s_term[(j - j0) * clen + col];
+              for (int e = f0; e < f1; ++e) sub4(r, t[e * clen]);
+            } else {
+              const float4 pr = s_term[(j - j0) * clen + col];
+              double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
+              for (int e = f0; e < f1; ++e) {
+                const float4 x = t[e * clen];
+                ax -= x.x;
+                ay -= x.y;
+                az -= x.z;
+                aw -= x.w;
+              }
+              r = make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
+                              static_cast<float>(aw));
+            }
+            C4[static_cast<long long>(w.src[j]) * nv + v0 + col] = r;
+          }
+        }
+        __syncthreads();
+        j0 = j1;
       }
-      __syncthreads();
     } else {
+      if (nfit) stage_wave(p, desc(buf ^ 1), o1, o2, l1, l2);
       const int items = (o1 - o0) * clen;
       for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int j = it / clen;
@@ -230,17 +252,16 @@ __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restr
         else
           peel_item<false, kB>(p, P4, C4, nv, o0 + j, v);
       }
-      if (more) {
-        l2 = p.pl_ptr[o2];
-        nfit = fits(o2 - o1, l2 - l1);
-        if (nfit) stage_wave(p, desc(buf ^ 1), o1, o2, l1, l2);
-      }
+      asm volatile("cp.async.wait_all;" ::: "memory");  // commit + wait for every copy issued
       __syncthreads();
     }
+    const int l3 = p.pl_ptr[o3];
     o0 = o1;
     o1 = o2;
+    o2 = o3;
     l0 = l1;
     l1 = l2;
+    l2 = l3;
     fit = nfit;
     buf ^= 1;
   }
@@ -294,10 +315,10 @@ cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, flo
   if (nv <= 0) return cudaSuccess;
   // Every CTA walks every wave, so the grid never exceeds the CTAs that can
   // be resident at once (a CTA waiting for a slot would repeat the chain).
-  const bool gather = g.S >= kGatherMinSources;
-  const size_t smem = gather ? kGatherSmem : 0;
-  auto launch = [&](auto kern) -> cudaError_t {  // kern: a peel_kernel<kB, gather>
-    if (gather) {
+  // The CTA count: the hint's (default 4 per SM), capped at the CTAs that
+  // can be resident at once for the kernel's shared memory.
+  auto chunk_for = [&](auto kern, size_t smem, long long* chunk) -> cudaError_t {
+    if (smem) {
       const cudaError_t e =
           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
       if (e != cudaSuccess) return e;
@@ -308,17 +329,32 @@ cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, flo
       cudaGetLastError();
       per_sm = 1;
     }
-    long long chunk = peel_chunk_for(nv, ctas);
+    *chunk = peel_chunk_for(nv, ctas);
     const long long slots = static_cast<long long>(per_sm) * num_sms();
-    if ((nv + chunk - 1) / chunk > slots) chunk = (nv + slots - 1) / slots;
+    if ((nv + *chunk - 1) / *chunk > slots) *chunk = (nv + slots - 1) / slots;
+    return cudaSuccess;
+  };
+  auto run = [&](auto kern, size_t smem, long long chunk) -> cudaError_t {
     const unsigned grid = static_cast<unsigned>((nv + chunk - 1) / chunk);
     kern<<<grid, kPeelThreads, smem, st>>>(p, P, C, nv, static_cast<int>(chunk), first_wave, compensate_depth);
     return cudaGetLastError();
   };
+  // The gathered form for tall codes, when one position's rows (at most
+  // sigma) over the CTA's columns fit a round of the term buffer.
+  auto go = [&](auto gather_kern, auto reg_kern) -> cudaError_t {
+    long long chunk = 0;
+    cudaError_t e;
+    if (g.S >= kGatherMinSources) {
+      if ((e = chunk_for(gather_kern, kGatherSmem, &chunk)) != cudaSuccess) return e;
+      if (static_cast<long long>(std::max(1, g.sigma)) * chunk <= kTermCap) return run(gather_kern, kGatherSmem, chunk);
+    }
+    if ((e = chunk_for(reg_kern, 0, &chunk)) != cudaSuccess) return e;
+    return run(reg_kern, 0, chunk);
+  };
   switch (batch_for(g.sigma)) {
-    case 4: return gather ? launch(peel_kernel<4, true>) : launch(peel_kernel<4, false>);
-    case 8: return gather ? launch(peel_kernel<8, true>) : launch(peel_kernel<8, false>);
-    default: return gather ? launch(peel_kernel<16, true>) : launch(peel_kernel<16, false>);
+    case 4: return go(peel_kernel<4, true>, peel_kernel<4, false>);
+    case 8: return go(peel_kernel<8, true>, peel_kernel<8, false>);
+    default: return go(peel_kernel<16, true>, peel_kernel<16, false>);
   }
 }
 

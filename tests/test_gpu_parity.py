@@ -528,10 +528,11 @@ def test_gathered_peel_waves(libbpx, prec, peel_ctas, comp):
     """A tall code (Construction A n=12, k=9, b=120: 1080 sources, ~118
     narrow waves), whose peel gathers each wave's blocks into shared memory.
     Integer inputs keep every product and every peeled row exact, so C must
-    equal A B bit for bit: on the default grid (every wave fits the gather
-    buffer), on a 16-CTA grid whose wide column slices send the wider waves
-    down the register path (both paths in one launch), plain and with the
-    FP64-compensated subtraction on every wave."""
+    equal A B bit for bit: on the default grid (every wave in one round of
+    the term buffer) and on a 16-CTA grid whose wide column slices (128
+    float4 columns: 44 block rows per round) split the wider waves into
+    several rounds, plain and with the FP64-compensated subtraction on every
+    wave."""
     bpx = libbpx
     code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
     h, K, N = 2, 64, 4096
@@ -545,6 +546,48 @@ def test_gathered_peel_waves(libbpx, prec, peel_ctas, comp):
         C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=opts)
         assert info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] > 50
         assert np.array_equal(C[:M], exact), (prec, peel_ctas, comp, t)
+
+
+@pytest.mark.parametrize("comp", [-1, 0])
+def test_gathered_peel_with_register_waves(libbpx, comp):
+    """Both peel forms in one launch: the tall code above extended by 306
+    sources, each in one cell of a new column together with a source that
+    the base code recovers at depth 6, so that wave 7 resolves more than 256
+    positions (beyond the gather descriptors) and takes the register path
+    while every other wave is gathered.  Integer inputs: C equals A B bit for
+    bit, and the schedule equals the oracle's."""
+    bpx = libbpx
+    base = o.construction_a(12, 9, 120)
+    er = list(np.nonzero(W.erasure_mask(12, 3, 5))[0])
+    sch = o.wave_schedule(base, o.surviving_cells(base, er))
+    d0 = 6
+    at_d0 = [s for s in range(base.num_sources) if sch.depth[s] == d0]
+    assert at_d0
+    k, b = 9, 154                       # grid of 1386 source ids: 1080 base + 306 new
+    extra = list(range(base.num_sources, b * k))
+    columns = [[] for _ in range(13)]
+    for c, cell in enumerate(base.cells):
+        columns[base.col_of_cell[c]].append(tuple(cell))
+    columns[12] = [(at_d0[i % len(at_d0)], s) for i, s in enumerate(extra)]
+    code = bpx.Code.from_columns(13, k, b, columns, 3)
+    ref = o.Code(name="mixed", n=13, k=k, b=b, num_sources=b * k,
+                 cells=[tuple(sorted(c)) for col in columns for c in col],
+                 col_of_cell=[j for j, col in enumerate(columns) for _ in col],
+                 heights=[len(col) for col in columns], proj=[None] * 13, e=3)
+    m = W.mask_from_columns(13, er)
+    sch2 = o.wave_schedule(ref, o.surviving_cells(ref, er))
+    assert sch2.ok and sum(1 for s in range(ref.num_sources) if sch2.depth[s] == d0 + 1) > 256
+    h, K, N = 2, 64, 4096
+    M = ref.num_sources * h - 3
+    A = W.matrix((M, K), "int", 93)
+    B = W.matrix((K, N), "int", 94)
+    opts = bpx.default_opts(compensate_depth=comp)
+    for prec in ("fp32", "bf16x3"):
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=opts)
+        assert info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] == sch2.num_waves
+        assert np.array_equal(C[:M], o.reference_product(A, B)), (prec, comp)
+    order, _rec, _i = bpx.schedule(code, torch.from_numpy(m).cuda(), bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32))
+    assert [tuple(int(x) for x in r) for r in order.cpu().numpy()] == [tuple(x) for x in sch2.order]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "mxfp8", "exact"])
