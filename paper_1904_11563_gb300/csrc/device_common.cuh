@@ -124,15 +124,18 @@ struct GJob {
   int M, N, K, h;
   long long bsplit_base, enc_base, peel_base;
   int peel_chunk;
+  int enc_sblocks;  // grouped encode: row blocks per k-chunk, in groups of kEncGroupRows
 };
 
-// Index of the last job whose base (selected by `field`) is <= x.
-template <typename F>
-__device__ __forceinline__ int find_job(const GJob* jobs, int njobs, long long x, F field) {
-  int lo = 0, hi = njobs - 1;
+// Index of the last entry of the ascending array bases[0 .. n) that is <= x:
+// the job of a grouped launch's CTA x.  The bases of one stage sit in a
+// dense array (8 bytes a job, cached by every SM) rather than in the job
+// records, so the search costs a few L1 hits per CTA.
+__device__ __forceinline__ int find_base(const long long* __restrict__ bases, int n, long long x) {
+  int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (field(jobs[mid]) <= x) lo = mid;
+    if (__ldg(bases + mid) <= x) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -157,15 +160,32 @@ __host__ __device__ inline int enc_k_chunks(int K) {
 // Grid sizes of the multi-job kernels for one job.
 inline long long bsplit_ctas(int N, int K) { return static_cast<long long>((N + 63) / 64) * ((K + 63) / 64); }
 inline long long encode_ctas(long long rows, int K) { return enc_row_blocks(rows, K) * enc_k_chunks(K); }
+// The grouped encode's CTA takes kEncGroupRows row blocks of one k-chunk, so
+// that its job search and index arithmetic are shared by more rows.
+constexpr int kEncGroupRows = 4;
+inline long long enc_group_sblocks(long long rows, int K) {
+  return (enc_row_blocks(rows, K) + kEncGroupRows - 1) / kEncGroupRows;
+}
+inline long long encode_group_ctas(long long rows, int K) { return enc_group_sblocks(rows, K) * enc_k_chunks(K); }
 int peel_chunk_for(long long nv, int ctas_hint);
 
 // Launchers (defined in the .cu files).  All return cudaError_t of the launch.
 cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, cudaStream_t st);
-cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st);
-cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, bool split,
-                                      cudaStream_t st);
-cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
-                              int compensate_depth, int max_sigma, cudaStream_t st);
+// d_bases: the jobs' first CTA in the launch, ascending (job order).
+cudaError_t launch_b_split_group(const GJob* d_jobs, const long long* d_bases, int njobs, long long total_ctas,
+                                 cudaStream_t st);
+cudaError_t launch_encode_split_group(const GJob* d_jobs, const long long* d_bases, int njobs,
+                                      long long total_ctas, bool split, cudaStream_t st);
+// Grouped peel: jobs d_order[0 .. ngather) in the gathered form (CTAs
+// [0, gather_ctas)), the rest on the register path (CTAs [gather_ctas,
+// total_ctas)), the latter on `side` between the events when both run;
+// d_bases[i] = the first CTA of job d_order[i].
+cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const long long* d_bases, int njobs,
+                              int ngather, long long gather_ctas, long long total_ctas, int first_wave,
+                              int compensate_depth, int max_sigma, cudaStream_t st, cudaStream_t side,
+                              cudaEvent_t fork, cudaEvent_t join);
+// Whether a job's peel can take the gathered form with this chunk.
+bool peel_gather_ok(int S, int sigma, long long chunk);
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st);
 size_t tc_job_bytes();

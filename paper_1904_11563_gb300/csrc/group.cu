@@ -31,6 +31,16 @@ struct bpx_group {
   int graph_key[5] = {0, 0, 0, 0, 0};
   int peel_target = 0;                // peel CTAs aimed at per job (0 = 4 x the SM count)
   std::vector<bpx::GJob> host_jobs;   // the device job table's host copy (re-planned peels)
+  // peel launch order: the jobs in the gathered form first, then the rest
+  size_t order_off = 0;
+  // the grouped launches' first CTA per job: B split and encode (job order),
+  // peel (peel order), three dense arrays of njobs
+  size_t bases_off = 0;
+  std::vector<int32_t> peel_order;
+  int peel_ngather = 0;
+  long long peel_gather_ctas = 0;
+  cudaStream_t side = nullptr;        // the register-path peel beside the gathered one
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -63,17 +73,68 @@ int ensure_table(bpx_group* G, int config, cudaStream_t st) {
 }
 
 // The grouped peel's launch plan: each job's float4 columns cut into chunks
-// so that the job gets about G->peel_target CTAs (0: 4 x the SM count), and
-// the jobs' CTA ranges laid end to end.
+// so that the job gets about G->peel_target CTAs (0: 4 x the SM count); the
+// jobs whose peel takes the gathered form (tall codes) first, then the rest,
+// their CTA ranges laid end to end in that order.
 void plan_peel(bpx_group* G) {
-  long long pe = 0;
-  for (auto& g : G->host_jobs) {
+  const int njobs = static_cast<int>(G->host_jobs.size());
+  std::vector<int32_t> gat, reg;
+  for (int j = 0; j < njobs; ++j) {
+    auto& g = G->host_jobs[j];
     const long long nv = static_cast<long long>(g.h) * g.N / 4;
     g.peel_chunk = bpx::peel_chunk_for(nv, G->peel_target);
-    g.peel_base = pe;
-    pe += (nv + g.peel_chunk - 1) / g.peel_chunk;
+    const bpx_code* c = G->jobs[j].code;
+    (bpx::peel_gather_ok(c->S, c->sigma, g.peel_chunk) ? gat : reg).push_back(j);
   }
+  long long pe = 0;
+  auto lay = [&](const std::vector<int32_t>& js) {
+    for (int j : js) {
+      auto& g = G->host_jobs[j];
+      const long long nv = static_cast<long long>(g.h) * g.N / 4;
+      g.peel_base = pe;
+      pe += (nv + g.peel_chunk - 1) / g.peel_chunk;
+    }
+  };
+  lay(gat);
+  G->peel_gather_ctas = pe;
+  lay(reg);
   G->peel_total = pe;
+  G->peel_ngather = static_cast<int>(gat.size());
+  G->peel_order = gat;
+  G->peel_order.insert(G->peel_order.end(), reg.begin(), reg.end());
+}
+
+const long long* bases(const bpx_group* G, int which) {  // 0: B split, 1: encode, 2: peel
+  return reinterpret_cast<const long long*>(static_cast<char*>(G->ws) + G->bases_off) + which * G->jobs.size();
+}
+
+// Uploads the job table, the peel order and the base arrays (after plan_peel).
+cudaError_t upload_jobs(bpx_group* G, cudaStream_t st) {
+  const size_t njobs = G->host_jobs.size();
+  std::vector<long long> b(3 * njobs);
+  for (size_t j = 0; j < njobs; ++j) {
+    b[j] = G->host_jobs[j].bsplit_base;
+    b[njobs + j] = G->host_jobs[j].enc_base;
+    b[2 * njobs + j] = G->host_jobs[G->peel_order[j]].peel_base;
+  }
+  cudaError_t e = cudaMemcpyAsync(static_cast<char*>(G->ws) + G->gjob_off, G->host_jobs.data(),
+                                  sizeof(bpx::GJob) * njobs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<char*>(G->ws) + G->order_off, G->peel_order.data(), sizeof(int32_t) * njobs,
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<char*>(G->ws) + G->bases_off, b.data(), sizeof(long long) * b.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+  return e;
+}
+
+cudaError_t launch_group_peel(bpx_group* G, int comp, cudaStream_t st) {
+  const auto* gj = reinterpret_cast<const bpx::GJob*>(static_cast<char*>(G->ws) + G->gjob_off);
+  const auto* order = reinterpret_cast<const int32_t*>(static_cast<char*>(G->ws) + G->order_off);
+  return bpx::launch_peel_group(gj, order, bases(G, 2), static_cast<int>(G->jobs.size()), G->peel_ngather,
+                                G->peel_gather_ctas, G->peel_total, 2, comp, G->max_sigma, st, G->side, G->fork,
+                                G->join);
 }
 
 int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
@@ -88,11 +149,11 @@ int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
     return cuda_fail(e, "grouped schedule");
   mark(o, BPX_STAGE_SCHEDULE, 1, st);
   mark(o, BPX_STAGE_B_PREP, 0, st);
-  if ((e = bpx::launch_b_split_group(gj, njobs, G->bsplit_total, st)) != cudaSuccess)
+  if ((e = bpx::launch_b_split_group(gj, bases(G, 0), njobs, G->bsplit_total, st)) != cudaSuccess)
     return cuda_fail(e, "grouped B split");
   mark(o, BPX_STAGE_B_PREP, 1, st);
   mark(o, BPX_STAGE_A_PREP, 0, st);
-  if ((e = bpx::launch_encode_split_group(gj, njobs, G->enc_total, split, st)) != cudaSuccess)
+  if ((e = bpx::launch_encode_split_group(gj, bases(G, 1), njobs, G->enc_total, split, st)) != cudaSuccess)
     return cuda_fail(e, "grouped encode");
   mark(o, BPX_STAGE_A_PREP, 1, st);
   mark(o, BPX_STAGE_GEMM, 0, st);
@@ -102,8 +163,7 @@ int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
   mark(o, BPX_STAGE_GEMM, 1, st);
   (void)direct;
   mark(o, BPX_STAGE_PEEL, 0, st);
-  if ((e = bpx::launch_peel_group(gj, njobs, G->peel_total, 2, comp, G->max_sigma, st)) != cudaSuccess)
-    return cuda_fail(e, "grouped peel");
+  if ((e = launch_group_peel(G, comp, st)) != cudaSuccess) return cuda_fail(e, "grouped peel");
   mark(o, BPX_STAGE_PEEL, 1, st);
   return BPX_OK;
 }
@@ -139,6 +199,10 @@ extern "C" int bpx_group_create(const bpx_job* jobs, int njobs, int precision, b
   }
   G->gjob_off = off;
   off = bpx::align_up(off + sizeof(bpx::GJob) * njobs, 256);
+  G->order_off = off;
+  off = bpx::align_up(off + sizeof(int32_t) * njobs, 256);
+  G->bases_off = off;
+  off = bpx::align_up(off + 3 * sizeof(long long) * njobs, 256);
   G->tc_off = off;
   off = bpx::align_up(off + bpx::tc_job_bytes() * njobs, 256);
   G->total = off;
@@ -185,7 +249,8 @@ extern "C" int bpx_group_init(bpx_group* G, void* ws, size_t ws_bytes, bpx_strea
     g.bsplit_base = bs;
     bs += bpx::bsplit_ctas(J.N, J.K);
     g.enc_base = en;
-    en += bpx::encode_ctas(static_cast<long long>(c->num_cells) * J.h, J.K);
+    g.enc_sblocks = static_cast<int>(bpx::enc_group_sblocks(static_cast<long long>(c->num_cells) * J.h, J.K));
+    en += bpx::encode_group_ctas(static_cast<long long>(c->num_cells) * J.h, J.K);
     bpx::TcSpec& sp = G->specs[j];
     sp.p = g.p;
     sp.a_hi = g.a_hi;
@@ -204,10 +269,12 @@ extern "C" int bpx_group_init(bpx_group* G, void* ws, size_t ws_bytes, bpx_strea
   G->enc_total = en;
   G->host_jobs = gj;
   plan_peel(G);
-  cudaError_t e = cudaMemcpyAsync(static_cast<char*>(ws) + G->gjob_off, G->host_jobs.data(),
-                                  sizeof(bpx::GJob) * njobs, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "bpx_group_init: job table");
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bpx_group_init: sync");
+  cudaError_t e = cudaSuccess;
+  if (!G->side) e = cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !G->fork) e = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !G->join) e = cudaEventCreateWithFlags(&G->join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_group_init: peel stream and events");
+  if ((e = upload_jobs(G, st)) != cudaSuccess) return cuda_fail(e, "bpx_group_init: job table");
   G->table_config = -1;
   return ensure_table(G, G->tuned_config, st);
 }
@@ -396,14 +463,10 @@ extern "C" int bpx_group_autotune_peel(bpx_group* G, const int* targets, int nta
   // one full run so that every job's plan, products and direct blocks exist;
   // re-running the peel alone then recomputes the same C
   if (int rc = run_group(G, nullptr, G->tuned_config, st)) return rc;
-  const int njobs = static_cast<int>(G->jobs.size());
-  const auto* gj = reinterpret_cast<const bpx::GJob*>(static_cast<char*>(G->ws) + G->gjob_off);
   auto upload = [&](int target) -> int {
     G->peel_target = target;
     plan_peel(G);
-    cudaError_t e = cudaMemcpyAsync(static_cast<char*>(G->ws) + G->gjob_off, G->host_jobs.data(),
-                                    sizeof(bpx::GJob) * njobs, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const cudaError_t e = upload_jobs(G, st);
     return e == cudaSuccess ? BPX_OK : cuda_fail(e, "bpx_group_autotune_peel: job table");
   };
   int best = targets[0];
@@ -411,7 +474,7 @@ extern "C" int bpx_group_autotune_peel(bpx_group* G, const int* targets, int nta
                 [&](int target) -> int {
                   if (G->peel_target != target || G->peel_total == 0)
                     if (int r = upload(target)) return r;
-                  cudaError_t e = bpx::launch_peel_group(gj, njobs, G->peel_total, 2, -1, G->max_sigma, st);
+                  cudaError_t e = launch_group_peel(G, -1, st);
                   return e == cudaSuccess ? BPX_OK : cuda_fail(e, "autotune launch");
                 },
                 &best, best_ms);
@@ -455,5 +518,8 @@ extern "C" void bpx_group_free(bpx_group* G) {
   if (!G) return;
   if (G->exec) cudaGraphExecDestroy(G->exec);
   if (G->graph) cudaGraphDestroy(G->graph);
+  if (G->fork) cudaEventDestroy(G->fork);
+  if (G->join) cudaEventDestroy(G->join);
+  if (G->side) cudaStreamDestroy(G->side);
   delete G;
 }

@@ -274,14 +274,18 @@ peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int 
   peel_body<kB, kGather>(p, P, C, nv, chunk, first_wave, compensate_depth, blockIdx.x);
 }
 
-template <int kB>
+// A grouped peel launch over the jobs order[0 .. n): their CTA ranges lie
+// end to end from `base` on, job order[i] from bases[i].
+template <int kB, bool kGather>
 __global__ void __launch_bounds__(kPeelThreads)
-peel_group_kernel(const GJob* __restrict__ jobs, int njobs, int first_wave, int compensate_depth) {
-  const long long b = blockIdx.x;
-  const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.peel_base; });
-  const GJob& J = jobs[j];
+peel_group_kernel(const GJob* __restrict__ jobs, const int32_t* __restrict__ order,
+                  const long long* __restrict__ bases, int n, long long base, int first_wave,
+                  int compensate_depth) {
+  const long long b = base + blockIdx.x;
+  const int i = find_base(bases, n, b);
+  const GJob& J = jobs[order[i]];
   const long long nv = static_cast<long long>(J.h) * J.N / 4;
-  peel_body<kB, false>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - J.peel_base);
+  peel_body<kB, kGather>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - __ldg(bases + i));
 }
 
 int batch_for(int sigma) { return sigma > 9 ? 16 : (sigma > 5 ? 8 : 4); }
@@ -294,19 +298,53 @@ int peel_chunk_for(long long nv, int ctas_hint) {
   return static_cast<int>(std::max<long long>(8, (chunk + 7) / 8 * 8));
 }
 
-cudaError_t launch_peel_group(const GJob* d_jobs, int njobs, long long total_ctas, int first_wave,
-                              int compensate_depth, int max_sigma, cudaStream_t st) {
+bool peel_gather_ok(int S, int sigma, long long chunk) {
+  return S >= kGatherMinSources && chunk <= kPeelThreads &&
+         static_cast<long long>(std::max(1, sigma)) * chunk <= kTermCap;
+}
+
+cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const long long* d_bases, int njobs,
+                              int ngather, long long gather_ctas, long long total_ctas, int first_wave,
+                              int compensate_depth, int max_sigma, cudaStream_t st, cudaStream_t side,
+                              cudaEvent_t fork, cudaEvent_t join) {
   if (total_ctas <= 0) return cudaSuccess;
-  const unsigned grid = static_cast<unsigned>(total_ctas);
-  // Register path only: a batch runs many short CTAs, and the gather
-  // buffer's shared memory would cut how many fit on an SM (measured slower
-  // on the 512-job batch: 14.0 vs 9.2 ms).
-  switch (batch_for(max_sigma)) {
-    case 4: peel_group_kernel<4><<<grid, kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave, compensate_depth); break;
-    case 8: peel_group_kernel<8><<<grid, kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave, compensate_depth); break;
-    default: peel_group_kernel<16><<<grid, kPeelThreads, 0, st>>>(d_jobs, njobs, first_wave, compensate_depth);
+  const long long reg_ctas = total_ctas - gather_ctas;
+  const bool both = gather_ctas > 0 && reg_ctas > 0;
+  // The register launch goes to the side stream when both run, so that its
+  // short CTAs fill the slots the gather CTAs' shared memory leaves free.
+  cudaError_t e;
+  if (both) {
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  auto go = [&](auto gather_kern, auto reg_kern) -> cudaError_t {
+    if (gather_ctas > 0) {
+      cudaError_t r = cudaFuncSetAttribute(gather_kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(kGatherSmem));
+      if (r != cudaSuccess) return r;
+      gather_kern<<<static_cast<unsigned>(gather_ctas), kPeelThreads, kGatherSmem, st>>>(
+          d_jobs, d_order, d_bases, ngather, 0, first_wave, compensate_depth);
+      if ((r = cudaGetLastError()) != cudaSuccess) return r;
+    }
+    if (reg_ctas > 0) {
+      reg_kern<<<static_cast<unsigned>(reg_ctas), kPeelThreads, 0, both ? side : st>>>(
+          d_jobs, d_order + ngather, d_bases + ngather, njobs - ngather, gather_ctas, first_wave,
+          compensate_depth);
+      return cudaGetLastError();
+    }
+    return cudaSuccess;
+  };
+  switch (batch_for(max_sigma)) {
+    case 4: e = go(peel_group_kernel<4, true>, peel_group_kernel<4, false>); break;
+    case 8: e = go(peel_group_kernel<8, true>, peel_group_kernel<8, false>); break;
+    default: e = go(peel_group_kernel<16, true>, peel_group_kernel<16, false>);
+  }
+  if (e != cudaSuccess) return e;
+  if (both) {
+    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_peel(const DevGraph& g, const DevPlan& p, const float* P, float* C, int N, int h,

@@ -133,26 +133,32 @@ b_split_kernel(const float* __restrict__ B, int K, int N, __nv_bfloat16* bt_hi, 
 
 // Grouped launches: a flat grid over every job's CTAs; each CTA finds its job
 // and its local (x, y) block, x fastest as in the single-job grids.
-__global__ void __launch_bounds__(256) b_split_group_kernel(const GJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(256)
+b_split_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict__ bases, int njobs) {
   const long long b = blockIdx.x;
-  const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.bsplit_base; });
+  const int j = find_base(bases, njobs, b);
   const GJob& J = jobs[j];
-  const long long local = b - J.bsplit_base;
-  const int gx = (J.N + kTile - 1) / kTile;
+  const uint32_t local = static_cast<uint32_t>(b - __ldg(bases + j));  // < 2^31: one launch's CTAs
+  const uint32_t gx = (J.N + kTile - 1) / kTile, by = local / gx;
   b_split_body(J.B, J.K, J.N, static_cast<__nv_bfloat16*>(J.b_hi), static_cast<__nv_bfloat16*>(J.b_lo),
-               static_cast<int>(local % gx), static_cast<int>(local / gx));
+               static_cast<int>(local - by * gx), static_cast<int>(by));
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kEncThreads) encode_group_kernel(const GJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(kEncThreads)
+encode_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict__ bases, int njobs) {
   const long long b = blockIdx.x;
-  const int j = find_job(jobs, njobs, b, [](const GJob& J) { return J.enc_base; });
+  const int j = find_base(bases, njobs, b);
   const GJob& J = jobs[j];
-  const long long local = b - J.enc_base;
-  const long long rblocks = enc_row_blocks(static_cast<long long>(J.g.num_cells) * J.h, J.K);
-  encode_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, nullptr, static_cast<__nv_bfloat16*>(J.a_hi),
-                     static_cast<__nv_bfloat16*>(J.a_lo), static_cast<int>(local % rblocks),
-                     static_cast<int>(local / rblocks));
+  // kEncGroupRows row blocks of one k-chunk (row blocks past the job's rows
+  // return at once: their coded rows are beyond the surviving cells')
+  const uint32_t local = static_cast<uint32_t>(b - __ldg(bases + j));  // < 2^31: one launch's CTAs
+  const uint32_t sb = static_cast<uint32_t>(J.enc_sblocks), kc = local / sb;
+  const int rb0 = static_cast<int>(local - kc * sb) * kEncGroupRows;
+#pragma unroll 1
+  for (int i = 0; i < kEncGroupRows; ++i)
+    encode_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, nullptr, static_cast<__nv_bfloat16*>(J.a_hi),
+                       static_cast<__nv_bfloat16*>(J.a_lo), rb0 + i, static_cast<int>(kc));
 }
 
 // ---- MXFP8 staging -------------------------------------------------------
@@ -319,20 +325,21 @@ cudaError_t launch_encode_split(const DevGraph& g, const DevPlan& p, const float
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_split_group(const GJob* d_jobs, int njobs, long long total_ctas, cudaStream_t st) {
+cudaError_t launch_b_split_group(const GJob* d_jobs, const long long* d_bases, int njobs, long long total_ctas,
+                                 cudaStream_t st) {
   if (total_ctas <= 0) return cudaSuccess;
-  b_split_group_kernel<<<static_cast<unsigned>(total_ctas), 256, 0, st>>>(d_jobs, njobs);
+  b_split_group_kernel<<<static_cast<unsigned>(total_ctas), 256, 0, st>>>(d_jobs, d_bases, njobs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_encode_split_group(const GJob* d_jobs, int njobs, long long total_ctas, bool split,
-                                      cudaStream_t st) {
+cudaError_t launch_encode_split_group(const GJob* d_jobs, const long long* d_bases, int njobs,
+                                      long long total_ctas, bool split, cudaStream_t st) {
   if (total_ctas <= 0) return cudaSuccess;
   // plain bf16 jobs have no lo buffer: the hi-only variant never touches it
   if (split)
-    encode_group_kernel<2><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, njobs);
+    encode_group_kernel<2><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, d_bases, njobs);
   else
-    encode_group_kernel<1><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, njobs);
+    encode_group_kernel<1><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, d_bases, njobs);
   return cudaGetLastError();
 }
 

@@ -171,6 +171,41 @@ def test_peel_autotune_replans_and_stays_exact(libbpx):
             _check_exact(bpx, jobs, refs)
 
 
+# Tall projection codes (more than 1024 sources: hundreds of peel waves),
+# whose peels take the gathered form beside the register-path peels of the
+# small jobs in the same grouped run.
+TALL = [dict(code=("mojette_a", 12, 9, 120), M=2160, N=512, K=256, h=2, e=3, n=12, mask_seed=11),
+        dict(code=("mojette_a", 16, 12, 100), M=1197, N=768, K=128, h=1, e=4, n=16, mask_seed=12)]
+
+
+@pytest.mark.parametrize("comp", [-1, 0])
+def test_grouped_tall_jobs_gathered_peel(libbpx, comp):
+    """A batch mixing two tall Construction A jobs with six small jobs: the
+    grouped peel runs the tall ones in its gathered form and the rest on the
+    register path (two launches side by side), plain and FP64-compensated;
+    bit-exact on integer inputs in a run, in graph replays, and under each
+    peel plan the autotuner tries (wider column slices split waves into
+    rounds)."""
+    bpx = libbpx
+    for sp in TALL:
+        assert o.construction_a(*sp["code"][1:]).num_sources >= 1024
+    jobs, refs = _build(bpx, TALL + SPECS[:6], "int", 600)
+    G = bpx.Group(jobs, bpx.BF16X3)
+    opts = bpx.default_opts(compensate_depth=comp)
+    G.run(opts)
+    torch.cuda.synchronize()
+    _check_exact(bpx, jobs, refs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for t in (2, 19, 608):
+            G.autotune_peel([t])
+            for j in jobs:
+                j["C"].zero_()
+            G.graph_launch(opts)
+            stream.synchronize()
+            _check_exact(bpx, jobs, refs)
+
+
 def test_single_job_peel_autotune(libbpx):
     """bpx_autotune_peel: the fastest peel CTA count among the candidates;
     the tuned run and the runs under each candidate stay bit-exact."""
