@@ -162,7 +162,7 @@ inline long long bsplit_ctas(int N, int K) { return static_cast<long long>((N + 
 inline long long encode_ctas(long long rows, int K) { return enc_row_blocks(rows, K) * enc_k_chunks(K); }
 // The grouped encode's CTA takes kEncGroupRows row blocks of one k-chunk, so
 // that its job search and index arithmetic are shared by more rows.
-constexpr int kEncGroupRows = 4;
+constexpr int kEncGroupRows = 8;
 inline long long enc_group_sblocks(long long rows, int K) {
   return (enc_row_blocks(rows, K) + kEncGroupRows - 1) / kEncGroupRows;
 }

@@ -39,8 +39,8 @@ struct bpx_group {
   std::vector<int32_t> peel_order;
   int peel_ngather = 0;
   long long peel_gather_ctas = 0;
-  cudaStream_t side = nullptr;        // the register-path peel beside the gathered one
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr;        // the B split beside the schedule; the register-path peel beside the gathered one
+  cudaEvent_t fork = nullptr, join = nullptr, fork_b = nullptr, join_b = nullptr;
 };
 
 namespace {
@@ -144,14 +144,22 @@ int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
   const int direct = o ? o->direct_write : 1;
   const int comp = o ? o->compensate_depth : -1;
   cudaError_t e;
+  // The B split needs no plan: it runs on the side stream beside the
+  // schedule (whose tallest jobs take hundreds of dependent rounds), issued
+  // after it so that the schedule's CTAs are placed first.
+  if ((e = cudaEventRecord(G->fork_b, st)) != cudaSuccess) return cuda_fail(e, "grouped B split fork");
   mark(o, BPX_STAGE_SCHEDULE, 0, st);
   if ((e = bpx::launch_schedule_group(gj, njobs, G->max_state_bytes, st)) != cudaSuccess)
     return cuda_fail(e, "grouped schedule");
   mark(o, BPX_STAGE_SCHEDULE, 1, st);
-  mark(o, BPX_STAGE_B_PREP, 0, st);
-  if ((e = bpx::launch_b_split_group(gj, bases(G, 0), njobs, G->bsplit_total, st)) != cudaSuccess)
+  if ((e = cudaStreamWaitEvent(G->side, G->fork_b, 0)) != cudaSuccess) return cuda_fail(e, "grouped B split fork");
+  mark(o, BPX_STAGE_B_PREP, 0, G->side);
+  if ((e = bpx::launch_b_split_group(gj, bases(G, 0), njobs, G->bsplit_total, G->side)) != cudaSuccess)
     return cuda_fail(e, "grouped B split");
-  mark(o, BPX_STAGE_B_PREP, 1, st);
+  mark(o, BPX_STAGE_B_PREP, 1, G->side);
+  if ((e = cudaEventRecord(G->join_b, G->side)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, G->join_b, 0)) != cudaSuccess)
+    return cuda_fail(e, "grouped B split join");
   mark(o, BPX_STAGE_A_PREP, 0, st);
   if ((e = bpx::launch_encode_split_group(gj, bases(G, 1), njobs, G->enc_total, split, st)) != cudaSuccess)
     return cuda_fail(e, "grouped encode");
@@ -273,7 +281,9 @@ extern "C" int bpx_group_init(bpx_group* G, void* ws, size_t ws_bytes, bpx_strea
   if (!G->side) e = cudaStreamCreateWithFlags(&G->side, cudaStreamNonBlocking);
   if (e == cudaSuccess && !G->fork) e = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming);
   if (e == cudaSuccess && !G->join) e = cudaEventCreateWithFlags(&G->join, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(e, "bpx_group_init: peel stream and events");
+  if (e == cudaSuccess && !G->fork_b) e = cudaEventCreateWithFlags(&G->fork_b, cudaEventDisableTiming);
+  if (e == cudaSuccess && !G->join_b) e = cudaEventCreateWithFlags(&G->join_b, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "bpx_group_init: side stream and events");
   if ((e = upload_jobs(G, st)) != cudaSuccess) return cuda_fail(e, "bpx_group_init: job table");
   G->table_config = -1;
   return ensure_table(G, G->tuned_config, st);
@@ -520,6 +530,8 @@ extern "C" void bpx_group_free(bpx_group* G) {
   if (G->graph) cudaGraphDestroy(G->graph);
   if (G->fork) cudaEventDestroy(G->fork);
   if (G->join) cudaEventDestroy(G->join);
+  if (G->fork_b) cudaEventDestroy(G->fork_b);
+  if (G->join_b) cudaEventDestroy(G->join_b);
   if (G->side) cudaStreamDestroy(G->side);
   delete G;
 }
