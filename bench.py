@@ -1004,15 +1004,24 @@ def run_straggler(args, wl):
     timed = plans[warm:]
     useful = 2.0 * M * N * K
     rows = [int((p_["mask"] == 0).sum().item()) * h for p_ in timed]
-    mult = {"bf16x3": 3, "bf16": 1, "fp32": 1}.get(prec)
+    if prec == "exact":
+        S_ex = bpx.exact_params(code, K)["S"]
+        mult = S_ex * (S_ex + 1) // 2     # digit pairs (i, l) with i + l < S
+    else:
+        mult = {"bf16x3": 3, "bf16": 1, "fp32": 1}[prec]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    roof = None
-    if mult and prec != "fp32":
-        ach = 2.0 * float(np.mean(rows)) * N * K * mult / (stage["gemm"] * 1e-3) / 1e12
+    ach = 2.0 * float(np.mean(rows)) * N * K * mult / (stage["gemm"] * 1e-3) / 1e12
+    if prec != "fp32":
         pk = peaks.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": None, "kernel": "coded tcgen05 GEMM"}
+                "traffic": None, "kernel": "coded tcgen05 GEMM",
+                "work_per_launch": "2 x coded rows x N x K x %d MMA flops" % mult}
+    else:
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        pk = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel": "coded FP32 SIMT GEMM", "work_per_launch": "2 x coded rows x N x K"}
     H = sum(1.0 / j for j in range(1, code.num_cells + 1))
     line = {"metric": METRIC, "value": useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
             "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -1027,7 +1036,8 @@ def run_straggler(args, wl):
                       "t_all_cells_expected_unscaled": H / wl["mu"],
                       "units": "1 / mu; T_c = sigma_c X_c"},
             "computed_cells_mean": float(np.mean(rows)) / h,
-            "roofline": roof, "clocks": ck, "gpu_launches": 5 * steps}
+            "roofline": roof, "clocks": ck,
+            "gpu_launches": {"bf16x3": 5, "bf16": 5, "fp32": 4, "exact": 7}[prec] * steps}
     print(json.dumps(line), flush=True)
 
 
