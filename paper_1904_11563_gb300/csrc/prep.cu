@@ -39,18 +39,25 @@ __device__ __forceinline__ void encode_body(const DevGraph& g, const DevPlan& p,
   const int k8 = (kchunk * tpr + threadIdx.x % tpr) * kEncVec;
   if (k8 >= K) return;
   const bool full = k8 + kEncVec <= K;  // K % 8 == 0, so a chunk is full or absent
-  float acc[kEncVec];
+  // the 8 sums as packed pairs (add.rn.f32x2: two FP32 adds an issue slot,
+  // each rounded as a scalar add; the same ascending order per element)
+  uint64_t acc2[kEncVec / 2] = {0, 0, 0, 0};
+  if (full) {
+    for (int e = e0; e < e1; ++e) {
+      const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+      if (arow >= M) continue;
+      const float* src = A + arow * K + k8;
+      uint64_t x[kEncVec / 2];
+      asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(x[0]), "=l"(x[1]) : "l"(src));
+      asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(x[2]), "=l"(x[3]) : "l"(src + 4));
 #pragma unroll
-  for (int i = 0; i < kEncVec; ++i) acc[i] = 0.f;
-  for (int e = e0; e < e1; ++e) {
-    const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
-    if (arow >= M || !full) continue;
-    const float4* src = reinterpret_cast<const float4*>(A + arow * K + k8);
-    const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
-    acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
-    acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
+      for (int q = 0; q < kEncVec / 2; ++q) asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc2[q]) : "l"(x[q]));
+    }
   }
   if (!full) return;
+  float acc[kEncVec];
+#pragma unroll
+  for (int q = 0; q < kEncVec / 2; ++q) asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * q]), "=f"(acc[2 * q + 1]) : "l"(acc2[q]));
   const long long o = static_cast<long long>(row) * K + k8;
   if (kMode == 0) {
     float4* d = reinterpret_cast<float4*>(out_f32 + o);
