@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 
 #include "device_common.cuh"
+#include "rn_scaled.cuh"
 
 namespace bpx {
 namespace {
@@ -38,37 +39,6 @@ __device__ __forceinline__ int exponent_of(uint32_t amax_bits) {
   int e;
   frexpf(m, &e);
   return e;
-}
-
-// RN_fp32(q 2^e) for an exact integer q, in integer arithmetic: keep the top
-// 24 bits of |q| (fewer where the result is subnormal: its last bit is worth
-// 2^-149), round the dropped bits to nearest even, and assemble the float's
-// bits; a carry out of the significand moves into the exponent field, and a
-// result past the largest float becomes infinity.  One rounding of the exact
-// value, so the same bits as rounding the exact FP64 product q 2^e
-// (|q| < 2^53) to FP32, without the FP64 pipe.
-__device__ __forceinline__ float rn_float_scaled(long long q, int e) {
-  if (q == 0) return 0.f;
-  const uint32_t sign = q < 0 ? 0x80000000u : 0u;
-  const unsigned long long m = q < 0 ? 0ull - static_cast<unsigned long long>(q) : static_cast<unsigned long long>(q);
-  const int top = 63 - __clzll(static_cast<long long>(m));  // m in [2^top, 2^(top + 1))
-  const int E = top + e;                                     // result in [2^E, 2^(E + 1))
-  const int keep = E >= -126 ? 24 : E + 150;                 // significand bits the float holds
-  if (keep < 0) return __uint_as_float(sign);                // below half the smallest subnormal
-  const int drop = top + 1 - keep;
-  unsigned long long mant;
-  if (drop <= 0) {
-    mant = m << -drop;
-  } else {
-    mant = drop >= 64 ? 0ull : m >> drop;
-    const unsigned long long rem = drop >= 64 ? m : m & ((1ull << drop) - 1ull);
-    const unsigned long long half = 1ull << (drop - 1);
-    mant += (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
-  }
-  // normal: ((E + 126) << 23) + mant, mant in [2^23, 2^24]; subnormal: mant
-  const long long bits = E >= -126 ? (static_cast<long long>(E + 126) << 23) + static_cast<long long>(mant)
-                                                 : static_cast<long long>(mant);
-  return __uint_as_float(sign | static_cast<uint32_t>(bits >= 0x7F800000LL ? 0x7F800000LL : bits));
 }
 
 // rint(x 2^shift): exact power-of-two scaling (|result| <= 2^24), then round
