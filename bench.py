@@ -103,6 +103,8 @@ def _parse():
     ap.add_argument("--inflight", type=int, default=2,
                     help="steps in flight in the timed region of `value` (each on its own stream with its own "
                          "workspace, C and info words); 1 = one step at a time")
+    ap.add_argument("--compensate-depth", type=int, default=-1,
+                    help="peel the sources deeper than this with compensated subtraction (-1: off)")
     ap.add_argument("--gemm-config", type=int, default=0,
                     help="tensor-core GEMM tile config; 0 = the library default, -1 = run the library's "
                          "autotuner first")
@@ -401,7 +403,7 @@ def run_ours(args, wl):
             if prec in ("bf16x3", "bf16", "exact"):
                 cfg, _tuned_ms = bpx.autotune(code, A, Bm, h, P, masks[0], ws, C=C)
         tuned[prec] = cfg
-        opts = bpx.default_opts(gemm_config=cfg)
+        opts = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth)
         try:
             for i in range(warm):
                 bpx.coded_matmul(code, A, Bm, h, P, masks[i % wl["trials"]], ws, C=C, opts=opts, info=info)
@@ -421,7 +423,7 @@ def run_ours(args, wl):
         clocks.begin()
         t0.record()
         for i in range(steps):
-            o = bpx.default_opts(gemm_config=cfg)
+            o = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth)
             o.stage_events = sev.ptr(i)
             bpx.coded_matmul(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o, info=info)
         t1.record()
@@ -580,6 +582,8 @@ def run_ours(args, wl):
         "%d steps in flight on %d streams (each its own workspace, C and info words); stage times and "
         "the roofline from the same steps run one at a time" % (max(1, args.inflight), max(1, args.inflight))
         if args.inflight > 1 else "one step at a time")
+    if args.compensate_depth >= 0:
+        line["config"]["compensate_depth"] = args.compensate_depth
     line["stages_ms"] = R["stage"]
     line["stages_ms_by_precision"] = {p_: r_["stage"] for p_, r_ in results.items()}
     line["gemm_config"] = tuned
@@ -648,7 +652,7 @@ def run_ours(args, wl):
     # synchronous bpx_coded_matmul_host call per step.
     if not args.no_e2e and rank == 0:
         P = bpx.PRECISIONS[head]
-        o_e2e = bpx.default_opts(gemm_config=tuned.get(head, 0))
+        o_e2e = bpx.default_opts(gemm_config=tuned.get(head, 0), compensate_depth=args.compensate_depth)
         hA = A.cpu().pin_memory()
         hB = Bm.cpu().pin_memory()
         hmasks = [torch.from_numpy(_mask(W, wl, t)).pin_memory() for t in range(wl["trials"])]

@@ -115,8 +115,9 @@ typedef struct {
 typedef struct {
   int direct_write;     /* 1 (default): the product epilogue writes each depth-1 resolver
                            straight into its C block, so the peel skips those sources */
-  int compensate_depth; /* sources deeper than this are peeled in FP64 before one rounding;
-                           < 0 (default -1): never */
+  int compensate_depth; /* sources deeper than this are peeled with compensated subtraction
+                           (TwoSum: each step's rounding error kept in a second FP32 term, one
+                           final rounding); < 0 (default -1): never */
   int peel_ctas;        /* 0 = auto (a multiple of the SM count) */
   int gemm_config;      /* 0 = defaults; otherwise band * 1000 + seg_kb * 10 + tile (bpx_autotune).
                            BPX_MXFP8 reads band * 1000 + tile: tiles 9 / 0 = CTA-pair MMAs (the

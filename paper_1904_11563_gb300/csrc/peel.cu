@@ -32,50 +32,67 @@ __device__ __forceinline__ void sub4(float4& a, const float4& x) {
   a.w -= x.w;
 }
 
+// Compensated subtraction s - x (Knuth's TwoSum of s and -x): t = fl(s - x)
+// and its exact rounding error, which is added to the running error term c
+// (both FP32, no multiplies, so no contraction can change them).  A chain of
+// these ends in one rounding fl(s + c): within about one FP32 rounding of the
+// exact result plus a second-order term, on the FP32 pipes (GB300's FP64
+// rate is a small fraction of its FP32 rate).
+__device__ __forceinline__ void two_sub(float& s, float& c, float x) {
+  const float t = s - x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (-x - bp);
+  s = t;
+}
+
+__device__ __forceinline__ void two_sub4(float4& s, float4& c, const float4& x) {
+  two_sub(s.x, c.x, x.x);
+  two_sub(s.y, c.y, x.y);
+  two_sub(s.z, c.z, x.z);
+  two_sub(s.w, c.w, x.w);
+}
+
+__device__ __forceinline__ float4 two_sum_round(const float4& s, const float4& c) {
+  return make_float4(s.x + c.x, s.y + c.y, s.z + c.z, s.w + c.w);
+}
+
 // One (source, float4) item: C_s[v] = P_r[v] - sum of the listed blocks,
 // subtracted in ascending source id.
-template <bool kF64, int kB>
+template <bool kComp, int kBatch>
 __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, float4* C4, long long nv,
                                           int i, long long v) {
+  // the compensated form holds a second float4 per item: narrower batches
+  // keep the kernel's register count (shared with the plain form) unchanged
+  constexpr int kB = kComp ? (kBatch < 4 ? kBatch : 4) : kBatch;
   const int s = p.order[i];
   const int r = p.pl_res[i];
   int e = p.pl_ptr[i];
   const int e1 = p.pl_ptr[i + 1];
   const float4 pr = ldg_stream(P4 + static_cast<long long>(r) * nv + v);
-  if (!kF64) {
-    // kB list entries, then kB independent block loads, then the ascending
-    // subtractions: two round trips per kB subtrahends.  kB follows the
-    // code's largest degree: wide batches hide latency on deep, sparse
-    // waves; narrow ones keep registers low for the wide, bandwidth-bound
-    // waves of tall blocks.
-    float4 acc = pr;
-    for (; e < e1; e += kB) {
-      int t[kB];
-      float4 x[kB];
+  // kB list entries, then kB independent block loads, then the ascending
+  // subtractions: two round trips per kB subtrahends.  kB follows the code's
+  // largest degree: wide batches hide latency on deep, sparse waves; narrow
+  // ones keep registers low for the wide, bandwidth-bound waves of tall
+  // blocks.  Deep chains (kComp) subtract with TwoSum compensation.
+  float4 acc = pr, err = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (; e < e1; e += kB) {
+    int t[kB];
+    float4 x[kB];
 #pragma unroll
-      for (int q = 0; q < kB; ++q) t[q] = (e + q < e1) ? p.pl_list[e + q] : -1;
+    for (int q = 0; q < kB; ++q) t[q] = (e + q < e1) ? p.pl_list[e + q] : -1;
 #pragma unroll
-      for (int q = 0; q < kB; ++q)
-        x[q] = t[q] >= 0 ? C4[static_cast<long long>(t[q]) * nv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < kB; ++q)
+      x[q] = t[q] >= 0 ? C4[static_cast<long long>(t[q]) * nv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < kB; ++q)
-        if (t[q] >= 0) sub4(acc, x[q]);
+    for (int q = 0; q < kB; ++q) {
+      if (t[q] < 0) continue;
+      if (kComp)
+        two_sub4(acc, err, x[q]);
+      else
+        sub4(acc, x[q]);
     }
-    C4[static_cast<long long>(s) * nv + v] = acc;
-  } else {
-    // Deep chains: subtract in FP64 and round once.
-    double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
-    for (; e < e1; ++e) {
-      const float4 x = C4[p.pl_list[e] * nv + v];
-      ax -= x.x;
-      ay -= x.y;
-      az -= x.z;
-      aw -= x.w;
-    }
-    C4[static_cast<long long>(s) * nv + v] =
-        make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
-                    static_cast<float>(aw));
   }
+  C4[static_cast<long long>(s) * nv + v] = kComp ? two_sum_round(acc, err) : acc;
 }
 
 // Gathered waves (tall codes with thin blocks: hundreds of deep, narrow
@@ -223,17 +240,10 @@ __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restr
               r = s_term[(j - j0) * clen + col];
               for (int e = f0; e < f1; ++e) sub4(r, t[e * clen]);
             } else {
-              const float4 pr = s_term[(j - j0) * clen + col];
-              double ax = pr.x, ay = pr.y, az = pr.z, aw = pr.w;
-              for (int e = f0; e < f1; ++e) {
-                const float4 x = t[e * clen];
-                ax -= x.x;
-                ay -= x.y;
-                az -= x.z;
-                aw -= x.w;
-              }
-              r = make_float4(static_cast<float>(ax), static_cast<float>(ay), static_cast<float>(az),
-                              static_cast<float>(aw));
+              float4 err = make_float4(0.f, 0.f, 0.f, 0.f);
+              r = s_term[(j - j0) * clen + col];
+              for (int e = f0; e < f1; ++e) two_sub4(r, err, t[e * clen]);
+              r = two_sum_round(r, err);
             }
             C4[static_cast<long long>(w.src[j]) * nv + v0 + col] = r;
           }

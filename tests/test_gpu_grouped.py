@@ -182,7 +182,7 @@ TALL = [dict(code=("mojette_a", 12, 9, 120), M=2160, N=512, K=256, h=2, e=3, n=1
 def test_grouped_tall_jobs_gathered_peel(libbpx, comp):
     """A batch mixing two tall Construction A jobs with six small jobs: the
     grouped peel runs the tall ones in its gathered form and the rest on the
-    register path (two launches side by side), plain and FP64-compensated;
+    register path (two launches side by side), plain and compensated;
     bit-exact on integer inputs in a run, in graph replays, and under each
     peel plan the autotuner tries (wider column slices split waves into
     rounds)."""

@@ -249,8 +249,9 @@ def test_undecodable_partial(libbpx):
 
 
 def test_compensated_peel(libbpx):
-    """compensate_depth = 0 forces the FP64 subtraction on every wave; the
-    result stays within tolerance and equals the plain path on integers."""
+    """compensate_depth = 0 forces the compensated subtraction on every
+    wave; the result stays within tolerance and equals the plain path on
+    integers."""
     bpx = libbpx
     code, ref = _pair(bpx, "table3")
     h, M, K, N = 6, 54, 48, 40
@@ -429,7 +430,7 @@ def test_construction_a_full_size_integer_bit_exact(libbpx, prec):
 def test_precision_study_loguniform(libbpx, wl_name, code_name, prec):
     """Precision workload: magnitudes log-uniform on [1e-3, 1e3] with random
     signs (cancellation in the peel), every mask of <= 2 erased columns
-    (Table I also its 3-column ones), compensated (FP64) peel below depth 3;
+    (Table I also its 3-column ones), compensated peel below depth 3;
     every block within its tolerance times its propagation factor."""
     bpx = libbpx
     wl = W.WORKLOADS[wl_name]
@@ -531,7 +532,7 @@ def test_gathered_peel_waves(libbpx, prec, peel_ctas, comp):
     equal A B bit for bit: on the default grid (every wave in one round of
     the term buffer) and on a 16-CTA grid whose wide column slices (128
     float4 columns: 44 block rows per round) split the wider waves into
-    several rounds, plain and with the FP64-compensated subtraction on every
+    several rounds, plain and with the compensated subtraction on every
     wave."""
     bpx = libbpx
     code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
@@ -546,6 +547,61 @@ def test_gathered_peel_waves(libbpx, prec, peel_ctas, comp):
         C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=opts)
         assert info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] > 50
         assert np.array_equal(C[:M], exact), (prec, peel_ctas, comp, t)
+
+
+def _ulps(a, b):
+    """Distance in units in the last place between FP32 arrays (monotone
+    integer map of the bit patterns)."""
+    ai = a.view(np.int32).astype(np.int64)
+    bi = b.view(np.int32).astype(np.int64)
+    ai = np.where(ai < 0, -(ai & 0x7FFFFFFF), ai)
+    bi = np.where(bi < 0, -(bi & 0x7FFFFFFF), bi)
+    return np.abs(ai - bi)
+
+
+@pytest.mark.parametrize("b", [120, 100])
+def test_compensated_subtraction_rounds_once(libbpx, b):
+    """The compensated peel (compensate_depth = 0) rounds each subtraction
+    chain once: every decoded element equals the FP32 rounding of the exact
+    value P_r - sum C_t of its own inputs (the products and the decoded
+    blocks it subtracts), on a deep code with heavy cancellation (sources
+    log-uniform in magnitude on [1e-3, 1e3], random signs; products rounded
+    once from FP64 sums).  The plain peel, rounding after every subtraction,
+    misses that rounding on most elements, so the check discriminates.
+    Construction A n=12, k=9: b = 120 (1080 sources, gathered waves) and
+    b = 100 (900 sources, register path)."""
+    bpx = libbpx
+    code, ref = bpx.Code.mojette_a(12, 9, b), o.construction_a(12, 9, b)
+    h, N = 1, 256
+    m = W.erasure_mask(12, 3, 5)
+    sch = o.wave_schedule(ref, o.surviving_cells(ref, list(np.nonzero(m)[0])))
+    assert sch.ok and sch.num_waves > 50
+    rng = np.random.default_rng(7)
+    S = ref.num_sources
+    X = (np.exp(rng.uniform(np.log(1e-3), np.log(1e3), (S, N))) * rng.choice([-1, 1], (S, N))).astype(np.float32)
+    P = np.zeros((len(ref.cells) * h, N), dtype=np.float32)
+    for c in sorted(set(r for _s, r, _d in sch.order)):
+        P[c] = np.sum(X[list(ref.cells[c])].astype(np.float64), axis=0).astype(np.float32)
+    ws = bpx.Workspace(code, S * h, N, 8, h, bpx.FP32)
+    bpx.schedule(code, torch.from_numpy(m).cuda(), ws)
+    dP = torch.from_numpy(P).cuda()
+    frac = {}
+    for comp in (-1, 0):
+        C = bpx.alloc_C(code, h, N)
+        bpx.peel_decode(code, dP, N, h, C, ws, direct_written=False, opts=bpx.default_opts(compensate_depth=comp))
+        Cn = C.cpu().numpy()
+        worst, exact, total = 0, 0, 0
+        for s, r, d in sch.order:
+            v = P[r].astype(np.float64)
+            for t in ref.cells[r]:
+                if t != s:
+                    v = v - Cn[t].astype(np.float64)
+            u = _ulps(Cn[s], v.astype(np.float32))
+            worst, exact, total = max(worst, int(u.max())), exact + int((u == 0).sum()), total + u.size
+        frac[comp] = exact / total
+        if comp == 0:
+            assert worst <= 1 and frac[0] >= 0.999, (b, worst, frac[0])
+    assert frac[-1] < 0.9, frac
 
 
 @pytest.mark.parametrize("comp", [-1, 0])
