@@ -184,7 +184,7 @@ cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const 
                               int ngather, long long gather_ctas, long long total_ctas, int first_wave,
                               int compensate_depth, int max_sigma, cudaStream_t st, cudaStream_t side,
                               cudaEvent_t fork, cudaEvent_t join);
-// Whether a job's peel can take the gathered form with this chunk.
+// Whether a job's peel can take the gathered form in a grouped launch with this chunk.
 bool peel_gather_ok(int S, int sigma, long long chunk);
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st);

@@ -111,13 +111,17 @@ __device__ __forceinline__ void peel_item(const DevPlan& p, const float4* P4, fl
 // the CTA's slice for every position and list entry congruent to t / clen.
 // Waves with more positions or list entries than the descriptor buffers hold
 // take the register path.
-constexpr int kTermCap = 5632;  // float4 block elements of one round (88 KB)
+constexpr int kTermCap = 5632;       // float4 block elements of one round (88 KB): one job
+constexpr int kTermCapGroup = 3200;  // grouped launches (50 KB): three CTAs per SM for the many chains
 constexpr int kListCap = 2048;  // subtrahend list entries of one wave
 constexpr int kPosCap = 256;    // order positions of one wave
 constexpr int kGatherMinSources = 1024;  // codes this tall peel in hundreds of waves
 constexpr int kDescInts = kListCap + 3 * kPosCap + 1;  // one descriptor buffer
-// 110 KB: two CTAs of kPeelThreads per SM
-constexpr size_t kGatherSmem = static_cast<size_t>(kTermCap) * 16 + 2 * static_cast<size_t>(kDescInts) * 4;
+// dynamic shared memory of the gathered form: 110 KB for one job (two CTAs
+// per SM), 72 KB for grouped launches (three)
+constexpr size_t gather_smem(int cap) { return static_cast<size_t>(cap) * 16 + 2 * static_cast<size_t>(kDescInts) * 4; }
+constexpr size_t kGatherSmem = gather_smem(kTermCap);
+constexpr size_t kGatherSmemGroup = gather_smem(kTermCapGroup);
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
@@ -154,9 +158,9 @@ __device__ __forceinline__ void stage_wave(const DevPlan& p, const WaveDesc& w, 
   for (int t = threadIdx.x; t < nl; t += blockDim.x) cp_async4(w.list + t, p.pl_list + l0 + t);
 }
 
-// kGather: the launch provides kGatherSmem bytes of dynamic shared memory, and
-// sigma * chunk <= kTermCap (one position's rows fit a round).
-template <int kB, bool kGather>
+// kGather: the launch provides gather_smem(kCap) bytes of dynamic shared
+// memory, and sigma * chunk <= kCap (one position's rows fit a round).
+template <int kB, bool kGather, int kCap = kTermCap>
 __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restrict__ P, float* C,
                                           long long nv, int chunk, int first_wave,
                                           int compensate_depth, long long cta) {
@@ -185,11 +189,11 @@ __device__ __forceinline__ void peel_body(const DevPlan& p, const float* __restr
     return;
   }
   float4* s_term = reinterpret_cast<float4*>(peel_smem);
-  auto desc = [&](int b) { return WaveDesc(peel_smem + static_cast<size_t>(kTermCap) * 16 + b * (kDescInts * 4)); };
+  auto desc = [&](int b) { return WaveDesc(peel_smem + static_cast<size_t>(kCap) * 16 + b * (kDescInts * 4)); };
   // this thread's column and its first position / entry (stride G)
   const int col = threadIdx.x % clen, g0 = threadIdx.x / clen;
   const int G = static_cast<int>(blockDim.x) / clen;
-  const int cap = kTermCap / clen;  // block rows of one round
+  const int cap = kCap / clen;  // block rows of one round
   auto fits = [&](int np, int nl) {
     return clen <= static_cast<int>(blockDim.x) && np <= kPosCap && nl <= kListCap;
   };
@@ -295,7 +299,7 @@ peel_group_kernel(const GJob* __restrict__ jobs, const int32_t* __restrict__ ord
   const int i = find_base(bases, n, b);
   const GJob& J = jobs[order[i]];
   const long long nv = static_cast<long long>(J.h) * J.N / 4;
-  peel_body<kB, kGather>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - __ldg(bases + i));
+  peel_body<kB, kGather, kTermCapGroup>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - __ldg(bases + i));
 }
 
 int batch_for(int sigma) { return sigma > 9 ? 16 : (sigma > 5 ? 8 : 4); }
@@ -310,7 +314,7 @@ int peel_chunk_for(long long nv, int ctas_hint) {
 
 bool peel_gather_ok(int S, int sigma, long long chunk) {
   return S >= kGatherMinSources && chunk <= kPeelThreads &&
-         static_cast<long long>(std::max(1, sigma)) * chunk <= kTermCap;
+         static_cast<long long>(std::max(1, sigma)) * chunk <= kTermCapGroup;
 }
 
 cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const long long* d_bases, int njobs,
@@ -330,9 +334,9 @@ cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const 
   auto go = [&](auto gather_kern, auto reg_kern) -> cudaError_t {
     if (gather_ctas > 0) {
       cudaError_t r = cudaFuncSetAttribute(gather_kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(kGatherSmem));
+                                           static_cast<int>(kGatherSmemGroup));
       if (r != cudaSuccess) return r;
-      gather_kern<<<static_cast<unsigned>(gather_ctas), kPeelThreads, kGatherSmem, st>>>(
+      gather_kern<<<static_cast<unsigned>(gather_ctas), kPeelThreads, kGatherSmemGroup, st>>>(
           d_jobs, d_order, d_bases, ngather, 0, first_wave, compensate_depth);
       if ((r = cudaGetLastError()) != cudaSuccess) return r;
     }
