@@ -364,7 +364,7 @@ def test_many_tiles_per_cta(libbpx, prec, cfg):
         _check_blocks(C, R, ref, A, B, h, m, prec)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "bf16", "mxfp8"])
 def test_full_size_sysmoj_8192_sampled(libbpx, prec):
     """The benchmark workload at full size (A, B 8192 x 8192 N(0,1), h = 128,
     3 erased columns) in the benchmark's launch configuration; blocks of C
@@ -391,6 +391,46 @@ def test_full_size_sysmoj_8192_sampled(libbpx, prec):
         c = C[s * h:(s + 1) * h].cpu().numpy()
         err = np.linalg.norm(c - r) / np.linalg.norm(r)
         assert err <= TOL[prec] * max(1.0, nu[s]), (prec, s, sch.depth[s], err, nu[s])
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "mxfp8", "exact"])
+def test_steps_in_flight_on_two_streams(libbpx, prec):
+    """The benchmark's launch configuration: steps in flight on two streams,
+    each with its own workspace, C and info words, issued alternately with
+    different masks -- every step's C equals the same step run alone on the
+    default stream, bit for bit."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 32, 64 * 32, 512, 1024
+    A, B = W.device_inputs(M, K, N, "normal", 81)
+    P = bpx.PRECISIONS[prec]
+    masks = [torch.from_numpy(W.erasure_mask(code.n, 3, 400 + t)).cuda() for t in range(6)]
+    want = []
+    ws0 = bpx.Workspace(code, M, N, K, h, P)
+    for t in range(6):
+        C, info = bpx.coded_matmul(code, A, B, h, P, masks[t], ws0)
+        torch.cuda.synchronize()
+        assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+        want.append(C.clone())
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    wss = [bpx.Workspace(code, M, N, K, h, P) for _ in streams]
+    got = [None] * 6
+    torch.cuda.synchronize()
+    for t in range(6):
+        j = t % 2
+        with torch.cuda.stream(streams[j]):
+            got[t] = bpx.coded_matmul(code, A, B, h, P, masks[t], wss[j])
+            if t >= 4:  # keep the last two in flight together
+                continue
+        if t % 2 == 1:
+            for st in streams:
+                st.synchronize()
+    for st in streams:
+        st.synchronize()
+    for t in range(6):
+        C, info = got[t]
+        assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+        assert torch.equal(C, want[t]), (prec, t)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32"])
