@@ -307,7 +307,8 @@ int bpx_peel_decode(const bpx_code* code, const float* d_products, int N, int h,
  *     P_c^d = sum_{i+l=d} D_i(A_c) D_l(B) exactly;
  *   - the peel forms Q_c = sum_d 2^(w (S-1-d)) P_c^d in int64, subtracts
  *     exactly, and writes C_s = RN_fp32(Q_s 2^(w (S-1) - 2 bits + e_A[j] +
- *     e_B[n])) (Q_s exact in FP64, one rounding).
+ *     e_B[n])): one rounding of the exact value, done in integer arithmetic
+ *     (|Q_s| < 2^53, so the same bits as rounding the exact FP64 value).
  * The only errors are the fixed-point rounding of A and B and the dropped
  * pairs, both about 2^-24 relative to max|A row j| max|B column n| per K term.
  * Products cost S (S+1) / 2 bf16 MMAs per k-step (sigma 2: 6; sigma 8: 10;
