@@ -98,6 +98,24 @@ def test_exact_codes_ragged_bit_exact(libbpx, name, h, M, K, N, dist):
         _assert_bits(C, R, sch, h, M, (name, tuple(m)))
 
 
+@pytest.mark.parametrize("peel_ctas", [0, 4])
+def test_exact_tall_code(libbpx, peel_ctas):
+    """A tall code (Construction A n=12, k=9, b=120: 1080 sources, ~118
+    waves) through the exact path on the default peel grid and on a 4-CTA
+    grid (128 columns a CTA), M short of S h: bit for bit equal to the
+    oracle's exact-slice decode."""
+    bpx = libbpx
+    code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
+    h, K, N = 2, 64, 1024
+    M = ref.num_sources * h - 3
+    A, B = W.inputs(M, K, N, "normal", 67)
+    m = W.erasure_mask(12, 3, 5)
+    C, info = _run(bpx, code, A, B, h, m, opts=bpx.default_opts(peel_ctas=peel_ctas))
+    R, _Q, sch = o.exact_slice_coded_matmul(ref, A, B, h, list(np.nonzero(m)[0]))
+    assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] > 50
+    _assert_bits(C, R, sch, h, M, ("A12_9_120", peel_ctas))
+
+
 def test_exact_planes_then_peel(libbpx):
     """a3 alone: the S int32 diagonal planes of every surviving cell equal
     the oracle's exact digit products; then a4 alone from those planes."""
