@@ -299,7 +299,8 @@ peel_group_kernel(const GJob* __restrict__ jobs, const int32_t* __restrict__ ord
   const int i = find_base(bases, n, b);
   const GJob& J = jobs[order[i]];
   const long long nv = static_cast<long long>(J.h) * J.N / 4;
-  peel_body<kB, kGather, kTermCapGroup>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth, b - __ldg(bases + i));
+  peel_body<kB, kGather, kTermCapGroup>(J.p, J.products, J.C, nv, J.peel_chunk, first_wave, compensate_depth,
+                                        b - __ldg(bases + i));
 }
 
 int batch_for(int sigma) { return sigma > 9 ? 16 : (sigma > 5 ? 8 : 4); }
