@@ -433,14 +433,20 @@ int bpx_group_create(const bpx_job* jobs, int njobs, int precision, bpx_group** 
 size_t bpx_group_workspace_bytes(const bpx_group* group);
 
 /* Binds the workspace: uploads every job's code graph and the job tables,
- * encodes the TMA descriptors; synchronizes `stream`. */
+ * encodes the TMA descriptors, creates the group's side stream and events;
+ * synchronizes `stream`. */
 int bpx_group_init(bpx_group* group, void* d_ws, size_t ws_bytes, bpx_stream stream);
 
 /* Runs every job: one launch per stage over all jobs (a1 schedule, B split,
  * a2 encode + split, one persistent grouped tcgen05 GEMM over all jobs' tiles,
- * a4 peel).  No host synchronization or allocation inside: the call can be
- * captured in a CUDA graph.  Each job's outcome lands in its info words.
- * opts->gemm_config must keep the planned tile width (0 = the planned one). */
+ * a4 peel).  The B split runs on the group's side stream beside the
+ * schedule, and the register-path peel beside the gathered one (tall codes),
+ * forked from and joined back to `stream` with events, so the call is still
+ * ordered on `stream` as one unit.  No host synchronization or allocation
+ * inside: the call can be captured in a CUDA graph.  Each job's outcome lands
+ * in its info words.  Runs of one group must not overlap (they share the
+ * workspace and the side stream).  opts->gemm_config must keep the planned
+ * tile width (0 = the planned one). */
 int bpx_grouped_run(bpx_group* group, const bpx_opts* opts, bpx_stream stream);
 
 /* Captures bpx_grouped_run into a CUDA graph owned by the group on the first
