@@ -121,7 +121,8 @@ typedef struct {
   int peel_ctas;        /* 0 = auto (a multiple of the SM count) */
   int gemm_config;      /* 0 = defaults; otherwise band * 1000 + seg_kb * 10 + tile (bpx_autotune).
                            BPX_MXFP8 reads band * 1000 + tile: tiles 9 / 0 = CTA-pair MMAs (the
-                           default, 16009), 3 / 4 / 7 / 8 = B multicast pairs, others 1-CTA */
+                           default, 16009), 1 / 2 / 5 / 6 = 1-CTA MMAs.  Tile codes 3, 4, 7, 8
+                           and negative values name no kernel: BPX_ERR_INVAL */
   void* const* stage_events; /* NULL, or cudaEvent_t[2 * BPX_NUM_STAGES] created by the caller:
                                 events 2i / 2i+1 are recorded on the stream right before / after
                                 stage i (enum bpx_stage).  Used to time kernels in place. */
@@ -467,8 +468,7 @@ int bpx_group_autotune(bpx_group* group, const int* configs, int nconfigs, bpx_s
 /* Tile autotuner for one coded multiplication on the tensor cores: runs the
  * whole path once, then times the GEMM under each candidate configuration.
  * gemm_config = band * 1000 + seg_kb * 10 + tile, tile 1 = 128x256 and
- * 2 = 128x128 output tiles, 3 / 4 = the same in clusters of two CTAs that
- * share (multicast) each B tile, 5..8 = tiles 1..4 with 32-wide instead of
+ * 2 = 128x128 output tiles, 5 / 6 = tiles 1 / 2 with 32-wide instead of
  * 64-wide k-slices, 0 / 9 = 256x256 tiles computed by CTA-pair MMAs
  * (cta_group::2; each CTA of the cluster holds 128 rows of A and half of
  * the B tile) with 64- / 32-wide k-slices; seg_kb = k-blocks of 64 per TMEM
@@ -476,7 +476,8 @@ int bpx_group_autotune(bpx_group* group, const int* configs, int nconfigs, bpx_s
  * band.  gemm_config 0 = the default, 8080.  Precisions BPX_BF16,
  * BPX_BF16X3 and BPX_EXACT (which uses the tile shape, pairing, k-slice and
  * band, with its own exact segment length; its default is also 8080).
- * Synchronizes. */
+ * Tile codes 3, 4, 7 and 8 name no kernel (BPX_ERR_INVAL).  No kernel loads
+ * by TMA multicast.  Synchronizes. */
 int bpx_autotune(const bpx_code* code, const float* d_A, const float* d_B, int M, int N, int K, int h,
                  int precision, const uint8_t* d_erasure_mask, float* d_C, void* d_ws, size_t ws_bytes,
                  const int* configs, int nconfigs, bpx_stream stream, int* best_config, float* best_ms);

@@ -3,14 +3,19 @@
 Usage: ``python -m paper_1904_11563_gb300.build`` or ``build()`` from Python.
 Each translation unit compiles in its own nvcc process (in parallel); the
 objects go to ``_build/`` beside this file and the shared library next to the
-package's Python files.  A unit is recompiled when it or any header is newer
-than its object.
+package's Python files.  A unit is recompiled unless its object carries the
+SHA-256 of everything that went into it: the unit's text, every header's
+text, the compiler flags, the nvcc release and the host machine type (so an
+object built on another machine or from other sources is never linked).  The
+library is relinked unless it carries the hash of its objects' hashes.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -55,32 +60,68 @@ def _compile(src, obj, verbose, extra):
     return r.stderr
 
 
+def _nvcc_version() -> str:
+    r = subprocess.run([_nvcc(), "--version"], capture_output=True, text=True)
+    return r.stdout.strip().splitlines()[-1] if r.stdout.strip() else "unknown"
+
+
+def _read_hash(path):
+    try:
+        with open(path) as f:
+            return f.read().strip()
+    except OSError:
+        return None
+
+
+def _write_hash(path, h):
+    with open(path, "w") as f:
+        f.write(h + "\n")
+
+
 def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     """Compiles every CUDA/C++ source of the package into libbpx.so; returns
     its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
-    hdr_mtime = max((os.path.getmtime(h) for h in _headers()), default=0.0)
-    jobs = []
-    objs = []
+    common = hashlib.sha256()
+    for part in (*_flags(), *extra_flags, _nvcc_version(), platform.machine(), sys.platform):
+        common.update(part.encode() + b"\0")
+    for hdr in sorted(_headers()):
+        with open(hdr, "rb") as f:
+            common.update(os.path.basename(hdr).encode() + b"\0" + f.read() + b"\0")
+    jobs, objs, hashes = [], [], []
     for s in srcs:
         o = os.path.join(BUILD, os.path.basename(s) + ".o")
+        h = common.copy()
+        with open(s, "rb") as f:
+            h.update(f.read())
+        digest = h.hexdigest()
         objs.append(o)
-        if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_mtime):
-            jobs.append((s, o))
+        hashes.append(digest)
+        if force or not os.path.exists(o) or _read_hash(o + ".sha256") != digest:
+            jobs.append((s, o, digest))
     logs = []
     if jobs:
+        for _s, o, _d in jobs:  # a failed compile leaves no object that looks current
+            if os.path.exists(o + ".sha256"):
+                os.remove(o + ".sha256")
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
-            futs = [ex.submit(_compile, s, o, verbose, list(extra_flags)) for s, o in jobs]
+            futs = [ex.submit(_compile, s, o, verbose, list(extra_flags)) for s, o, _d in jobs]
             for f in futs:
                 logs.append(f.result())
-    if jobs or not os.path.exists(LIB):
+        for _s, o, d in jobs:
+            _write_hash(o + ".sha256", d)
+    lib_digest = hashlib.sha256("".join(hashes).encode()).hexdigest()
+    if jobs or not os.path.exists(LIB) or _read_hash(LIB + ".sha256") != lib_digest:
+        if os.path.exists(LIB + ".sha256"):
+            os.remove(LIB + ".sha256")
         cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        _write_hash(LIB + ".sha256", lib_digest)
     if verbose:
         for lg in logs:
             if lg.strip():

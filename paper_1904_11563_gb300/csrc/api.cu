@@ -220,6 +220,7 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
   const bpx::DevPlan p = bpx::make_plan(ws, L);
   char* base = static_cast<char*>(ws);
   const int config = opts ? opts->gemm_config : 0;
+  if (!bpx::gemm_config_ok(config)) return fail(BPX_ERR_INVAL, "bpx_coded_products: gemm_config %d names no tile", config);
   cudaError_t e = cudaSuccess;
   switch (precision) {
     case BPX_FP32: {
@@ -404,6 +405,8 @@ extern "C" int bpx_coded_matmul_2d(const bpx_code* c, const float* d_A, const fl
   const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision, true);
   if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
   const bpx_opts o = opts ? *opts : bpx_default_opts();
+  if (!bpx::gemm_config_ok(o.gemm_config))
+    return fail(BPX_ERR_INVAL, "bpx_coded_matmul_2d: gemm_config %d names no tile", o.gemm_config);
   cudaStream_t st = S(stream);
   stage_mark(&o, BPX_STAGE_SCHEDULE, 0, st);
   if (int rc = schedule_impl(c, d_mask, o.mask_cells != 0, ws, ws_bytes, nullptr, nullptr, d_info, st)) return rc;
@@ -441,6 +444,8 @@ extern "C" int bpx_coded_matmul(const bpx_code* c, const float* d_A, const float
   if (!c) return fail(BPX_ERR_INVAL, "bpx_coded_matmul: code is NULL");
   if (!d_C) return fail(BPX_ERR_INVAL, "bpx_coded_matmul: C is NULL");
   const bpx_opts o = opts ? *opts : bpx_default_opts();
+  if (!bpx::gemm_config_ok(o.gemm_config))
+    return fail(BPX_ERR_INVAL, "bpx_coded_matmul: gemm_config %d names no tile", o.gemm_config);
   const bpx::WsLayout L = bpx::ws_layout(c, M, N, K, h, precision);
   if (int rc = check_ws(c, ws, ws_bytes, L)) return rc;
   SideStream* side = c->S >= kOverlapSources ? side_stream() : nullptr;

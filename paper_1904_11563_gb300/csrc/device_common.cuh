@@ -186,6 +186,9 @@ cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const 
                               cudaEvent_t fork, cudaEvent_t join);
 // Whether a job's peel can take the gathered form in a grouped launch with this chunk.
 bool peel_gather_ok(int S, int sigma, long long chunk);
+// gemm_config is a tile configuration the GEMM kernels have (tile codes 3,
+// 4, 7 and 8 do not exist; negative values are invalid).
+bool gemm_config_ok(int config);
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st);
 size_t tc_job_bytes();

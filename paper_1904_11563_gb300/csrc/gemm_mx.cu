@@ -87,11 +87,7 @@ __device__ __forceinline__ void raise_mx(const MxParams& P, int code, volatile i
   }
 }
 
-// kPair: clusters of two CTAs take the two m-tiles of a pair with the same B
-// tile; each loads half of the B tile and multicasts it into both CTAs'
-// stages, and each MMA commit releases the stage in both CTAs (as in the
-// bf16 kernel).  The scale blocks are small and loaded by each CTA in full.
-template <bool kPair>
+// One CTA per 128 x 256 tile.
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                const __grid_constant__ MxParams P) {
@@ -104,19 +100,18 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Mc = P.ctr[CTR_NSURV] * P.h;
   const int m_tiles = (Mc + BM - 1) / BM;
-  const int m_units = kPair ? (m_tiles + 1) / 2 : m_tiles;
+  const int m_units = m_tiles;
   const int num_tiles = m_units * P.n_tiles;
   const int k_blocks = P.K / kMxBK;
   const int KS = k_blocks;
-  const uint32_t rank = kPair ? cluster_rank() : 0u;
-  const int cid = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
-  const int nclusters = kPair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+  const int cid = static_cast<int>(blockIdx.x);
+  const int nclusters = static_cast<int>(gridDim.x);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < kMxStages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), kPair ? 2 : 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     mbar_init(smem_u32(&dfull_bar), 1);
     mbar_init(smem_u32(&dempty_bar), 8);
@@ -132,11 +127,10 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
   }
   fence_before();
   __syncthreads();
-  if (kPair) cluster_sync();  // the peer's barriers exist before any multicast lands
   fence_after();
   const uint32_t tmem_base = tmem_base_sh;
 
-  // (m-unit, n) of tile t in bands of m-units, then the CTA's own m-tile
+  // (m, n) of tile t in bands of m-tiles
   auto tile_mn = [&](long long t, int& m, int& n) {
     const int band_tiles = P.group * P.n_tiles;
     const int band = static_cast<int>(t / band_tiles);
@@ -144,7 +138,6 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     const int rows_in_band = min(P.group, m_units - band * P.group);
     m = band * P.group + r % rows_in_band;
     n = r / rows_in_band;
-    if (kPair) m = 2 * m + static_cast<int>(rank);
   };
 
   if (warp == 0) {
@@ -168,13 +161,7 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, kMxTx);
           tma_load_2d(base, &map_a, fb, kb * kMxBK, mt * BM);
-          if (kPair) {
-            constexpr uint32_t kHalf = (kMxBN / 2) * kMxBK;
-            tma_load_2d_mc(base + kMxA + rank * kHalf, &map_b, fb, kb * kMxBK,
-                           nt * kMxBN + static_cast<int>(rank) * (kMxBN / 2), 3);
-          } else {
-            tma_load_2d(base + kMxA, &map_b, fb, kb * kMxBK, nt * kMxBN);
-          }
+          tma_load_2d(base + kMxA, &map_b, fb, kb * kMxBK, nt * kMxBN);
           bulk_load(base + kMxSfa, P.sfa + (static_cast<long long>(mt) * KS + kb) * 512, 512, fb);
           bulk_load(base + kMxSfb, P.sfb + (static_cast<long long>(nt) * KS + kb) * 1024, 1024, fb);
         }
@@ -217,10 +204,7 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 32 fp8 = 32 B
             umma_mx(tmem_base, ad + adv, bd + adv, idesc_mx(kk), sf, sf + 4, (kb == 0 && kk == 0) ? 0u : 1u);
           }
-          if (kPair)
-            umma_commit_mc(smem_u32(&empty_bar[s]), 3);
-          else
-            umma_commit(smem_u32(&empty_bar[s]));
+          umma_commit(smem_u32(&empty_bar[s]));
         }
         if (!ok) break;
         umma_commit(smem_u32(&dfull_bar));
@@ -281,7 +265,6 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 
   fence_before();
   __syncthreads();
-  if (kPair) cluster_sync();  // no CTA leaves while its peer may still write into it
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
@@ -556,19 +539,15 @@ cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, co
   if (K % kMxBK != 0) return cudaErrorInvalidValue;
   const long long rows = static_cast<long long>(num_cells) * h;
   CUtensorMap ma, mb;
-  // config: band * 1000 + tile code; paired tiles (codes 3, 4, 7, 8) share
-  // each B tile through multicast in clusters of two (measured no faster on
-  // the benchmark: the fp8 kernel is bound by the MMA work its four 50 KB
-  // stages can hold, not by the L2 feed)
-  // (codes 9 and 0: 256 x 256 tiles of CTA-pair MMAs, gemm_mx_pair_kernel;
-  // the default (config 0) is 16009, the fastest measured: GEMM 0.501 ms on
-  // the benchmark against 0.533 ms for 1-CTA MMAs)
+  // config: band * 1000 + tile code; codes 9 and 0: 256 x 256 tiles of
+  // CTA-pair MMAs (gemm_mx_pair_kernel; the default, config 0, is 16009, the
+  // fastest measured: GEMM 0.501 ms on the benchmark against 0.533 ms for
+  // 1-CTA MMAs); codes 1, 2, 5, 6: 128 x 256 tiles of 1-CTA MMAs
+  if (!gemm_config_ok(config)) return cudaErrorInvalidValue;
   if (config == 0) config = 16009;
   const int tc = config % 10;
   const bool cta_pair = tc == 9 || tc == 0;
-  const bool paired = config > 0 && (tc == 3 || tc == 4 || tc == 7 || tc == 8);
-  if (!make_map_u8(&ma, a8, rows, K, BM) ||
-      !make_map_u8(&mb, b8, N, K, (paired || cta_pair) ? kMxBN / 2 : kMxBN))
+  if (!make_map_u8(&ma, a8, rows, K, BM) || !make_map_u8(&mb, b8, N, K, cta_pair ? kMxBN / 2 : kMxBN))
     return cudaErrorInvalidValue;
   MxParams P;
   P.sfa = static_cast<const uint8_t*>(sfa);
@@ -625,41 +604,13 @@ cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, co
   }
   const size_t smem = static_cast<size_t>(kMxStages) * kMxStageBytes + 1024;
   const long long tiles = static_cast<long long>(P.m_tiles_max) * P.n_tiles;
-  if (!paired) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_mx_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    const int grid = static_cast<int>(std::min<long long>(tiles, std::max(1, num_sms() - reserved_sms())));
-    if (grid <= 0) return cudaSuccess;
-    gemm_mx_kernel<false><<<grid, kThreads, smem, st>>>(ma, mb, P);
-    return cudaGetLastError();
-  }
-  auto kern = gemm_mx_kernel<true>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaError_t e = cudaFuncSetAttribute(gemm_mx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  if (tiles <= 0) return cudaSuccess;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3(2 * (num_sms() / 2));
-  int resident = 0;
-  if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) != cudaSuccess || resident <= 0) {
-    cudaGetLastError();
-    resident = num_sms() / 2;
-  }
-  resident = std::max(1, resident - (reserved_sms() + 1) / 2);
-  const long long pairs = ((P.m_tiles_max + 1) / 2) * static_cast<long long>(P.n_tiles);
-  const int clusters = static_cast<int>(std::min<long long>(pairs, resident));
-  cfg.gridDim = dim3(2 * clusters);
-  return cudaLaunchKernelEx(&cfg, kern, ma, mb, P);
+  const int grid = static_cast<int>(std::min<long long>(tiles, std::max(1, num_sms() - reserved_sms())));
+  if (grid <= 0) return cudaSuccess;
+  gemm_mx_kernel<<<grid, kThreads, smem, st>>>(ma, mb, P);
+  return cudaGetLastError();
 }
 
 }  // namespace bpx

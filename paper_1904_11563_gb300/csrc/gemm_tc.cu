@@ -175,13 +175,11 @@ __device__ __forceinline__ TileRef locate(const TcJob* jobs, int njobs, long lon
   return R;
 }
 
-// kPair: launched in clusters of two CTAs that take the two m-tiles of a pair
-// with the same B tile; each CTA TMA-loads half of the B tile and multicasts
-// it into both CTAs' stage, and each MMA commit releases the stage in both
-// CTAs, so a stage is refilled only once both have consumed it.
-// kPair == 2: the same pairs of m-tiles, computed by CTA-pair MMAs
-// (cta_group::2, M = 256): each CTA loads only its own A rows and its half of
-// the B tile, so a CTA's shared memory takes a third less traffic per MMA.
+// kPair == 2: launched in clusters of two CTAs that take the two m-tiles of
+// a pair with the same B tile, computed by CTA-pair MMAs (cta_group::2,
+// M = 256): each CTA loads only its own A rows and its half of the B tile,
+// so a CTA's shared memory takes a third less traffic per MMA.  kPair == 0:
+// one CTA per tile.  (No variant loads by TMA multicast.)
 // kMode == kModeExact: exact-slice digit products (plain bf16 MMAs over the
 // digit planes, k-slices of the diagonal's digit pairs in sequence; FP32
 // segments exact by construction, promoted to int32 and stored to the
@@ -193,6 +191,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
                long long total_tiles, int group, int seg_kb) {
   constexpr bool kExact = kMode == kModeExact;
   constexpr bool k2D = kMode == kMode2D;
+  static_assert(kPair == 0 || kPair == 2, "tiles are 1-CTA or CTA-pair MMAs");
   constexpr bool k2Sm = kPair == 2;
   using St = Stage<kSplit, k2Sm ? kBN / 2 : kBN, kBK>;  // a CTA pair holds half the B tile each
   constexpr int kTmemCols = 2 * kBN;  // two FP32 segment accumulators
@@ -222,7 +221,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
     abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), kPair == 1 ? 2 : 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&sfull_bar[a]), 1);
@@ -248,7 +247,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
   }
   fence_before();
   __syncthreads();
-  if (kPair) cluster_sync();  // the peer's barriers exist before any multicast lands
+  if (kPair) cluster_sync();  // the peer's barriers exist before any of its copies or commits land
   fence_after();
   const uint32_t tmem_base = tmem_base_sh;
 
@@ -313,16 +312,8 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           mbar_expect_tx(fb, St::kBytes);
           tma_load_2d(base + St::kAhi, &T.J->map_ahi, fb, xa, ya);
           if (kSplit) tma_load_2d(base + St::kAlo, &T.J->map_alo, fb, xa, ya);
-          if (kPair) {
-            // this CTA's half of the B tile, into both CTAs of the pair
-            constexpr uint32_t kHalf = (kBN / 2) * kBK * 2;
-            const int yh = yb + static_cast<int>(rank) * (kBN / 2);
-            tma_load_2d_mc(base + St::kBhi + rank * kHalf, &T.J->map_bhi, fb, xb, yh, 3);
-            if (kSplit) tma_load_2d_mc(base + St::kBlo + rank * kHalf, &T.J->map_blo, fb, xb, yh, 3);
-          } else {
-            tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, xb, yb);
-            if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, xb, yb);
-          }
+          tma_load_2d(base + St::kBhi, &T.J->map_bhi, fb, xb, yb);
+          if (kSplit) tma_load_2d(base + St::kBlo, &T.J->map_blo, fb, xb, yb);
         }
       }
       if ((!ok || abort_flag) && !(k2Sm && rank != 0)) {
@@ -390,8 +381,6 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
             }
             if (k2Sm)
               umma_commit_pair(smem_u32(&empty_bar[s]));
-            else if (kPair)
-              umma_commit_mc(smem_u32(&empty_bar[s]), 3);
             else
               umma_commit(smem_u32(&empty_bar[s]));
           }
@@ -552,20 +541,22 @@ bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box
 }
 
 // Tile configurations the autotuner chooses among (gemm_config % 10):
-// 1 = 128x256, 2 = 128x128, 3 = 128x256 paired (B multicast), 4 = 128x128
-// paired; 5..8 = the same with 32-wide k-slices (64-byte swizzle, twice the
-// stages of half the size); 9 / 0 = 256x256 tiles of CTA-pair MMAs (128x256
-// per CTA) with 32- / 64-wide k-slices.
+// 1 = 128x256, 2 = 128x128, 5 / 6 = the same with 32-wide k-slices (64-byte
+// swizzle, twice the stages of half the size); 9 / 0 = 256x256 tiles of
+// CTA-pair MMAs (128x256 per CTA) with 32- / 64-wide k-slices.  Codes 3, 4,
+// 7 and 8 are not tile configurations (rejected as invalid).
+bool tile_valid(int config) {
+  const int t = config % 10;
+  return config >= 0 && t != 3 && t != 4 && t != 7 && t != 8;
+}
 int tile_bn(int config) {
   const int t = config % 10;
-  return (t == 2 || t == 4 || t == 6 || t == 8) ? 128 : 256;
+  return (t == 2 || t == 6) ? 128 : 256;
 }
-// 0: one CTA per tile; 1: CTA pairs sharing the B tile by multicast; 2: CTA
-// pairs computing one tile with cta_group::2 MMAs.
+// 0: one CTA per tile; 2: CTA pairs computing one tile with cta_group::2 MMAs.
 int tile_pair(int config) {
   const int t = config % 10;
-  if (t == 9 || t == 0) return 2;
-  return (t == 3 || t == 4 || t == 7 || t == 8) ? 1 : 0;
+  return (t == 9 || t == 0) ? 2 : 0;
 }
 int tile_bk(int config) { return (config % 10) >= 5 ? 32 : 64; }
 
@@ -582,7 +573,7 @@ cudaError_t launch_variant(const TcJob& single, const TcJob* table, int njobs, l
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (total_tiles <= 0) return cudaSuccess;
-  if (!kPair) {
+  if (kPair == 0) {
     const int grid = static_cast<int>(std::min<long long>(total_tiles, std::max(1, num_sms() - reserved_sms())));
     kern<<<grid, kThreads, smem, st>>>(single, table, njobs, total_tiles, group, seg_kb);
     return cudaGetLastError();
@@ -619,13 +610,9 @@ cudaError_t dispatch_bk(bool split3, int bn, int pair, const TcJob& single, cons
 #define BPX_LV(SPLIT, STAGES, BN, PAIR) \
   launch_variant<SPLIT, STAGES, BN, PAIR, kBK, kMode>(single, table, njobs, total_tiles, group, seg_kb, st)
   // CTA-pair MMAs: a stage holds the CTA's A rows and half the B tile
-  if (pair == 2 && bn == 256) return split3 ? BPX_LV(true, 3 * m, 256, 2) : BPX_LV(false, 6 * m, 256, 2);
-  if (split3) {
-    if (bn == 128) return pair ? BPX_LV(true, 3 * m, 128, true) : BPX_LV(true, 3 * m, 128, false);
-    return pair ? BPX_LV(true, 2 * m, 256, true) : BPX_LV(true, 2 * m, 256, false);
-  }
-  if (bn == 128) return pair ? BPX_LV(false, 6 * m, 128, true) : BPX_LV(false, 6 * m, 128, false);
-  return pair ? BPX_LV(false, 4 * m, 256, true) : BPX_LV(false, 4 * m, 256, false);
+  if (pair == 2) return split3 ? BPX_LV(true, 3 * m, 256, 2) : BPX_LV(false, 6 * m, 256, 2);
+  if (split3) return bn == 128 ? BPX_LV(true, 3 * m, 128, 0) : BPX_LV(true, 2 * m, 256, 0);
+  return bn == 128 ? BPX_LV(false, 6 * m, 128, 0) : BPX_LV(false, 4 * m, 256, 0);
 #undef BPX_LV
 }
 
@@ -636,13 +623,10 @@ template <int kBK>
 cudaError_t dispatch_exact_bk(int bn, int pair, const TcJob& J, long long total_tiles, int group, int seg,
                               cudaStream_t st) {
   constexpr int m = BK / kBK;
-  if (pair == 2 && bn == 256)
+  if (pair == 2)
     return launch_variant<false, 6 * m, 256, 2, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
-  if (bn == 128)
-    return pair ? launch_variant<false, 6 * m, 128, true, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st)
-                : launch_variant<false, 6 * m, 128, false, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
-  return pair ? launch_variant<false, 4 * m, 256, true, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st)
-              : launch_variant<false, 4 * m, 256, false, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
+  if (bn == 128) return launch_variant<false, 6 * m, 128, 0, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
+  return launch_variant<false, 4 * m, 256, 0, kBK, kModeExact>(J, nullptr, 1, total_tiles, group, seg, st);
 }
 
 cudaError_t dispatch_exact(int bn, int pair, int bk, const TcJob& J, long long total_tiles, int group, int seg,
@@ -726,6 +710,7 @@ bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo,
 // d_table (n * tc_job_bytes() bytes) and synchronises.
 cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, void* d_table,
                            long long* total_tiles, cudaStream_t st) {
+  if (!tile_valid(config)) return cudaErrorInvalidValue;
   int group, seg_kb, bn, bk;
   int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
@@ -751,10 +736,13 @@ cudaError_t tc_build_table(const TcSpec* specs, int n, bool split3, int config, 
 
 size_t tc_job_bytes() { return sizeof(TcJob); }
 
+bool gemm_config_ok(int config) { return tile_valid(config); }
+
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
                            const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
                            bool split3, float* products, float* C_direct, int config,
                            int32_t* info_out, cudaStream_t st) {
+  if (!tile_valid(config)) return cudaErrorInvalidValue;
   (void)g;
   int group, seg_kb, bn, bk;
   int pair;
@@ -774,6 +762,7 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
 cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void* b_planes, int num_cells, int N,
                               int K, int h, const ExactParams& P, int32_t* planes, int config, int32_t* info_out,
                               cudaStream_t st) {
+  if (!tile_valid(config)) return cudaErrorInvalidValue;
   int group, seg_kb, bn, bk;
   int pair;
   // Default: 256x256 tiles of CTA-pair MMAs, 64-wide k-slices, bands of 8
@@ -801,6 +790,7 @@ cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void
 cudaError_t launch_gemm_2d(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
                            const void* b_lo, int N, int K, int h, int w, bool split3, float* products,
                            float* C_direct, int config, int32_t* info_out, cudaStream_t st) {
+  if (!tile_valid(config)) return cudaErrorInvalidValue;
   int group, seg_kb, bn, bk;
   int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
@@ -845,6 +835,7 @@ cudaError_t launch_gemm_2d(const DevGraph& g, const DevPlan& p, const void* a_hi
 // Grouped launch over a device table of jobs (tile_base set, maps encoded).
 cudaError_t launch_gemm_tc_grouped(const void* d_jobs, int njobs, long long total_tiles, bool split3,
                                    int config, cudaStream_t st) {
+  if (!tile_valid(config)) return cudaErrorInvalidValue;
   int group, seg_kb, bn, bk;
   int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);

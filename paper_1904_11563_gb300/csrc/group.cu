@@ -293,6 +293,7 @@ extern "C" int bpx_grouped_run(bpx_group* G, const bpx_opts* opts, bpx_stream st
   bpx::clear_error();
   if (!G || !G->ws) return fail(BPX_ERR_INVAL, "bpx_grouped_run: group not initialised");
   const int config = (opts && opts->gemm_config) ? opts->gemm_config : G->tuned_config;
+  if (!bpx::gemm_config_ok(config)) return fail(BPX_ERR_INVAL, "bpx_grouped_run: gemm_config %d names no tile", config);
   if (tile_of(config) != tile_of(G->table_config))
     return fail(BPX_ERR_INVAL, "bpx_grouped_run: tile shape %d differs from the planned one; "
                 "call bpx_group_autotune or bpx_group_set_config first", tile_of(config));
@@ -302,6 +303,7 @@ extern "C" int bpx_grouped_run(bpx_group* G, const bpx_opts* opts, bpx_stream st
 extern "C" int bpx_group_set_config(bpx_group* G, int config, bpx_stream stream) {
   bpx::clear_error();
   if (!G || !G->ws) return fail(BPX_ERR_INVAL, "bpx_group_set_config: group not initialised");
+  if (!bpx::gemm_config_ok(config)) return fail(BPX_ERR_INVAL, "bpx_group_set_config: gemm_config %d names no tile", config);
   G->tuned_config = config;
   return ensure_table(G, config, S(stream));
 }
@@ -312,6 +314,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
   cudaStream_t st = S(stream);
   if (!st) return fail(BPX_ERR_INVAL, "bpx_group_graph_launch needs a non-default stream");
   const int config = (opts && opts->gemm_config) ? opts->gemm_config : G->tuned_config;
+  if (!bpx::gemm_config_ok(config)) return fail(BPX_ERR_INVAL, "bpx_group_graph_launch: gemm_config %d names no tile", config);
   const int key[5] = {config, opts ? opts->direct_write : 1, opts ? opts->compensate_depth : -1, 1, G->peel_target};
   const bool same = G->exec && std::equal(key, key + 5, G->graph_key);
   if (!same) {
@@ -338,7 +341,7 @@ extern "C" int bpx_group_graph_launch(bpx_group* G, const bpx_opts* opts, bpx_st
 
 namespace {
 
-const int kDefaultConfigs[] = {8080, 16080, 4080, 8089, 16089, 8087, 16087, 8085, 8047, 16041, 8086, 8088};
+const int kDefaultConfigs[] = {8080, 16080, 4080, 8089, 16089, 8085, 16041, 8086, 16042};
 
 // Times `launch` on each config (one warm-up, then the best of three) and
 // returns the fastest.
@@ -353,6 +356,8 @@ int tune(const int* configs, int n, cudaStream_t st, F launch, int* best_config,
   cudaEventCreate(&b);
   float best = 1e30f;
   int arg = configs[0];
+  for (int i = 0; i < n; ++i)
+    if (!bpx::gemm_config_ok(configs[i])) return fail(BPX_ERR_INVAL, "autotune: gemm_config %d names no tile", configs[i]);
   for (int i = 0; i < n; ++i) {
     if (int rc = launch(configs[i])) {
       cudaEventDestroy(a);
@@ -432,7 +437,7 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
   if (precision == BPX_EXACT) {
     bpx::ExactParams P;
     if (int rc = bpx::exact_params(c, K, &P)) return rc;
-    static const int kExactConfigs[] = {8080, 16080, 8089, 8083, 8081, 4083, 16083, 8084, 8082, 8087};
+    static const int kExactConfigs[] = {8080, 16080, 4080, 8089, 8081, 8082, 8085};
     if (!configs || nconfigs <= 0) {
       configs = kExactConfigs;
       nconfigs = static_cast<int>(sizeof(kExactConfigs) / sizeof(kExactConfigs[0]));

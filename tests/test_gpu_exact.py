@@ -173,7 +173,7 @@ def test_exact_segments_at_the_accumulation_bound(libbpx):
     _assert_bits(C, R, sch, h, M, "all positive")
 
 
-@pytest.mark.parametrize("cfg", [0, 8087, 16085, 8086, 4088, 16081, 8044, 8080, 8089])
+@pytest.mark.parametrize("cfg", [0, 8085, 16085, 8086, 4086, 16081, 8042, 8080, 8089])
 def test_exact_tile_configs_identical(libbpx, cfg):
     """Every tile configuration gives bit-identical results (the arithmetic
     is exact, so neither tile shape, CTA pairing, band nor segment choice can

@@ -344,9 +344,9 @@ def test_async_host_calls_in_flight(libbpx, prec):
             assert np.array_equal(S_["hC"].numpy(), want[3 * rnd + j])
 
 
-@pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16043), ("bf16x3", 8044),
-                                      ("bf16", 16043), ("bf16x3", 16022), ("bf16x3", 16045), ("bf16x3", 8047),
-                                      ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8048), ("bf16x3", 8089),
+@pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16041), ("bf16x3", 8042),
+                                      ("bf16", 16041), ("bf16x3", 16022), ("bf16x3", 16045), ("bf16x3", 8025),
+                                      ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8046), ("bf16x3", 8089),
                                       ("bf16", 16089), ("bf16x3", 8080), ("bf16", 4080)])
 def test_many_tiles_per_cta(libbpx, prec, cfg):
     """Bench-shaped code and block height at reduced N, K: ~600 output tiles
@@ -522,11 +522,11 @@ def test_mxfp8_table1_all_masks(libbpx):
         _check_blocks(C, R, ref, A, B, wl["h"], m, "mxfp8")
 
 
-@pytest.mark.parametrize("cfg", [0, 8001, 4003])
+@pytest.mark.parametrize("cfg", [0, 8001, 4009])
 def test_mxfp8_many_tiles(libbpx, cfg):
     """~600 tiles of 128 x 256 on the benchmark code: the single TMEM
-    accumulator is drained and refilled on every tile of every CTA (1-CTA,
-    CTA-pair and multicast-pair forms)."""
+    accumulator is drained and refilled on every tile of every CTA (1-CTA
+    and CTA-pair forms)."""
     bpx = libbpx
     code, ref = _pair(bpx, "sys8_3_8")
     h, M, K, N = 128, 8192, 512, 2048
@@ -536,6 +536,20 @@ def test_mxfp8_many_tiles(libbpx, cfg):
     assert info[bpx.INFO_STATUS] == bpx.OK
     R, sch = _oracle_decode(ref, A, B, h, m)
     _check_blocks(C, R, ref, A, B, h, m, "mxfp8")
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "mxfp8", "exact"])
+@pytest.mark.parametrize("cfg", [8083, 8084, 4087, 16088, -1])
+def test_configs_without_a_tile_are_refused(libbpx, prec, cfg):
+    """Tile codes 3, 4, 7, 8 (and negative configs) name no GEMM variant:
+    the call fails with ERR_INVAL before anything is launched."""
+    bpx = libbpx
+    code, _ref = _pair(bpx, "table1")
+    A, B = W.inputs(512, 256, 128, "uniform", 0)
+    m = W.erasure_mask(5, 2, 1)
+    with pytest.raises(bpx.BpxError) as ei:
+        _run(bpx, code, A, B, 128, bpx.PRECISIONS[prec], m, opts=bpx.default_opts(gemm_config=cfg))
+    assert ei.value.code == bpx.ERR_INVAL
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "exact"])
