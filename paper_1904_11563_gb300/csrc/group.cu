@@ -343,7 +343,14 @@ namespace {
 
 const int kDefaultConfigs[] = {8080, 16080, 4080, 8089, 16089, 8085, 16041, 8086, 16042};
 
-// Times `launch` on each config (one warm-up, then the best of three) and
+// BPX_OK when every candidate GEMM config names a tile.
+int check_configs(const int* configs, int n, const char* who) {
+  for (int i = 0; configs && i < n; ++i)
+    if (!bpx::gemm_config_ok(configs[i])) return fail(BPX_ERR_INVAL, "%s: gemm_config %d names no tile", who, configs[i]);
+  return BPX_OK;
+}
+
+// Times `launch` on each candidate (one warm-up, then the best of three) and
 // returns the fastest.
 template <typename F>
 int tune(const int* configs, int n, cudaStream_t st, F launch, int* best_config, float* best_ms) {
@@ -356,8 +363,6 @@ int tune(const int* configs, int n, cudaStream_t st, F launch, int* best_config,
   cudaEventCreate(&b);
   float best = 1e30f;
   int arg = configs[0];
-  for (int i = 0; i < n; ++i)
-    if (!bpx::gemm_config_ok(configs[i])) return fail(BPX_ERR_INVAL, "autotune: gemm_config %d names no tile", configs[i]);
   for (int i = 0; i < n; ++i) {
     if (int rc = launch(configs[i])) {
       cudaEventDestroy(a);
@@ -396,6 +401,7 @@ extern "C" int bpx_group_autotune(bpx_group* G, const int* configs, int nconfigs
                                   int* best_config, float* best_ms) {
   bpx::clear_error();
   if (!G || !G->ws) return fail(BPX_ERR_INVAL, "bpx_group_autotune: group not initialised");
+  if (int rc = check_configs(configs, nconfigs, "bpx_group_autotune")) return rc;
   cudaStream_t st = S(stream);
   // one full run so that every job's plan and staged operands exist
   if (int rc = run_group(G, nullptr, G->table_config > 0 ? G->table_config : 0, st)) return rc;
@@ -423,6 +429,7 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
   bpx::clear_error();
   if (precision != BPX_BF16 && precision != BPX_BF16X3 && precision != BPX_EXACT)
     return fail(BPX_ERR_UNSUPPORTED, "bpx_autotune tunes the tensor-core GEMM (BPX_BF16 / BPX_BF16X3 / BPX_EXACT)");
+  if (int rc = check_configs(configs, nconfigs, "bpx_autotune")) return rc;
   // one full run: plan, staged operands
   if (int rc = bpx_coded_matmul(c, d_A, d_B, M, N, K, h, precision, d_mask, d_C, nullptr, ws, ws_bytes,
                                 nullptr, stream))
