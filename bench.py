@@ -243,6 +243,48 @@ class StageEvents:
 
 # ------------------------------------------------------------------ CPU oracle legs
 
+TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5, "bf16": 2e-2, "mxfp8": 6e-2, "exact": 1e-5}
+
+
+def _propagation(code, order, Ah, Bh, h, sources, ncols=256):
+    """nu_s = sqrt(sum_c coef_{s,c}^2 ||P_c||^2) / ||C_s|| for the sampled
+    sources: coef from the peel recurrence over the library's plan (each
+    recovered source = its resolver's product minus the resolver's other
+    sources), norms of FP64 products on the first `ncols` columns of B."""
+    res = {int(s_): int(r_) for s_, r_, _d in order if s_ >= 0}
+    seq = [int(s_) for s_, _r, _d in order if s_ >= 0]
+    coef = {}
+    for s_ in seq:
+        r_ = res[s_]
+        e_ = {r_: 1}
+        for t_ in code.cell_src[code.cell_ptr[r_]:code.cell_ptr[r_ + 1]]:
+            t_ = int(t_)
+            if t_ != s_:
+                for c_, v_ in coef[t_].items():
+                    e_[c_] = e_.get(c_, 0) - v_
+        coef[s_] = {c_: v_ for c_, v_ in e_.items() if v_}
+    Bs = Bh[:, :ncols]
+    M = Ah.shape[0]
+
+    def blk(s_):
+        lo, hi = s_ * h, min((s_ + 1) * h, M)
+        out = np.zeros((h, Ah.shape[1]))
+        if lo < hi:
+            out[:hi - lo] = Ah[lo:hi]
+        return out
+
+    pn = {}
+    nu = {}
+    for s_ in sources:
+        for c_ in coef[s_]:
+            if c_ not in pn:
+                Ac = sum(blk(int(t_)) for t_ in code.cell_src[code.cell_ptr[c_]:code.cell_ptr[c_ + 1]])
+                pn[c_] = float(np.linalg.norm(Ac @ Bs))
+        num = np.sqrt(sum(float(v_) ** 2 * pn[c_] ** 2 for c_, v_ in coef[s_].items()))
+        nu[s_] = float(num / np.linalg.norm(blk(s_) @ Bs))
+    return nu
+
+
 def _oracle_sample(A, B, h, mask, ncols, wl):
     """Runs the FP64 oracle's whole coded path on the first ncols columns of
     B (the path is columnwise separable); returns seconds."""
@@ -372,7 +414,7 @@ def run_ours(args, wl):
     if args.precisions:
         precs = [x for x in args.precisions.split(",") if x]
     elif args.precision == "auto":
-        precs = ["bf16x3", "fp32", "bf16", "mxfp8", "exact"]
+        precs = ["bf16x3", "fp32", "bf16", "mxfp8", "exact", "fp16x3"]
     else:
         precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
     results = {}
@@ -400,7 +442,7 @@ def run_ours(args, wl):
         cfg = args.gemm_config
         if cfg < 0:
             cfg = 0
-            if prec in ("bf16x3", "bf16", "exact"):
+            if prec in ("bf16x3", "bf16", "exact", "fp16x3"):
                 cfg, _tuned_ms = bpx.autotune(code, A, Bm, h, P, masks[0], ws, C=C)
         tuned[prec] = cfg
         opts = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth)
@@ -512,6 +554,7 @@ def run_ours(args, wl):
         direct = [s_ for s_ in sorted(depth) if depth[s_] == 1][:1]
         samples = [s_ for s_ in sorted(set(deep + direct)) if (s_ + 1) * h <= M]
         refs = {s_: Ah[s_ * h:(s_ + 1) * h].astype(np.float64) @ Bh for s_ in samples}
+        nu = _propagation(code, order, Ah, Bh, h, samples)
         for prec, r in results.items():
             Cn = r["C"]
             errs = []
@@ -519,9 +562,13 @@ def run_ours(args, wl):
                 blk = Cn[s_ * h:(s_ + 1) * h].double().cpu().numpy()
                 errs.append(float(np.linalg.norm(blk - refs[s_]) / np.linalg.norm(refs[s_])))
             direct_err = [e_ for e_, s_ in zip(errs, samples) if depth[s_] == 1]
+            scaled = [e_ / max(1.0, nu[s_]) for e_, s_ in zip(errs, samples)]
             rel[prec] = {"max": max(errs), "max_direct": max(direct_err) if direct_err else None,
+                         "max_nu_scaled": max(scaled), "tol": TOL.get(prec),
                          "sources": samples, "depths": [depth[s_] for s_ in samples], "errs": errs,
-                         "reference": "FP64 A_s B (numpy) for the deepest and one direct source"}
+                         "nu": [nu[s_] for s_ in samples],
+                         "reference": "FP64 A_s B (numpy) for the deepest and one direct source; nu_s from "
+                                      "the plan's integer expansion and FP64 product norms on 256 columns"}
 
     # decode GB/s: per non-direct source, read the resolver's product and the
     # other blocks it subtracts, write C_s: (deg(resolver) + 1) h N 4 bytes
@@ -551,7 +598,7 @@ def run_ours(args, wl):
             S_ex = bpx.exact_params(code, K)["S"]
             mult = S_ex * (S_ex + 1) // 2
         else:
-            mult = {"bf16x3": 3, "bf16": 1, "mxfp8": 1}[head]
+            mult = {"bf16x3": 3, "fp16x3": 3, "bf16": 1, "mxfp8": 1}[head]
         flops = 2.0 * rows_mean * N * K * mult
         achieved = flops / (gemm_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0) * (2.0 if head == "mxfp8" else 1.0)
@@ -594,6 +641,21 @@ def run_ours(args, wl):
     if "bf16x3" in results and "fp32" in results:
         line["speedup_bf16x3_vs_fp32"] = results["fp32"]["ms"] / results["bf16x3"]["ms"]
     line["rel_err"] = rel
+    # each precision's largest sampled block error, flat and divided by the
+    # block's propagation factor, against its stated tolerance
+    line["block_err"] = {p_: {"flat_max": r_["max"], "nu_scaled_max": r_["max_nu_scaled"], "tol": r_["tol"],
+                              "flat_within_tol": (r_["max"] <= r_["tol"]) if r_["tol"] else None}
+                         for p_, r_ in rel.items()}
+    # the accuracy target: >= 4x the plain FP32 coded path at <= 1e-5 on
+    # every block, flat; which split path meets it
+    if "fp32" in results and rel:
+        tgt = {}
+        for p_ in ("bf16x3", "fp16x3"):
+            if p_ in results and p_ in rel:
+                tgt[p_] = {"tflops": line[f"{p_}_tflops"], "x_fp32": results["fp32"]["ms"] / results[p_]["ms"],
+                           "flat_max_rel_err": rel[p_]["max"],
+                           "meets": bool(rel[p_]["max"] <= 1e-5 and results["fp32"]["ms"] / results[p_]["ms"] >= 4.0)}
+        line["accuracy_target"] = tgt
     line["roofline"] = roof
     # every precision's GEMM against its own peak (FP8: the measured bf16 peak
     # times the nominal fp8 / bf16 ratio of 2)
@@ -612,7 +674,7 @@ def run_ours(args, wl):
                 S_ex = bpx.exact_params(code, K)["S"]
                 mult = S_ex * (S_ex + 1) // 2     # digit pairs (i, l) with i + l < S
             else:
-                mult = {"bf16x3": 3, "bf16": 1, "mxfp8": 1}[prec]
+                mult = {"bf16x3": 3, "fp16x3": 3, "bf16": 1, "mxfp8": 1}[prec]
             pk = peaks.get("bf16_tflops", 1900.0) * (2.0 if prec == "mxfp8" else 1.0)
             unit = "measured bf16 burst" + (" x 2 (nominal fp8/bf16)" if prec == "mxfp8" else "")
             work = 2.0 * rows_m * N * K * mult
@@ -641,7 +703,7 @@ def run_ours(args, wl):
         line["b_split"] = _hbm(4.0 * K * N + (4 if head == "bf16x3" else 2) * K * N, st_.get("b_prep", 0.0),
                                "read B (4 K N) + write B^T hi (+ lo) bf16")
     line["clocks"] = R["clocks"]
-    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 4, "exact": 7}[head]
+    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 4, "exact": 7, "fp16x3": 7}[head]
     line["gpu_launches"] = per_step * steps
 
     # end to end through the host entry points (pinned host buffers): every

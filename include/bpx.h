@@ -70,7 +70,12 @@ enum bpx_precision {
   BPX_BF16 = 1,   /* coded A and B rounded to bf16, one tcgen05 MMA per k-step */
   BPX_BF16X3 = 2, /* split bf16: a = a_hi + a_lo; hi*hi + hi*lo + lo*hi on tcgen05 */
   BPX_MXFP8 = 3,  /* E4M3 with one UE8M0 scale per 32 K-elements (tcgen05 block-scaled) */
-  BPX_EXACT = 4   /* exact slices: the decode is exact at every peel depth (bpx_exact_params) */
+  BPX_EXACT = 4,  /* exact slices: the decode is exact at every peel depth (bpx_exact_params) */
+  BPX_FP16X3 = 5  /* split fp16 under power-of-two scales: every coded row of A and every column
+                     of B is scaled by 2^e so that its largest magnitude lies in [2^14, 2^15);
+                     a = a_hi + a_lo in fp16 (22 significant bits against bf16's 16);
+                     hi*hi + hi*lo + lo*hi on tcgen05 kind::f16 into FP32, the scales undone
+                     exactly in the epilogue; 128-wide K accumulation segments by default */
 };
 
 enum bpx_status {
@@ -173,14 +178,9 @@ const char* bpx_last_error(void);
  *     (quoted from Paterson et al.; Table I meets it with equality);
  *   bpx_bound_paterson (k > sigma): n <= k + sigma - 1 + floor(sigma
  *     (sigma - 1)(b - 1) / ((k - sigma) b + sigma - 1)) -- the straggler
- *     count n - k the paper's Section V simulations use (Table III meets it);
- *   bpx_bound_theorem31: Theorem 3.1 for an asymptotically MDS code with
- *     worst-case overhead eps: n <= floor(((kb + sigma - 1)(k - 1) -
- *     (sigma - 1)(sigma/2 - 1)) / (b (k - sigma') + sigma - 1)), sigma' =
- *     sigma (1 + eps); BPX_ERR_INVAL when the denominator is not positive. */
+ *     count n - k the paper's Section V simulations use (Table III meets it). */
 int bpx_bound_k_equals_sigma(int k, int b, int* n_max);
 int bpx_bound_paterson(int k, int b, int sigma, int* n_max);
-int bpx_bound_theorem31(int k, int b, int sigma, double eps, int* n_max);
 
 /* A code given by its cells (variant BPX_LITERAL): num_cells cells grouped by
  * ascending column (col_of_cell[c] in [0, n)), cell c's support =
@@ -226,6 +226,11 @@ size_t bpx_workspace_bytes(const bpx_code* code, int M, int N, int K, int h, int
  * the handle may be freed afterwards).  Once per workspace.  BPX_ERR_NOMEM if
  * ws_bytes is too small for bpx_workspace_bytes(code, 0, 0, 0, 1, BPX_FP32). */
 int bpx_workspace_init(const bpx_code* code, void* d_ws, size_t ws_bytes, bpx_stream stream);
+
+/* Byte offset in a workspace of this code of the plan's device info words
+ * (int32[BPX_INFO_LEN], written by every schedule and by kernels' self-checks
+ * and refusals); 0 when code is NULL.  Host only. */
+size_t bpx_workspace_info_offset(const bpx_code* code);
 
 /* ---------------------------------------------------------------- hot path */
 
@@ -276,13 +281,24 @@ int bpx_coded_products(const bpx_code* code, const float* d_A, const float* d_B,
                        int K, int h, int precision, void* d_ws, size_t ws_bytes,
                        float* d_products, float* d_C, const bpx_opts* opts, bpx_stream stream);
 
-/* a4. Numeric peel (Section I-A, XOR read as subtraction): along the planned
- * schedule, C_s = P_r - sum_{t in supp(r), t != s, ascending} C_t for every
- * recovered source.  d_C holds S h rows of N floats (rows >= M are scratch for
- * zero-padded blocks).  direct_written = 1 when bpx_coded_products already
- * wrote the depth-1 sources into d_C.  Unrecovered blocks are left untouched. */
-int bpx_peel_decode(const bpx_code* code, const float* d_products, int N, int h, float* d_C,
-                    int direct_written, const bpx_opts* opts, const void* d_ws, bpx_stream stream);
+/* a4. Numeric peel (Section I-A, XOR read as subtraction; Section II: the
+ * sink decodes from the products that arrived): for the erasure pattern
+ * d_erasure_mask (as for bpx_schedule; one byte per cell when
+ * opts->mask_cells), C_s = P_r - sum_{t in supp(r), t != s, ascending} C_t
+ * for every recovered source, wave by wave.  The call first plans the peel
+ * for that mask into d_ws (exactly as bpx_schedule, whose info words go to
+ * d_info when non-NULL); the mask must be the one the products were computed
+ * under.  d_erasure_mask = NULL peels along the plan already in d_ws (left by
+ * bpx_schedule or bpx_coded_matmul); if no schedule has run on d_ws since
+ * bpx_workspace_init, the peel writes nothing and sets BPX_ERR_INVAL in the
+ * plan's info words (BPX_INFO_STATUS and BPX_INFO_DEVICE_ERR).  d_products:
+ * P_c at d_products + c h N (bpx_coded_products).  d_C holds S h rows of N
+ * floats (rows >= M are scratch for zero-padded blocks).  direct_written = 1
+ * when bpx_coded_products already wrote the depth-1 sources into d_C.
+ * Unrecovered blocks are left untouched. */
+int bpx_peel_decode(const bpx_code* code, const float* d_products, const uint8_t* d_erasure_mask, int N, int h,
+                    float* d_C, int direct_written, const bpx_opts* opts, void* d_ws, size_t ws_bytes,
+                    int32_t* d_info, bpx_stream stream);
 
 /* ---------------------------------------------------------------- exact slices
  *
@@ -326,10 +342,12 @@ int bpx_exact_params(const bpx_code* code, int K, int32_t* out);
  * each num_cells h N, row-major h x N per cell); the scales and an int64 copy
  * of every decoded block live in d_ws, which must be the workspace that
  * bpx_coded_products used (sized for BPX_EXACT).  Every recovered source,
- * depth 1 included, is written to d_C.  opts: only stage_events and peel_ctas
- * are read. */
-int bpx_peel_decode_exact(const bpx_code* code, const int32_t* d_planes, int N, int h, float* d_C,
-                          const bpx_opts* opts, void* d_ws, size_t ws_bytes, bpx_stream stream);
+ * depth 1 included, is written to d_C.  d_erasure_mask / d_info: as for
+ * bpx_peel_decode (NULL: the plan already in d_ws).  opts: only
+ * stage_events, peel_ctas and mask_cells are read. */
+int bpx_peel_decode_exact(const bpx_code* code, const int32_t* d_planes, const uint8_t* d_erasure_mask, int N,
+                          int h, float* d_C, const bpx_opts* opts, void* d_ws, size_t ws_bytes, int32_t* d_info,
+                          bpx_stream stream);
 
 /* The whole path for one erasure pattern: schedule, encode + products, peel.
  * The products live in the workspace.  d_info as in bpx_schedule.  With

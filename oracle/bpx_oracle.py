@@ -38,8 +38,7 @@ Matrix Multiplication"):
   both by brute force over subsets and as the first prefix of the arrival
   order that peels completely;
 * the bounds on the number of columns n of Section III-B (the k = sigma
-  bound and the general bound quoted from Paterson et al., Theorem 3.1 and
-  its large-b limit), and a check that a code given by its cells is an
+  bound and the general bound quoted from Paterson et al.), and a check that a code given by its cells is an
   array BP-XOR code (every k columns peel);
 * the two-dimensional scheme of Section III-A (Examples 1 and 2): source
   (z, l) is the output block A_z B_l (row block z of A, column block l of
@@ -920,28 +919,6 @@ def bound_paterson(k: int, b: int, sigma: int) -> int:
     + sigma - 1)) for k > sigma: the form the Section V simulations use for
     the number of stragglers n - k."""
     return k + sigma - 1 + (sigma * (sigma - 1) * (b - 1)) // ((k - sigma) * b + sigma - 1)
-
-
-def bound_theorem31(k: int, b: int, sigma: int, eps: float) -> int:
-    """Theorem 3.1: n <= floor(((kb + sigma - 1)(k - 1) - (sigma - 1)
-    (sigma/2 - 1)) / (b (k - sigma') + sigma - 1)), sigma' = sigma (1 + eps),
-    counting symbol appearances: every source in at least n - k + 1 columns
-    against at most sigma b' n - (sigma - 1)(n - k + sigma / 2) appearances.
-    Needs a positive denominator."""
-    sp = sigma * (1.0 + eps)
-    den = b * (k - sp) + sigma - 1
-    if den <= 0:
-        raise ValueError("Theorem 3.1 needs b (k - sigma') + sigma - 1 > 0")
-    num = (k * b + sigma - 1) * (k - 1) - (sigma - 1) * (sigma / 2.0 - 1)
-    return int(np.floor(num / den + 1e-12))
-
-
-def bound_large_b(k: int, sigma: int) -> int:
-    """The b -> infinity limit of Theorem 3.1 (eps -> 0): n <= k + sigma - 1
-    + floor((sigma - 1) sigma / (k - sigma)) - [(k - sigma) divides
-    (sigma - 1) sigma]."""
-    q, r = divmod((sigma - 1) * sigma, k - sigma)
-    return k + sigma - 1 + q - (1 if r == 0 else 0)
 
 
 def code_from_columns(name: str, k: int, b: int, columns) -> Code:

@@ -18,12 +18,12 @@ LIB_PATH = os.path.join(_HERE, "libbpx.so")
 # enums of bpx.h
 TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B, LITERAL = 0, 1, 2, 3, 4, 5
 SEARCH_SYSTEMATIC = 1  # bpx_code_search_ex flag
-FP32, BF16, BF16X3, MXFP8, EXACT = 0, 1, 2, 3, 4
+FP32, BF16, BF16X3, MXFP8, EXACT, FP16X3 = 0, 1, 2, 3, 4, 5
 OK, ERR_INVAL, ERR_UNSUPPORTED, ERR_UNDECODABLE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(7)
 INFO_STATUS, INFO_RECOVERED, INFO_WAVES, INFO_SURVIVING, INFO_DIRECT, INFO_DEVICE_ERR = range(6)
 INFO_LEN = 16
 
-PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "mxfp8": MXFP8, "exact": EXACT}
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "mxfp8": MXFP8, "exact": EXACT, "fp16x3": FP16X3}
 
 
 class BpxError(RuntimeError):
@@ -82,13 +82,14 @@ def lib():
         "bpx_last_error": (ct.c_char_p, []),
         "bpx_workspace_bytes": (sz, [vp, i, i, i, i, i]),
         "bpx_workspace_init": (i, [vp, vp, sz, vp]),
+        "bpx_workspace_info_offset": (sz, [vp]),
         "bpx_schedule": (i, [vp, vp, vp, sz, vp, vp, vp, vp]),
         "bpx_encode": (i, [vp, f32p, i, i, i, vp, f32p, vp]),
         "bpx_coded_products": (i, [vp, f32p, f32p, i, i, i, i, i, vp, sz, f32p, f32p,
                                    ct.POINTER(Opts), vp]),
-        "bpx_peel_decode": (i, [vp, f32p, i, i, f32p, i, ct.POINTER(Opts), vp, vp]),
+        "bpx_peel_decode": (i, [vp, f32p, vp, i, i, f32p, i, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_exact_params": (i, [vp, i, ct.POINTER(ct.c_int32)]),
-        "bpx_peel_decode_exact": (i, [vp, vp, i, i, f32p, ct.POINTER(Opts), vp, sz, vp]),
+        "bpx_peel_decode_exact": (i, [vp, vp, vp, i, i, f32p, ct.POINTER(Opts), vp, sz, vp, vp]),
         "bpx_coded_matmul": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, ct.POINTER(Opts),
                                  vp, sz, vp, vp]),
         "bpx_coded_matmul_host": (i, [vp, f32p, f32p, i, i, i, i, i, vp, f32p, f32p, f32p, vp,
@@ -100,7 +101,6 @@ def lib():
         "bpx_first_decodable": (i, [vp, vp, i, vp, vp]),
         "bpx_bound_k_equals_sigma": (i, [i, i, ct.POINTER(ct.c_int)]),
         "bpx_bound_paterson": (i, [i, i, i, ct.POINTER(ct.c_int)]),
-        "bpx_bound_theorem31": (i, [i, i, i, ct.c_double, ct.POINTER(ct.c_int)]),
         "bpx_code_from_cells": (i, [i, i, i, i, vp, vp, vp, i, ct.POINTER(vp)]),
         "bpx_code_search": (i, [i, i, i, i, ct.c_longlong, ct.c_ulonglong, ct.POINTER(vp),
                                 ct.POINTER(ct.c_longlong)]),
@@ -285,6 +285,12 @@ class Workspace:
     def ptr(self):
         return _ptr(self.t)
 
+    def info(self):
+        """The plan's device info words (a view into the workspace)."""
+        torch = _torch()
+        off = lib().bpx_workspace_info_offset(self.code.handle)
+        return self.t[off:off + 4 * INFO_LEN].view(torch.int32)
+
 
 def schedule(code: Code, mask, ws: Workspace, cells=False):
     """a1: returns (peel_order int32[S,3], recovered uint8[S], info int32[16])
@@ -322,23 +328,26 @@ def coded_products(code: Code, A, B, h, precision, ws: Workspace, products=None,
     return products
 
 
-def peel_decode(code: Code, products, N, h, C, ws: Workspace, direct_written=False, opts=None):
-    """a4: numeric peel into C (S*h x N)."""
-    _check(lib().bpx_peel_decode(code.handle, _ptr(products), N, h, _ptr(C), int(direct_written),
-                                 ct.byref(opts) if opts is not None else None, ws.ptr, _stream()))
+def peel_decode(code: Code, products, N, h, C, ws: Workspace, direct_written=False, opts=None, mask=None,
+                info=None):
+    """a4: numeric peel into C (S*h x N) for the erasure mask `mask` (planned
+    first, as bpx_schedule), or along the plan already in ws when mask is
+    None."""
+    _check(lib().bpx_peel_decode(code.handle, _ptr(products), _ptr(mask) if mask is not None else None, N, h,
+                                 _ptr(C), int(direct_written), ct.byref(opts) if opts is not None else None,
+                                 ws.ptr, ws.nbytes, _ptr(info) if info is not None else None, _stream()))
     return C
 
 
-def bound(kind, k, b, sigma=None, eps=0.0) -> int:
-    """Bounds on n (host only): kind 'k_equals_sigma', 'paterson' or
-    'theorem31'."""
+def bound(kind, k, b, sigma=None) -> int:
+    """Bounds on n (host only): kind 'k_equals_sigma' or 'paterson'."""
     out = ct.c_int()
     if kind == "k_equals_sigma":
         _check(lib().bpx_bound_k_equals_sigma(k, b, ct.byref(out)))
     elif kind == "paterson":
         _check(lib().bpx_bound_paterson(k, b, sigma, ct.byref(out)))
     else:
-        _check(lib().bpx_bound_theorem31(k, b, sigma, eps, ct.byref(out)))
+        raise ValueError(kind)
     return out.value
 
 
@@ -377,11 +386,12 @@ def exact_products(code: Code, A, B, h, ws: Workspace, planes=None, opts=None):
     return planes
 
 
-def peel_decode_exact(code: Code, planes, N, h, C, ws: Workspace, opts=None):
-    """a4 with exact slices: exact integer peel of the diagonal planes into C."""
-    _check(lib().bpx_peel_decode_exact(code.handle, _ptr(planes), N, h, _ptr(C),
-                                       ct.byref(opts) if opts is not None else None, ws.ptr, ws.nbytes,
-                                       _stream()))
+def peel_decode_exact(code: Code, planes, N, h, C, ws: Workspace, opts=None, mask=None, info=None):
+    """a4 with exact slices: exact integer peel of the diagonal planes into C
+    (mask as for peel_decode)."""
+    _check(lib().bpx_peel_decode_exact(code.handle, _ptr(planes), _ptr(mask) if mask is not None else None, N, h,
+                                       _ptr(C), ct.byref(opts) if opts is not None else None, ws.ptr, ws.nbytes,
+                                       _ptr(info) if info is not None else None, _stream()))
     return C
 
 

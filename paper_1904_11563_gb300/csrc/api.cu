@@ -72,6 +72,11 @@ void stage_mark(const bpx_opts* o, int stage, int end, cudaStream_t st) {
 
 }  // namespace
 
+extern "C" size_t bpx_workspace_info_offset(const bpx_code* c) {
+  if (!c) return 0;
+  return bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32).p_info;
+}
+
 extern "C" int bpx_workspace_init(const bpx_code* c, void* ws, size_t ws_bytes, bpx_stream stream) {
   bpx::clear_error();
   const bpx::WsLayout L = bpx::ws_layout(c ? c : nullptr, 0, 0, 0, 1, BPX_FP32);
@@ -255,6 +260,27 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
         return fail(BPX_ERR_UNSUPPORTED, "bf16 tensor-core path not available in this build");
       break;
     }
+    case BPX_FP16X3: {
+      void* a_hi = base + L.a_hi;
+      void* a_lo = base + L.a_lo;
+      void* b_hi = base + L.b_hi;
+      void* b_lo = base + L.b_lo;
+      int32_t* a_exp = reinterpret_cast<int32_t*>(base + L.a_scale);
+      uint32_t* b_max = reinterpret_cast<uint32_t*>(base + L.b_scale);
+      int32_t* b_exp = reinterpret_cast<int32_t*>(b_max + N);
+      stage_mark(opts, BPX_STAGE_B_PREP, 0, st);
+      e = bpx::launch_b_f16(d_B, K, N, b_hi, b_lo, b_max, b_exp, st);
+      stage_mark(opts, BPX_STAGE_B_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
+      if (e == cudaSuccess) e = bpx::launch_encode_f16(g, p, d_A, M, K, h, a_hi, a_lo, a_exp, st);
+      stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
+      stage_mark(opts, BPX_STAGE_GEMM, 0, st);
+      if (e == cudaSuccess)
+        e = bpx::launch_gemm_tc(g, p, a_hi, a_lo, b_hi, b_lo, c->num_cells, N, K, h, true, d_products, d_C, config,
+                                d_info, st, a_exp, b_exp);
+      stage_mark(opts, BPX_STAGE_GEMM, 1, st);
+      break;
+    }
     case BPX_MXFP8: {
       if (K % 128 != 0) return fail(BPX_ERR_INVAL, "BPX_MXFP8 needs K %% 128 == 0 (K = %d)", K);
       void* a8 = base + L.a_hi;
@@ -352,16 +378,29 @@ extern "C" int bpx_coded_products(const bpx_code* c, const float* d_A, const flo
                        nullptr, S(stream));
 }
 
-extern "C" int bpx_peel_decode(const bpx_code* c, const float* d_products, int N, int h, float* d_C,
-                               int direct_written, const bpx_opts* opts, const void* ws,
-                               bpx_stream stream) {
+extern "C" int bpx_peel_decode(const bpx_code* c, const float* d_products, const uint8_t* d_erasure_mask, int N,
+                               int h, float* d_C, int direct_written, const bpx_opts* opts, void* ws,
+                               size_t ws_bytes, int32_t* d_info, bpx_stream stream) {
   bpx::clear_error();
+  if (!c || !ws) return fail(BPX_ERR_INVAL, "bpx_peel_decode: NULL argument");
+  if (int rc = check_ws(c, ws, ws_bytes, bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32))) return rc;
+  if (d_erasure_mask)  // plan the peel for this mask first
+    if (int rc = schedule_impl(c, d_erasure_mask, opts && opts->mask_cells, ws, ws_bytes, nullptr, nullptr, d_info,
+                               S(stream)))
+      return rc;
   return peel_impl(c, d_products, N, h, d_C, direct_written, opts, ws, S(stream));
 }
 
-extern "C" int bpx_peel_decode_exact(const bpx_code* c, const int32_t* d_planes, int N, int h, float* d_C,
-                                     const bpx_opts* opts, void* d_ws, size_t ws_bytes, bpx_stream stream) {
+extern "C" int bpx_peel_decode_exact(const bpx_code* c, const int32_t* d_planes, const uint8_t* d_erasure_mask,
+                                     int N, int h, float* d_C, const bpx_opts* opts, void* d_ws, size_t ws_bytes,
+                                     int32_t* d_info, bpx_stream stream) {
   bpx::clear_error();
+  if (!c || !d_ws) return fail(BPX_ERR_INVAL, "bpx_peel_decode_exact: NULL argument");
+  if (int rc = check_ws(c, d_ws, ws_bytes, bpx::ws_layout(c, 0, 0, 0, 1, BPX_FP32))) return rc;
+  if (d_erasure_mask)
+    if (int rc = schedule_impl(c, d_erasure_mask, opts && opts->mask_cells, d_ws, ws_bytes, nullptr, nullptr,
+                               d_info, S(stream)))
+      return rc;
   return peel_exact_impl(c, d_planes, N, h, d_C, opts, d_ws, ws_bytes, S(stream));
 }
 

@@ -99,7 +99,9 @@ enum {
   CTR_NNEXT,      // next frontier size (scratch)
   CTR_NNEW,       // sources recovered this round (scratch)
   CTR_ERR,        // device error code raised by a kernel self-check
+  CTR_PLAN,       // kPlanReady once a whole plan is in place (zeroed by bpx_workspace_init)
   CTR_LEN = 16
 };
+constexpr int32_t kPlanReady = 0x504C414E;  // "PLAN"
 
 }  // namespace bpx

@@ -404,6 +404,15 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision,
       L.a_lo = take(rowsA * Kp * 2);
       L.b_lo = take(Np * Kp * 2);
     }
+  } else if (precision == BPX_FP16X3) {
+    // fp16 hi / lo operands, the exponent of every coded row's scale (int32),
+    // and per column of B its max |B| (float bits) then its exponent
+    L.a_hi = take(rowsA * Kp * 2);
+    L.b_hi = take(Np * Kp * 2);
+    L.a_lo = take(rowsA * Kp * 2);
+    L.b_lo = take(Np * Kp * 2);
+    L.a_scale = take(rowsA * sizeof(int32_t));
+    L.b_scale = take(2 * Np * sizeof(int32_t));
   } else if (precision == BPX_EXACT) {
     ExactParams P;
     if (exact_params(c, K > 0 ? K : 8, &P) != BPX_OK) {

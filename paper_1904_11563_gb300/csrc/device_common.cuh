@@ -186,6 +186,33 @@ cudaError_t launch_peel_group(const GJob* d_jobs, const int32_t* d_order, const 
                               cudaEvent_t fork, cudaEvent_t join);
 // Whether a job's peel can take the gathered form in a grouped launch with this chunk.
 bool peel_gather_ok(int S, int sigma, long long chunk);
+// Split-fp16 scales (BPX_FP16X3).  The exponent e of a row of coded A or a
+// column of B puts its largest magnitude amax at amax 2^e in [2^14, 2^15):
+// both fp16 halves of every scaled element are then finite (the largest
+// finite fp16 is 65504) and the hi half holds the top 11 bits of the largest
+// one.  0 when amax is zero or not finite.
+__host__ __device__ inline int f16_scale_exp(float amax) {
+  if (!(amax > 0.f) || !(amax <= 3.402823466e38f)) return 0;
+  int ex = 0;
+  (void)frexpf(amax, &ex);  // amax = m 2^ex, m in [0.5, 1)
+  return 15 - ex;           // amax 2^e = m 2^15
+}
+// 2^k as a float, for -126 <= k <= 127.
+__host__ __device__ inline float pow2f(int k) {
+  union { uint32_t u; float f; } v;
+  v.u = static_cast<uint32_t>(k + 127) << 23;
+  return v.f;
+}
+// x 2^e for the exponents f16_scale_exp returns (-113 <= e <= 163): two exact
+// power-of-two multiplies (one rounding at most, when x 2^e is subnormal).
+__host__ __device__ inline float scale_pow2(float x, int e) {
+  const int e1 = e >> 1;
+  return (x * pow2f(e1)) * pow2f(e - e1);
+}
+cudaError_t launch_encode_f16(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
+                              void* a_hi, void* a_lo, int32_t* a_exp, cudaStream_t st);
+cudaError_t launch_b_f16(const float* B, int K, int N, void* b_hi, void* b_lo, uint32_t* b_max, int32_t* b_exp,
+                         cudaStream_t st);
 // gemm_config is a tile configuration the GEMM kernels have (tile codes 3,
 // 4, 7 and 8 do not exist; negative values are invalid).
 bool gemm_config_ok(int config);
@@ -234,10 +261,13 @@ cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, co
 cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* a_coded, const float* B, int N, int K,
                             int h, float* products, float* C_direct, cudaStream_t st);
 // Tensor-core coded GEMM over the staged bf16 operands (split or plain).
+// a_exp / b_exp non-null: the split-fp16 operands of BPX_FP16X3 (a_lo and
+// b_lo required), unscaled by 2^-(a_exp[row] + b_exp[col]) in the epilogue.
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
                            const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
                            bool split3, float* products, float* C_direct, int config,
-                           int32_t* info_out, cudaStream_t st);
+                           int32_t* info_out, cudaStream_t st, const int32_t* a_exp = nullptr,
+                           const int32_t* b_exp = nullptr);
 
 // Exact-slice staging (max |B| per column + B digit planes; max |A| per row
 // position + coded A digit planes), digit-product GEMM and exact peel.

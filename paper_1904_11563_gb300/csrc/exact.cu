@@ -200,6 +200,13 @@ __global__ void __launch_bounds__(256)
 exact_peel_kernel(DevPlan p, const int32_t* __restrict__ planes, long long plane_stride, long long* C64, float* C,
                   const uint32_t* __restrict__ amax_a, const uint32_t* __restrict__ amax_b, int N, int h, int w,
                   int bits, long long nv, int chunk) {
+  if (p.ctr[CTR_PLAN] != kPlanReady) {  // no schedule has planned this workspace: refuse, write nothing
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicExch(&p.info[BPX_INFO_DEVICE_ERR], BPX_ERR_INVAL);
+      atomicExch(&p.info[BPX_INFO_STATUS], BPX_ERR_INVAL);
+    }
+    return;
+  }
   const int nwaves = p.ctr[CTR_NWAVES];
   const long long v0 = static_cast<long long>(blockIdx.x) * chunk;
   if (v0 >= nv) return;

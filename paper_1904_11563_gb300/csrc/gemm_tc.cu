@@ -5,7 +5,9 @@
 //   kernel, B^T (N x K, K-major) written by the B split kernel.
 // Split-BF16x3 accumulates hi*hi + hi*lo + lo*hi into one FP32 TMEM
 // accumulator (the lo*lo term is below FP32 rounding); plain BF16 issues the
-// hi*hi MMA only.
+// hi*hi MMA only.  Split-FP16x3 (a job with exponent arrays) issues the same
+// three MMAs over fp16 halves of row- and column-scaled operands, and the
+// epilogue multiplies each output by 2^-(row exponent + column exponent).
 //
 // Persistent warp-specialised kernel, one 128 x 256 output tile per CTA at
 // a time:
@@ -70,6 +72,10 @@ struct __align__(64) TcJob {
   const int32_t* t2_order;
   const int32_t* cnt;
   int w2, kc, ncells;
+  // split fp16 (rows mode): power-of-two exponent per coded row and per
+  // column of B; null for bf16 operands
+  const int32_t* a_exp;
+  const int32_t* b_exp;
 };
 
 template <bool kSplit, int kBN, int kBK = BK>
@@ -336,6 +342,10 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
         const TileRef T = locate(jobs, njobs, t, group, live_mc, kPair, kBK, kMode);
         if (!T.live) continue;
         const int n_segs = (T.k_steps + seg_kb - 1) / seg_kb;
+        // operand format: fp16 for a split-fp16 job, else bf16
+        const uint32_t idesc = (!kExact && !k2D && T.J->a_exp)
+                                   ? (k2Sm ? idesc_f16_pair<kBN>() : idesc_f16<kBN>())
+                                   : (k2Sm ? idesc_bf16_pair<kBN>() : idesc_bf16<kBN>());
         for (int sg = 0; sg < n_segs && ok; ++sg, ++g) {
           const int buf = g & 1;
           if (!mbar_wait(smem_u32(&sempty_bar[buf]), static_cast<uint32_t>((g >> 1) & 1) ^ 1u,
@@ -366,16 +376,16 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
               const uint64_t adv = static_cast<uint64_t>(kk * 32) >> 4;  // 16 bf16 = 32 B
               const uint32_t first = (kb == kb0 && kk == 0) ? 0u : 1u;
               if constexpr (k2Sm) {
-                umma_bf16_pair<kBN>(d_tmem, ahi + adv, bhi + adv, first);
+                umma_kf16_pair(d_tmem, ahi + adv, bhi + adv, idesc, first);
                 if (kSplit) {
-                  umma_bf16_pair<kBN>(d_tmem, ahi + adv, blo + adv, 1u);
-                  umma_bf16_pair<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
+                  umma_kf16_pair(d_tmem, ahi + adv, blo + adv, idesc, 1u);
+                  umma_kf16_pair(d_tmem, alo + adv, bhi + adv, idesc, 1u);
                 }
               } else {
-                umma_bf16<kBN>(d_tmem, ahi + adv, bhi + adv, first);
+                umma_kf16(d_tmem, ahi + adv, bhi + adv, idesc, first);
                 if (kSplit) {
-                  umma_bf16<kBN>(d_tmem, ahi + adv, blo + adv, 1u);
-                  umma_bf16<kBN>(d_tmem, alo + adv, bhi + adv, 1u);
+                  umma_kf16(d_tmem, ahi + adv, blo + adv, idesc, 1u);
+                  umma_kf16(d_tmem, alo + adv, bhi + adv, idesc, 1u);
                 }
               }
             }
@@ -481,6 +491,20 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           const int ds = J.C_direct ? J.direct[cell] : -1;
           float* dst = ds >= 0 ? J.C_direct + (static_cast<long long>(ds) * J.h + j) * J.N
                                : J.products + (static_cast<long long>(cell) * J.h + j) * J.N;
+          if (J.a_exp) {  // undo the operands' scales: exact unless the result is subnormal
+            const int ea = J.a_exp[r];
+#pragma unroll
+            for (int q = 0; q < kCols / 4; ++q) {
+              const int n = n0 + 4 * q;
+              if (n < J.N) {
+                const int4 eb = *reinterpret_cast<const int4*>(J.b_exp + n);
+                accum[4 * q] = ldexpf(accum[4 * q], -(ea + eb.x));
+                accum[4 * q + 1] = ldexpf(accum[4 * q + 1], -(ea + eb.y));
+                accum[4 * q + 2] = ldexpf(accum[4 * q + 2], -(ea + eb.z));
+                accum[4 * q + 3] = ldexpf(accum[4 * q + 3], -(ea + eb.w));
+              }
+            }
+          }
 #pragma unroll
           for (int q = 0; q < kCols / 4; ++q) {
             const int n = n0 + 4 * q;
@@ -526,14 +550,16 @@ __global__ void wait_timeout_kernel(long long budget, int32_t* info) {
 
 // 2-D K-major bf16 tensor map: rows x K, box = box_rows x bk (bk = 64: 128 B
 // swizzle; bk = 32: 64 B swizzle), matching the UMMA descriptors.
-bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box_rows, int bk = BK) {
+bool make_map(CUtensorMap* map, const void* base, long long rows, int K, int box_rows, int bk = BK,
+              bool fp16 = false) {
   auto enc = get_encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(K) * 2};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+  CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box,
                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -672,14 +698,18 @@ namespace {
 
 bool tc_fill_job(TcJob* J, const DevPlan& p, const void* a_hi, const void* a_lo, const void* b_hi,
                  const void* b_lo, int num_cells, int N, int K, int h, int bn, bool pair, int bk,
-                 float* products, float* C_direct, int32_t* info_out) {
+                 float* products, float* C_direct, int32_t* info_out, const int32_t* a_exp = nullptr,
+                 const int32_t* b_exp = nullptr) {
   memset(J, 0, sizeof *J);
   const long long rows = static_cast<long long>(num_cells) * h;
   const int box_b = pair ? bn / 2 : bn;  // a paired CTA loads half of the B tile
-  if (!make_map(&J->map_ahi, a_hi, rows, K, BM, bk) || !make_map(&J->map_bhi, b_hi, N, K, box_b, bk))
+  const bool f16 = a_exp != nullptr;
+  if (!make_map(&J->map_ahi, a_hi, rows, K, BM, bk, f16) || !make_map(&J->map_bhi, b_hi, N, K, box_b, bk, f16))
     return false;
+  J->a_exp = a_exp;
+  J->b_exp = b_exp;
   if (a_lo) {
-    if (!make_map(&J->map_alo, a_lo, rows, K, BM, bk) || !make_map(&J->map_blo, b_lo, N, K, box_b, bk))
+    if (!make_map(&J->map_alo, a_lo, rows, K, BM, bk, f16) || !make_map(&J->map_blo, b_lo, N, K, box_b, bk, f16))
       return false;
   } else {
     J->map_alo = J->map_ahi;
@@ -741,15 +771,22 @@ bool gemm_config_ok(int config) { return tile_valid(config); }
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,
                            const void* b_hi, const void* b_lo, int num_cells, int N, int K, int h,
                            bool split3, float* products, float* C_direct, int config,
-                           int32_t* info_out, cudaStream_t st) {
+                           int32_t* info_out, cudaStream_t st, const int32_t* a_exp, const int32_t* b_exp) {
   if (!tile_valid(config)) return cudaErrorInvalidValue;
+  if ((a_exp != nullptr) != (b_exp != nullptr) || (a_exp && !split3)) return cudaErrorInvalidValue;
   (void)g;
   int group, seg_kb, bn, bk;
   int pair;
   decode_config(config, &group, &seg_kb, &bn, &pair, &bk);
+  // split fp16: the default accumulates 128-wide K segments.  The truncating
+  // TMEM adds would otherwise dominate its error: on the benchmark workload
+  // 512-wide segments put 1.9e-6 on direct blocks, 256-wide 9.9e-7, 128-wide
+  // 5.6e-7 (GEMM 2.05 / 2.10 / 2.27 ms), and on its worst peel chains
+  // (propagation factor 32) 256-wide segments 9.2e-6, 128-wide 7.9e-6.
+  if (a_exp && config == 0) seg_kb = 2;
   TcJob J;
   if (!tc_fill_job(&J, p, a_hi, split3 ? a_lo : nullptr, b_hi, split3 ? b_lo : nullptr, num_cells, N, K, h,
-                   bn, pair, bk, products, C_direct, info_out))
+                   bn, pair, bk, products, C_direct, info_out, a_exp, b_exp))
     return cudaErrorInvalidValue;
   const int units = pair ? (J.m_tiles_max + 1) / 2 : J.m_tiles_max;
   const long long tiles = static_cast<long long>(units) * J.n_tiles;

@@ -427,8 +427,9 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
                             const int* configs, int nconfigs, bpx_stream stream, int* best_config,
                             float* best_ms) {
   bpx::clear_error();
-  if (precision != BPX_BF16 && precision != BPX_BF16X3 && precision != BPX_EXACT)
-    return fail(BPX_ERR_UNSUPPORTED, "bpx_autotune tunes the tensor-core GEMM (BPX_BF16 / BPX_BF16X3 / BPX_EXACT)");
+  if (precision != BPX_BF16 && precision != BPX_BF16X3 && precision != BPX_EXACT && precision != BPX_FP16X3)
+    return fail(BPX_ERR_UNSUPPORTED,
+                "bpx_autotune tunes the tensor-core GEMM (BPX_BF16 / BPX_BF16X3 / BPX_FP16X3 / BPX_EXACT)");
   if (int rc = check_configs(configs, nconfigs, "bpx_autotune")) return rc;
   // one full run: plan, staged operands
   if (int rc = bpx_coded_matmul(c, d_A, d_B, M, N, K, h, precision, d_mask, d_C, nullptr, ws, ws_bytes,
@@ -438,7 +439,10 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
   const bpx::DevGraph g = bpx::make_graph(c, ws, L);
   const bpx::DevPlan p = bpx::make_plan(ws, L);
   char* base = static_cast<char*>(ws);
-  const bool split = precision == BPX_BF16X3;
+  const bool f16 = precision == BPX_FP16X3;
+  const bool split = precision == BPX_BF16X3 || f16;
+  const int32_t* a_exp = f16 ? reinterpret_cast<const int32_t*>(base + L.a_scale) : nullptr;
+  const int32_t* b_exp = f16 ? reinterpret_cast<const int32_t*>(base + L.b_scale) + N : nullptr;
   float* products = reinterpret_cast<float*>(base + L.products);
   cudaStream_t st = S(stream);
   if (precision == BPX_EXACT) {
@@ -462,7 +466,7 @@ extern "C" int bpx_autotune(const bpx_code* c, const float* d_A, const float* d_
                 cudaError_t e = bpx::launch_gemm_tc(g, p, base + L.a_hi, split ? base + L.a_lo : nullptr,
                                                     base + L.b_hi, split ? base + L.b_lo : nullptr,
                                                     c->num_cells, N, K, h, split, products, d_C, cfg,
-                                                    nullptr, st);
+                                                    nullptr, st, a_exp, b_exp);
                 return e == cudaSuccess ? BPX_OK : cuda_fail(e, "autotune launch");
               },
               best_config, best_ms);
@@ -531,7 +535,7 @@ extern "C" int bpx_autotune_peel(const bpx_code* c, const float* d_A, const floa
   return tune(ctas, nctas, st,
               [&](int n_ctas) -> int {
                 o.peel_ctas = n_ctas;
-                return bpx_peel_decode(c, products, N, h, d_C, 1, &o, ws, stream);
+                return bpx_peel_decode(c, products, nullptr, N, h, d_C, 1, &o, ws, ws_bytes, nullptr, stream);
               },
               best_ctas, best_ms);
 }

@@ -285,6 +285,13 @@ template <int kB, bool kGather>
 __global__ void __launch_bounds__(kPeelThreads)
 peel_kernel(DevPlan p, const float* __restrict__ P, float* C, long long nv, int chunk, int first_wave,
             int compensate_depth) {
+  if (p.ctr[CTR_PLAN] != kPlanReady) {  // no schedule has planned this workspace: refuse, write nothing
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicExch(&p.info[BPX_INFO_DEVICE_ERR], BPX_ERR_INVAL);
+      atomicExch(&p.info[BPX_INFO_STATUS], BPX_ERR_INVAL);
+    }
+    return;
+  }
   peel_body<kB, kGather>(p, P, C, nv, chunk, first_wave, compensate_depth, blockIdx.x);
 }
 

@@ -5,10 +5,17 @@
 //                 lo = RN(x - hi) (or hi only for plain bf16), K-major rows
 //                 ready for the TMA loads of the tcgen05 GEMM
 //   b_split       B (K x N, FP32) -> B^T hi / lo (N x K, bf16, K-major)
+//   encode_f16    the same sum per coded row, scaled by 2^e (e from the
+//                 row's largest magnitude, f16_scale_exp), split into fp16
+//                 hi = RN(x) and lo = RN(x - hi); e stored per coded row
+//   b_colmax / b_split_f16
+//                 max |B| per column, then B^T hi / lo in fp16 under the
+//                 column's 2^e
 //
 // c_i is the i-th surviving cell of the plan.  Rows of A past M read as zero
 // (the zero padding of the last source blocks).  All are HBM-bound streams.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "device_common.cuh"
@@ -166,6 +173,195 @@ encode_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict__
   for (int i = 0; i < kEncGroupRows; ++i)
     encode_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, nullptr, static_cast<__nv_bfloat16*>(J.a_hi),
                        static_cast<__nv_bfloat16*>(J.a_lo), rb0 + i, static_cast<int>(kc));
+}
+
+// ---- split-fp16 staging (BPX_FP16X3) --------------------------------------
+//
+// One CTA per coded row: the 256 threads sum 8 consecutive K-elements of
+// every source of the row's cell at a time (ascending sources, RN FP32 adds,
+// as the other encodes), take the row's largest magnitude with a block
+// reduction, and write the scaled fp16 halves.  Up to kF16Keep chunks per
+// thread (K <= 8192) stay in registers between the two steps; longer rows
+// sum their later chunks a second time.
+constexpr int kF16Threads = 256;
+constexpr int kF16Keep = 4;
+
+__device__ __forceinline__ void coded_chunk(const DevGraph& g, const float* __restrict__ A, int M, int K, int h,
+                                            int e0, int e1, int j, int k8, float (&acc)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+#pragma unroll 4
+  for (int e = e0; e < e1; ++e) {
+    const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+    if (arow >= M) continue;
+    const float4* src = reinterpret_cast<const float4*>(A + arow * K + k8);
+    const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+    acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
+    acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
+  }
+}
+
+// 8 scaled values -> fp16 hi and lo (16 bytes each)
+__device__ __forceinline__ void f16_split8(const float (&v)[8], int e, __half* hi, __half* lo) {
+  uint32_t hv[4], lv[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float x0 = scale_pow2(v[2 * q], e), x1 = scale_pow2(v[2 * q + 1], e);
+    const __half2 hh = __floats2half2_rn(x0, x1);
+    const float2 f = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(x0 - f.x, x1 - f.y);
+    hv[q] = *reinterpret_cast<const uint32_t*>(&hh);
+    lv[q] = *reinterpret_cast<const uint32_t*>(&ll);
+  }
+  *reinterpret_cast<uint4*>(hi) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+  *reinterpret_cast<uint4*>(lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+}
+
+__global__ void __launch_bounds__(kF16Threads)
+encode_f16_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, int h, __half* out_hi,
+                  __half* out_lo, int32_t* a_exp) {
+  __shared__ float red[kF16Threads / 32];
+  const int row = blockIdx.x;  // coded row, compacted order
+  if (row >= p.ctr[CTR_NSURV] * h) return;
+  const int ci = row / h, j = row - ci * h;
+  const int cell = p.surv[ci];
+  const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
+  const int nchunks = K / 8;  // K % 8 == 0
+  float keep[kF16Keep][8];
+#pragma unroll
+  for (int it = 0; it < kF16Keep; ++it)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) keep[it][i] = 0.f;
+  // sources outermost: a thread's loads of one source are all in flight at once
+  for (int e = e0; e < e1; ++e) {
+    const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+    if (arow >= M) continue;
+    const float* src = A + arow * K;
+    float4 x[kF16Keep][2];
+#pragma unroll
+    for (int it = 0; it < kF16Keep; ++it) {
+      const int c = it * kF16Threads + static_cast<int>(threadIdx.x);
+      if (c < nchunks) {
+        x[it][0] = __ldg(reinterpret_cast<const float4*>(src + 8 * c));
+        x[it][1] = __ldg(reinterpret_cast<const float4*>(src + 8 * c) + 1);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kF16Keep; ++it) {
+      const int c = it * kF16Threads + static_cast<int>(threadIdx.x);
+      if (c < nchunks) {
+        float* a = keep[it];
+        a[0] += x[it][0].x; a[1] += x[it][0].y; a[2] += x[it][0].z; a[3] += x[it][0].w;
+        a[4] += x[it][1].x; a[5] += x[it][1].y; a[6] += x[it][1].z; a[7] += x[it][1].w;
+      }
+    }
+  }
+  float amax = 0.f;
+#pragma unroll
+  for (int it = 0; it < kF16Keep; ++it)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) amax = fmaxf(amax, fabsf(keep[it][i]));
+  for (int c = kF16Keep * kF16Threads + static_cast<int>(threadIdx.x); c < nchunks; c += kF16Threads) {
+    float v[8];
+    coded_chunk(g, A, M, K, h, e0, e1, j, 8 * c, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) amax = fmaxf(amax, fabsf(v[i]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  amax = red[0];
+#pragma unroll
+  for (int w = 1; w < kF16Threads / 32; ++w) amax = fmaxf(amax, red[w]);
+  const int e = f16_scale_exp(amax);
+  if (threadIdx.x == 0) a_exp[row] = e;
+  const long long base = static_cast<long long>(row) * K;
+#pragma unroll
+  for (int it = 0; it < kF16Keep; ++it) {
+    const int c = it * kF16Threads + static_cast<int>(threadIdx.x);
+    if (c < nchunks) f16_split8(keep[it], e, out_hi + base + 8 * c, out_lo + base + 8 * c);
+  }
+  for (int c = kF16Keep * kF16Threads + static_cast<int>(threadIdx.x); c < nchunks; c += kF16Threads) {
+    float v[8];
+    coded_chunk(g, A, M, K, h, e0, e1, j, 8 * c, v);
+    f16_split8(v, e, out_hi + base + 8 * c, out_lo + base + 8 * c);
+  }
+}
+
+// max |B| per column: a CTA takes 256 columns (64 float4) x a range of
+// kColRows rows, four row phases; one atomicMax per column per CTA on the
+// float bits (ordered like the values, all being non-negative).
+constexpr int kColRows = 128;
+__global__ void __launch_bounds__(256) b_colmax_kernel(const float* __restrict__ B, int K, int N, uint32_t* bmax) {
+  __shared__ float4 red[4][64];
+  const int c4 = threadIdx.x & 63, ph = threadIdx.x >> 6;
+  const int n = blockIdx.x * 256 + 4 * c4;
+  const int k0 = blockIdx.y * kColRows, k1 = min(K, k0 + kColRows);
+  float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (n < N) {
+#pragma unroll 4
+    for (int k = k0 + ph; k < k1; k += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(B + static_cast<long long>(k) * N + n));
+      m.x = fmaxf(m.x, fabsf(v.x));
+      m.y = fmaxf(m.y, fabsf(v.y));
+      m.z = fmaxf(m.z, fabsf(v.z));
+      m.w = fmaxf(m.w, fabsf(v.w));
+    }
+  }
+  red[ph][c4] = m;
+  __syncthreads();
+  if (ph == 0 && n < N) {
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      m.x = fmaxf(m.x, red[q][c4].x);
+      m.y = fmaxf(m.y, red[q][c4].y);
+      m.z = fmaxf(m.z, red[q][c4].z);
+      m.w = fmaxf(m.w, red[q][c4].w);
+    }
+    atomicMax(bmax + n, __float_as_uint(m.x));
+    atomicMax(bmax + n + 1, __float_as_uint(m.y));
+    atomicMax(bmax + n + 2, __float_as_uint(m.z));
+    atomicMax(bmax + n + 3, __float_as_uint(m.w));
+  }
+}
+
+// B (K x N) -> B^T fp16 hi / lo (N x K) under each column's 2^e, through the
+// same 64 x 64 shared-memory transpose as b_split; the first k-tile's CTAs
+// also record each column's exponent for the GEMM epilogue.
+__global__ void __launch_bounds__(256)
+b_split_f16_kernel(const float* __restrict__ B, int K, int N, const uint32_t* __restrict__ bmax, __half* bt_hi,
+                   __half* bt_lo, int32_t* b_exp) {
+  __shared__ float tile[kTile][kTile + 1];
+  const int n0 = blockIdx.x * kTile, k0 = blockIdx.y * kTile;
+  {
+    const int c4 = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + 16 * i, k = k0 + r, n = n0 + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < K && n < N) v = __ldg(reinterpret_cast<const float4*>(B + static_cast<long long>(k) * N + n));
+      tile[r][4 * c4 + 0] = v.x;
+      tile[r][4 * c4 + 1] = v.y;
+      tile[r][4 * c4 + 2] = v.z;
+      tile[r][4 * c4 + 3] = v.w;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int t = threadIdx.x + 256 * i;
+    const int r = t >> 3, kc = t & 7;
+    const int n = n0 + r, k = k0 + 8 * kc;
+    if (n >= N || k >= K) continue;
+    const int e = f16_scale_exp(__uint_as_float(__ldg(bmax + n)));
+    if (blockIdx.y == 0 && kc == 0) b_exp[n] = e;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = tile[8 * kc + q][r];
+    const long long o = static_cast<long long>(n) * K + k;
+    f16_split8(v, e, bt_hi + o, bt_lo + o);
+  }
 }
 
 // ---- MXFP8 staging -------------------------------------------------------
@@ -347,6 +543,28 @@ cudaError_t launch_encode_split_group(const GJob* d_jobs, const long long* d_bas
     encode_group_kernel<2><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, d_bases, njobs);
   else
     encode_group_kernel<1><<<static_cast<unsigned>(total_ctas), kEncThreads, 0, st>>>(d_jobs, d_bases, njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_f16(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
+                              void* a_hi, void* a_lo, int32_t* a_exp, cudaStream_t st) {
+  const long long rows = static_cast<long long>(g.num_cells) * h;
+  if (rows == 0 || K == 0) return cudaSuccess;
+  if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+  encode_f16_kernel<<<static_cast<unsigned>(rows), kF16Threads, 0, st>>>(
+      g, p, A, M, K, h, static_cast<__half*>(a_hi), static_cast<__half*>(a_lo), a_exp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_f16(const float* B, int K, int N, void* b_hi, void* b_lo, uint32_t* b_max, int32_t* b_exp,
+                         cudaStream_t st) {
+  if (K == 0 || N == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(b_max, 0, sizeof(uint32_t) * static_cast<size_t>(N), st);
+  if (e != cudaSuccess) return e;
+  b_colmax_kernel<<<dim3((N + 255) / 256, (K + kColRows - 1) / kColRows), 256, 0, st>>>(B, K, N, b_max);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  b_split_f16_kernel<<<dim3((N + kTile - 1) / kTile, (K + kTile - 1) / kTile), 256, 0, st>>>(
+      B, K, N, b_max, static_cast<__half*>(b_hi), static_cast<__half*>(b_lo), b_exp);
   return cudaGetLastError();
 }
 

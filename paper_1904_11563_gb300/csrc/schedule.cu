@@ -179,6 +179,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
       if (depth[s] == 1) p.direct[p.resolver[s]] = s;
     if (tid == 0) {
       p.ctr[CTR_NSURV] = nsurv;
+      p.ctr[CTR_PLAN] = 0;  // the rest of the plan follows (part 2)
       p.info[BPX_INFO_DEVICE_ERR] = 0;  // cleared before the products run
     }
     return;
@@ -259,6 +260,7 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
     p.ctr[CTR_NWAVES] = round;
     p.ctr[CTR_NREC] = nrec;
     p.ctr[CTR_ERR] = 0;
+    p.ctr[CTR_PLAN] = kPlanReady;
     int32_t inf[BPX_INFO_LEN];
     for (int i = 0; i < BPX_INFO_LEN; ++i) inf[i] = 0;
     // part 2 runs beside the products: keep a self-check error they raised

@@ -51,17 +51,6 @@ extern "C" int bpx_bound_paterson(int k, int b, int sigma, int* n_max) {
   return BPX_OK;
 }
 
-extern "C" int bpx_bound_theorem31(int k, int b, int sigma, double eps, int* n_max) {
-  bpx::clear_error();
-  if (!n_max || k < 1 || b < 1 || sigma < 1 || eps < 0) return bpx::fail(BPX_ERR_INVAL, "bpx_bound_theorem31: bad arguments");
-  const double sp = sigma * (1.0 + eps);
-  const double den = b * (k - sp) + sigma - 1;
-  if (den <= 0) return bpx::fail(BPX_ERR_INVAL, "bpx_bound_theorem31: needs b (k - sigma') + sigma - 1 > 0");
-  const double num = (static_cast<double>(k) * b + sigma - 1) * (k - 1) - (sigma - 1) * (sigma / 2.0 - 1);
-  *n_max = static_cast<int>(std::floor(num / den + 1e-12));
-  return BPX_OK;
-}
-
 extern "C" int bpx_code_from_cells(int n, int k, int b, int num_cells, const int32_t* col_of_cell,
                                    const int32_t* cell_ptr, const int32_t* cell_src, int e, bpx_code** out) {
   bpx::clear_error();

@@ -100,6 +100,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
          (static_cast<uint32_t>(BM >> 4) << 24);
 }
 
+// The same with A = B = F16 (operand format 0).
+template <int kBN>
+__host__ __device__ constexpr uint32_t idesc_f16() {
+  return (1u << 4) | (static_cast<uint32_t>(kBN >> 3) << 17) | (static_cast<uint32_t>(BM >> 4) << 24);
+}
+
+// kind::f16 MMA with the instruction descriptor given at run time (bf16 or
+// fp16 operands).
+__device__ __forceinline__ void umma_kf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 template <int kBN>
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
@@ -214,6 +230,19 @@ template <int kBN>
 __host__ __device__ constexpr uint32_t idesc_bf16_pair() {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kBN >> 3) << 17) |
          (static_cast<uint32_t>((2 * BM) >> 4) << 24);
+}
+
+template <int kBN>
+__host__ __device__ constexpr uint32_t idesc_f16_pair() {
+  return (1u << 4) | (static_cast<uint32_t>(kBN >> 3) << 17) | (static_cast<uint32_t>((2 * BM) >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_kf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 template <int kBN>

@@ -183,8 +183,10 @@ def test_2d_full_size_sysmoj_sampled(libbpx):
     direct = [s for s in range(64) if sch.depth[s] == 1][:1]
     Ah = A.cpu().numpy().astype(np.float64)
     Bh = B.cpu().numpy().astype(np.float64)
-    # propagation factors from 64 x 64 corners of every block (norm ratios)
-    sub = 64
+    # propagation factors from the leading 256 x 256 of every block: nu_s is
+    # a ratio of Frobenius norms of blocks with iid entries, which a sample
+    # of 65536 entries per block estimates to well under 1 %
+    sub = 256
     A_sub = np.concatenate([Ah[z * h:z * h + sub] for z in range(ref.b)])
     B_sub = np.concatenate([Bh[:, l * w:l * w + sub] for l in range(ref.k)], axis=1)
     nu = _nu_2d(ref, A_sub, B_sub, sub, sub, er)
@@ -193,4 +195,4 @@ def test_2d_full_size_sysmoj_sampled(libbpx):
         r = Ah[z * h:(z + 1) * h] @ Bh[:, l * w:(l + 1) * w]
         c = C[z * h:(z + 1) * h, l * w:(l + 1) * w].cpu().numpy()
         err = np.linalg.norm(c - r) / np.linalg.norm(r)
-        assert err <= 1e-5 * max(1.0, 1.5 * nu[s]), (s, sch.depth[s], err, nu[s])
+        assert err <= 1e-5 * max(1.0, nu[s]), (s, sch.depth[s], err, nu[s])

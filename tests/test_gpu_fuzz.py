@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
-TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-2, "mxfp8": 6e-2}
+TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5, "bf16": 2e-2, "mxfp8": 6e-2}
 CONFIGS = [0, 16041, 16042, 8041, 8042, 16045, 8046, 8085, 8086, 4081, 8080, 8089, 4080]
 
 
@@ -44,16 +44,25 @@ def _nu(ref, A, B, h, sch):
     return {s: nu.get(s, 1.0) for s in range(ref.num_sources)}
 
 
-@pytest.mark.parametrize("seed", range(60))
+PRECS = ["fp32", "bf16", "bf16x3", "mxfp8", "exact", "fp16x3"]
+
+
+@pytest.mark.parametrize("seed", range(72))
 def test_fuzz_one_dimensional(libbpx, seed):
     bpx = libbpx
     rng = np.random.default_rng(1000 + seed)
     code, ref = _random_code(bpx, rng)
-    prec = ["fp32", "bf16", "bf16x3", "mxfp8", "exact"][seed % 5]
+    prec = PRECS[seed % len(PRECS)]
     h = int(rng.choice([1, 2, 3, 7, 16, 33, 64, 130]))
     M = max(1, ref.num_sources * h - int(rng.integers(0, h)))
     K = 128 * int(rng.integers(1, 4)) if prec == "mxfp8" else 8 * int(rng.integers(1, 70))
     N = 4 * int(rng.integers(1, 150))
+    if prec == "mxfp8":
+        # E4M3 rounds each operand with an RMS relative error near 2.5 %, so a
+        # block's relative Frobenius error is a mean over its elements (about
+        # 3.6e-2 in expectation); blocks of >= 1024 elements keep that mean
+        # within a few percent of its expectation, below the 6e-2 tolerance
+        N = max(N, 4 * -(-1024 // (4 * h)))
     dist = ["uniform", "normal", "int"][int(rng.integers(0, 3))]
     A, B = W.inputs(M, K, N, dist, 2000 + seed)
     e = int(rng.integers(0, ref.n - ref.k + 1)) if ref.n > ref.k else 0
@@ -79,7 +88,7 @@ def test_fuzz_one_dimensional(libbpx, seed):
                 assert np.array_equal(C[lo:hi].view(np.uint32), R[lo:hi].view(np.uint32)), (seed, s)
         return
     R, _s = o.coded_matmul(ref, A, B, h, er)
-    if dist == "int" and prec in ("fp32", "bf16", "bf16x3") and K * 4 * ref.sigma < 2 ** 20:
+    if dist == "int" and prec in ("fp32", "bf16", "bf16x3", "fp16x3") and K * 4 * ref.sigma < 2 ** 20:
         for s in range(ref.num_sources):
             lo, hi = s * h, min((s + 1) * h, M)
             if sch.depth[s] and lo < hi:
@@ -95,7 +104,7 @@ def test_fuzz_one_dimensional(libbpx, seed):
         if nr == 0:
             continue
         err = np.linalg.norm(C[lo:hi] - r) / nr
-        assert err <= TOL[prec] * max(1.0, nu[s]) * (1.5 if prec == "mxfp8" else 1.0), (seed, prec, s, err, nu[s])
+        assert err <= TOL[prec] * max(1.0, nu[s]), (seed, prec, s, err, nu[s])
 
 
 @pytest.mark.parametrize("seed", range(20))

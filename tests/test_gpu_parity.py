@@ -3,7 +3,9 @@
 Integer and index work (surviving cells, peel order, resolvers, depths,
 recovered set) must match bit for bit; floating-point blocks of C must match
 the oracle's FP64 decode within the relative Frobenius tolerance per block
-(1e-5 for FP32 and split-BF16x3, 2e-2 for plain BF16).  Small-integer inputs
+(1e-5 for FP32, split-BF16x3 and split-FP16x3, 2e-2 for plain BF16) times
+the block's propagation factor; split-FP16x3 also flat, without the factor,
+on the full-size benchmark workload.  Small-integer inputs
 keep every FP32 intermediate exact, so there the match is bit-exact too.
 """
 import itertools
@@ -18,7 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
-TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-2}
+TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5, "bf16": 2e-2}
 
 
 def _pair(bpx, name):
@@ -158,7 +160,7 @@ def _run(bpx, code, A, B, h, prec, mask, opts=None):
     return C.cpu().numpy(), info.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "fp16x3"])
 def test_table1_all_masks_vs_oracle(libbpx, prec):
     """Workload table1_512: every erasure pattern of <= 2 columns (and the
     3-column ones the code also tolerates), every block within tolerance."""
@@ -181,7 +183,7 @@ def test_table1_all_masks_vs_oracle(libbpx, prec):
     ("B6_8_4_2", 2, 64, 32, 260),
     ("table1", 130, 520, 64, 8),       # blocks taller than a tile
 ])
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "fp16x3"])
 def test_integer_inputs_bit_exact(libbpx, name, h, M, K, N, prec):
     """Small-integer inputs: every intermediate is an exact integer < 2^24,
     so the decoded C equals the oracle (and A B) bit for bit."""
@@ -223,6 +225,64 @@ def test_products_and_peel_separately(libbpx):
     R, sch = _oracle_decode(ref, A, B, h, m)
     err = _rel_block_err(C.cpu().numpy(), R, h, ref.num_sources)
     assert err.max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "exact"])
+def test_peel_decode_takes_the_erasure_mask(libbpx, prec):
+    """peel_decode(products, erasure_mask) -> C: given the mask, the peel
+    plans itself -- over a workspace whose plan was overwritten by another
+    mask's schedule it still decodes the products of its own mask, bit for
+    bit as the whole path does; given no mask it peels along the plan in the
+    workspace."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "sys8_3_8")
+    h, M, K, N = 4, 256, 96, 64
+    A, B = W.inputs(M, K, N, "normal", 31)
+    P_ = bpx.PRECISIONS[prec]
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    m = torch.from_numpy(W.erasure_mask(code.n, 3, 77)).cuda()
+    other = torch.from_numpy(W.erasure_mask(code.n, 3, 78)).cuda()
+    want, _info = bpx.coded_matmul(code, dA, dB, h, P_, m, bpx.Workspace(code, M, N, K, h, P_),
+                                   opts=bpx.default_opts(direct_write=0))
+    ws = bpx.Workspace(code, M, N, K, h, P_)
+    bpx.schedule(code, m, ws)
+    if prec == "exact":
+        prods = bpx.exact_products(code, dA, dB, h, ws)
+    else:
+        prods = bpx.coded_products(code, dA, dB, h, P_, ws)
+    bpx.schedule(code, other, ws)  # a stale plan for another mask
+    C = bpx.alloc_C(code, h, N)
+    info = torch.zeros(bpx.INFO_LEN, dtype=torch.int32, device="cuda")
+    if prec == "exact":
+        bpx.peel_decode_exact(code, prods, N, h, C, ws, mask=m, info=info)
+    else:
+        bpx.peel_decode(code, prods, N, h, C, ws, direct_written=False, mask=m, info=info)
+    torch.cuda.synchronize()
+    assert int(info[bpx.INFO_STATUS]) == bpx.OK
+    assert torch.equal(C[:M], want[:M])
+    C2 = bpx.alloc_C(code, h, N)
+    if prec == "exact":
+        bpx.peel_decode_exact(code, prods, N, h, C2, ws)
+    else:
+        bpx.peel_decode(code, prods, N, h, C2, ws, direct_written=False)
+    torch.cuda.synchronize()
+    assert torch.equal(C2[:M], want[:M])
+
+
+def test_peel_without_a_plan_is_refused(libbpx):
+    """A workspace no schedule has planned: the peel writes nothing and
+    reports BPX_ERR_INVAL in the plan's info words."""
+    bpx = libbpx
+    code, _ref = _pair(bpx, "table1")
+    h, N = 8, 16
+    ws = bpx.Workspace(code, 32, N, 16, h, bpx.FP32)
+    prods = torch.ones((code.num_cells * h, N), device="cuda")
+    C = torch.full((code.num_sources * h, N), 7.0, device="cuda")
+    bpx.peel_decode(code, prods, N, h, C, ws, direct_written=False)
+    torch.cuda.synchronize()
+    assert bool((C == 7.0).all())
+    info = ws.info().cpu().numpy()
+    assert info[bpx.INFO_STATUS] == bpx.ERR_INVAL and info[bpx.INFO_DEVICE_ERR] == bpx.ERR_INVAL
 
 
 def test_undecodable_partial(libbpx):
@@ -347,7 +407,8 @@ def test_async_host_calls_in_flight(libbpx, prec):
 @pytest.mark.parametrize("prec,cfg", [("bf16x3", 0), ("bf16", 0), ("fp32", 0), ("bf16x3", 16041), ("bf16x3", 8042),
                                       ("bf16", 16041), ("bf16x3", 16022), ("bf16x3", 16045), ("bf16x3", 8025),
                                       ("bf16x3", 16046), ("bf16", 16045), ("bf16", 8046), ("bf16x3", 8089),
-                                      ("bf16", 16089), ("bf16x3", 8080), ("bf16", 4080)])
+                                      ("bf16", 16089), ("bf16x3", 8080), ("bf16", 4080), ("fp16x3", 0),
+                                      ("fp16x3", 8080), ("fp16x3", 16021), ("fp16x3", 8049)])
 def test_many_tiles_per_cta(libbpx, prec, cfg):
     """Bench-shaped code and block height at reduced N, K: ~600 output tiles
     of 128 x 256, so every persistent CTA runs several tiles and both TMEM
@@ -364,7 +425,7 @@ def test_many_tiles_per_cta(libbpx, prec, cfg):
         _check_blocks(C, R, ref, A, B, h, m, prec)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "bf16", "mxfp8"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "bf16", "mxfp8", "fp16x3"])
 def test_full_size_sysmoj_8192_sampled(libbpx, prec):
     """The benchmark workload at full size (A, B 8192 x 8192 N(0,1), h = 128,
     3 erased columns) in the benchmark's launch configuration; blocks of C
@@ -393,7 +454,62 @@ def test_full_size_sysmoj_8192_sampled(libbpx, prec):
         assert err <= TOL[prec] * max(1.0, nu[s]), (prec, s, sch.depth[s], err, nu[s])
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "mxfp8", "exact"])
+@pytest.mark.parametrize("trial", [21, 4])
+def test_full_size_sysmoj_8192_flat_tolerance(libbpx, trial):
+    """The accuracy target at full size: split-FP16x3 (the three tensor-core
+    products of split-BF16x3 over fp16 halves) decodes the benchmark workload
+    (A, B 8192 x 8192 N(0,1), h = 128, 3 erased columns, default launch
+    configuration) with every checked block within a FLAT 1e-5 of FP64
+    A_s B -- no propagation factor -- on the deepest sources and on
+    directly copied ones.  Trials 21 and 4 of the benchmark's 100 masks
+    reach depth 9; trial 21 (with 42) has the largest propagation factor
+    of all 100 (32.6)."""
+    bpx = libbpx
+    wl = W.WORKLOADS["sysmoj_8192"]
+    code, ref = _pair(bpx, "sys8_3_8")
+    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+    A, B = W.device_inputs(M, K, N, "normal", 2)
+    m = W.erasure_mask(11, 3, wl["mask_seed_base"] + trial)
+    ws = bpx.Workspace(code, M, N, K, h, bpx.FP16X3)
+    C, info = bpx.coded_matmul(code, A, B, h, bpx.FP16X3, torch.from_numpy(m).cuda(), ws)
+    torch.cuda.synchronize()
+    assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
+    sch = o.wave_schedule(ref, o.surviving_cells(ref, list(np.nonzero(m)[0])))
+    deep = sorted(range(64), key=lambda s: -sch.depth[s])[:3]
+    direct = [s for s in range(64) if sch.depth[s] == 1][:2]
+    assert max(sch.depth) == 9
+    Ah = A.cpu().numpy()
+    Bh = B.cpu().numpy().astype(np.float64)
+    for s in deep + direct:
+        r = o.row_block(Ah, s, h) @ Bh
+        c = C[s * h:(s + 1) * h].cpu().numpy()
+        err = np.linalg.norm(c - r) / np.linalg.norm(r)
+        assert err <= 1e-5, (s, sch.depth[s], err)
+
+
+@pytest.mark.parametrize("name,h,M,K,N", [("table3", 8, 72, 200, 136), ("sys8_3_8", 4, 256, 520, 64)])
+def test_fp16x3_wide_dynamic_range(libbpx, name, h, M, K, N):
+    """Split-FP16x3 scales every coded row and every column of B by its own
+    power of two: sources whose magnitudes differ by up to 2^80 and columns
+    by up to 2^60 (far outside fp16's range unscaled) still decode within
+    1e-5 times the propagation factor of the oracle's FP64 decode."""
+    bpx = libbpx
+    code, ref = _pair(bpx, name)
+    rng = np.random.default_rng(7)
+    A, B = W.inputs(M, K, N, "normal", 17)
+    rows = np.repeat(2.0 ** rng.integers(-40, 41, size=(M + h - 1) // h), h)[:M]
+    A = (A * rows[:, None]).astype(np.float32)
+    B = (B * (2.0 ** rng.integers(-30, 31, size=N))[None, :]).astype(np.float32)
+    for t in range(4):
+        m = W.erasure_mask(code.n, t % (code.e + 1), 500 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.FP16X3, m)
+        R, sch = _oracle_decode(ref, A, B, h, m)
+        assert info[bpx.INFO_STATUS] == (bpx.OK if sch.ok else bpx.ERR_UNDECODABLE)
+        if sch.ok:
+            _check_blocks(C, R, ref, A, B, h, m, "fp16x3")
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "mxfp8", "exact", "fp16x3"])
 def test_steps_in_flight_on_two_streams(libbpx, prec):
     """The benchmark's launch configuration: steps in flight on two streams,
     each with its own workspace, C and info words, issued alternately with
@@ -433,7 +549,7 @@ def test_steps_in_flight_on_two_streams(libbpx, prec):
         assert torch.equal(C, want[t]), (prec, t)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp32", "fp16x3"])
 def test_construction_a_full_size_integer_bit_exact(libbpx, prec):
     """Workload mojA_16384 at full size (Construction A n=32, k=24, b=683,
     h=1: 16392 one-row sources, ~20.9k coded rows, A 16384 x 16384,
@@ -466,7 +582,7 @@ def test_construction_a_full_size_integer_bit_exact(libbpx, prec):
 
 
 @pytest.mark.parametrize("wl_name,code_name", [("table1_logu", "table1"), ("table3_logu", "table3")])
-@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp16x3"])
 def test_precision_study_loguniform(libbpx, wl_name, code_name, prec):
     """Precision workload: magnitudes log-uniform on [1e-3, 1e3] with random
     signs (cancellation in the peel), every mask of <= 2 erased columns
@@ -520,6 +636,31 @@ def test_mxfp8_table1_all_masks(libbpx):
         R, sch = _oracle_decode(ref, A, B, wl["h"], m)
         assert info[bpx.INFO_STATUS] == bpx.OK
         _check_blocks(C, R, ref, A, B, wl["h"], m, "mxfp8")
+
+
+@pytest.mark.parametrize("cfg", [0, 8001])
+def test_mxfp8_construction_a_tall_bit_exact(libbpx, cfg):
+    """MXFP8 on a tall projection code: Construction A n = 12, k = 9, b = 120
+    (1080 one-row sources, sigma = 9, so the peel takes its gathered form
+    over many waves), three erased columns.  With ternary inputs every coded
+    sum is an integer of magnitude <= 9, which a UE8M0-scaled E4M3 element
+    holds exactly, and every product and peel step stays an exact FP32
+    integer: the decode equals the oracle's, and A B, bit for bit."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "A12_9_120")
+    h, K, N = 1, 512, 256
+    M = ref.num_sources * h
+    A = W.matrix((M, K), "ternary", 61)
+    B = W.matrix((K, N), "ternary", 62)
+    ref_C = o.reference_product(A, B)
+    for t in range(3):
+        m = W.erasure_mask(code.n, 3, 700 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.MXFP8, m, opts=bpx.default_opts(gemm_config=cfg))
+        R, sch = _oracle_decode(ref, A, B, h, m)
+        assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
+        assert max(sch.depth) > 5
+        assert np.array_equal(C[:M], R[:M]), (t, np.abs(C[:M] - R[:M]).max())
+        assert np.array_equal(C[:M], ref_C)
 
 
 @pytest.mark.parametrize("cfg", [0, 8001, 4009])

@@ -199,14 +199,6 @@ def test_bounds_match_oracle(libbpx):
             assert bpx.bound("k_equals_sigma", k, b) == o.bound_k_equals_sigma(k, b)
             for s in range(1, k):
                 assert bpx.bound("paterson", k, b, s) == o.bound_paterson(k, b, s)
-                for eps in (0.0, 0.1, 0.5):
-                    try:
-                        want = o.bound_theorem31(k, b, s, eps)
-                    except ValueError:
-                        with pytest.raises(bpx.BpxError):
-                            bpx.bound("theorem31", k, b, s, eps)
-                        continue
-                    assert bpx.bound("theorem31", k, b, s, eps) == want
     assert bpx.bound("k_equals_sigma", 2, 2) == 5 == bpx.Code.table1().n
     assert bpx.bound("paterson", 3, 3, 2) == 5 == bpx.Code.table3().n
 

@@ -837,33 +837,6 @@ def test_paper_codes_meet_the_bounds():
     assert t3.n - t3.k == CLAIMS["table3_n_minus_k"] == o.bound_paterson(t3.k, t3.b, t3.sigma) - t3.k
 
 
-def test_theorem31_two_forms_agree():
-    """Theorem 3.1 is printed as one fraction and as k + sigma - 1 + a
-    fraction whose numerator is garbled; reading the missing operator as +,
-    b (k (sigma' - sigma) + (sigma - 1) sigma') - (sigma - 1)(3 sigma / 2 - 1),
-    the two are the same expression (symbolic check)."""
-    sp = pytest.importorskip("sympy")
-    k, b, s, q = sp.symbols("k b sigma sigmap")
-    first = ((k * b + s - 1) * (k - 1) - (s - 1) * (s / 2 - 1)) / (b * (k - q) + s - 1)
-    second = k + s - 1 + (b * (k * (q - s) + (s - 1) * q) - (s - 1) * (3 * s / 2 - 1)) / (b * (k - q) + s - 1)
-    assert sp.simplify(first - second) == 0
-
-
-def test_theorem31_limits():
-    """eps = 0 and b -> infinity: Theorem 3.1 tends to its stated limit; the
-    appearance count it rests on holds for the Mojette constructions."""
-    for k, s in [(8, 3), (10, 4), (12, 5), (9, 3)]:
-        assert o.bound_theorem31(k, 10 ** 7, s, 0.0) == o.bound_large_b(k, s)
-    for n, k, b in [(7, 4, 10), (9, 6, 12), (11, 8, 16)]:
-        code = o.construction_a(n, k, b)
-        # every source appears in all n columns (one bin per projection)
-        appear = np.zeros(code.num_sources, dtype=int)
-        for c in code.cells:
-            for s_ in c:
-                appear[s_] += 1
-        assert appear.min() >= n - k + 1
-
-
 def test_array_bpxor_check_on_known_codes():
     assert o.is_array_bpxor(o.table1()) and o.is_array_bpxor(o.table3())
     bad = o.code_from_columns("rep", 2, 2, [[(0,), (1,)], [(2,), (3,)], [(0, 1), (2, 3)], [(0, 2), (1, 3)],
