@@ -531,6 +531,9 @@ void bpx_group_free(bpx_group* group);
  * the mask (input) and the outputs; NULL outputs are skipped.
  *   - The first call on each device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     The address is kept for the life of the process: after a device reset
+ *     (cudaDeviceReset, or anything else that replaces the device's primary
+ *     context) do not call this entry point again in that process.
  *   - Codes whose scratch exceeds 8 MiB are rejected with BPX_ERR_INVAL
  *     (roughly 3 num_edges + 8 num_cells + 9 num_sources int32 words).
  *   - Every call uploads its code's graph into the shared array and reuses
