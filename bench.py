@@ -38,6 +38,7 @@ CODE_TEXT = {
                       "in the two-dimensional scheme (source (z, l) = A_z B_l, 1024 x 1024 blocks)",
     "sysmoj_8192_straggler": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, "
                              "slopes 0,+1,-1); processor-level stragglers, task times sigma_c X_c, X_c ~ Exp(1)",
+    "mojA_bsweep": "Mojette Construction A n=32 (k=24 x b grid, q=1, p=-15..16), e=8, b in {16, 32, 64, 683}",
     "batch512": "512 jobs: half array codes (Table I, Table III, systematic Mojette n=6..32, e=2..3), "
                 "half Construction A (n=6..32, e=n//4); each job its own seeded mask",
 }
@@ -95,7 +96,7 @@ def _parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "mxfp8", "fp32", "exact"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "mxfp8", "fp32", "exact", "fp16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-inflight", type=int, default=3,
@@ -246,11 +247,13 @@ class StageEvents:
 TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5, "bf16": 2e-2, "mxfp8": 6e-2, "exact": 1e-5}
 
 
-def _propagation(code, order, Ah, Bh, h, sources, ncols=256):
+def _propagation(code, order, Ah, Bh, h, sources, ncols=256, kappa=None):
     """nu_s = sqrt(sum_c coef_{s,c}^2 ||P_c||^2) / ||C_s|| for the sampled
     sources: coef from the peel recurrence over the library's plan (each
     recovered source = its resolver's product minus the resolver's other
-    sources), norms of FP64 products on the first `ncols` columns of B."""
+    sources), norms of FP64 products on the first `ncols` columns of B.
+    With a dict `kappa`, also kappa_s = sum_c |coef_{s,c}| ||P_c|| / ||C_s||
+    (the worst case) into it."""
     res = {int(s_): int(r_) for s_, r_, _d in order if s_ >= 0}
     seq = [int(s_) for s_, _r, _d in order if s_ >= 0]
     coef = {}
@@ -281,7 +284,10 @@ def _propagation(code, order, Ah, Bh, h, sources, ncols=256):
                 Ac = sum(blk(int(t_)) for t_ in code.cell_src[code.cell_ptr[c_]:code.cell_ptr[c_ + 1]])
                 pn[c_] = float(np.linalg.norm(Ac @ Bs))
         num = np.sqrt(sum(float(v_) ** 2 * pn[c_] ** 2 for c_, v_ in coef[s_].items()))
-        nu[s_] = float(num / np.linalg.norm(blk(s_) @ Bs))
+        den = np.linalg.norm(blk(s_) @ Bs)
+        nu[s_] = float(num / den)
+        if kappa is not None:
+            kappa[s_] = float(sum(abs(float(v_)) * pn[c_] for c_, v_ in coef[s_].items()) / den)
     return nu
 
 
@@ -1107,6 +1113,96 @@ def run_straggler(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_bsweep(args, wl):
+    """Construction A n = 32, k = 24, e = 8 at every grid height b of the
+    sweep: the worst-case overhead eps against the conditioning of the peel
+    (depth, nu_s, kappa_s), and every precision's relative error per depth
+    against FP64 A_s B, with its useful TFLOP/s (one seeded mask per b)."""
+    import torch
+    from paper_1904_11563_gb300 import build as B_
+    B_.build()
+    from paper_1904_11563_gb300 import bpx
+    from paper_1904_11563_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    K, N, h = wl["K"], wl["N"], 1
+    precs = [p_ for p_ in (args.precisions.split(",") if args.precisions else
+                           ["fp32", "bf16x3", "fp16x3", "mxfp8", "exact"]) if p_]
+    sweep = []
+    head_tflops = None
+    for b in wl["bs"]:
+        code = bpx.Code.mojette_a(32, 24, b)
+        S = code.num_sources
+        M = S
+        A, Bm = W.device_inputs(M, K, N, wl["dist"], wl["seed"], device=dev)
+        mask = torch.from_numpy(W.erasure_mask(32, wl["e"], wl["mask_seed_base"])).to(dev)
+        order, _rec, info = bpx.schedule(code, mask, bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32, device=dev))
+        order = order.cpu().numpy()
+        assert int(info.cpu()[bpx.INFO_STATUS]) == bpx.OK
+        depth = {int(s_): int(d_) for s_, _r, d_ in order if s_ >= 0}
+        nsurv = int(info.cpu()[bpx.INFO_SURVIVING])
+        # up to three sources per depth bucket [2^i, 2^(i+1))
+        buckets = {}
+        for s_ in sorted(depth, key=lambda x: (-depth[x], x)):
+            bi = int(np.floor(np.log2(depth[s_])))
+            if len(buckets.setdefault(bi, [])) < 3:
+                buckets[bi].append(s_)
+        samples = sorted(s_ for v_ in buckets.values() for s_ in v_)
+        Ah = A.cpu().numpy()
+        Bh = Bm.cpu().numpy().astype(np.float64)
+        refs = {s_: Ah[s_:s_ + 1].astype(np.float64) @ Bh for s_ in samples}
+        nu, kap = {}, {}
+        if b <= 64:   # the integer expansion of the deep codes is too large to walk here
+            nu = _propagation(code, order, Ah, Bh, h, samples, ncols=N, kappa=kap)
+        errs, tflops = {}, {}
+        for prec in precs:
+            P = bpx.PRECISIONS[prec]
+            ws = bpx.Workspace(code, M, N, K, h, P, device=dev)
+            C = bpx.alloc_C(code, h, N, dev)
+            bpx.coded_matmul(code, A, Bm, h, P, mask, ws, C=C)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(3):
+                _C, inf = bpx.coded_matmul(code, A, Bm, h, P, mask, ws, C=C)
+            t1.record()
+            torch.cuda.synchronize()
+            assert int(inf.cpu()[bpx.INFO_STATUS]) == bpx.OK
+            tflops[prec] = 2.0 * M * N * K / (t0.elapsed_time(t1) / 3 * 1e-3) / 1e12
+            Cn = C.double().cpu().numpy()
+            errs[prec] = {s_: float(np.linalg.norm(Cn[s_] - refs[s_]) / np.linalg.norm(refs[s_])) for s_ in samples}
+            del ws, C
+        by_depth = []
+        for bi in sorted(buckets):
+            ss = buckets[bi]
+            row = {"depths": [2 ** bi, 2 ** (bi + 1) - 1], "sources": ss,
+                   "err_max": {p_: max(errs[p_][s_] for s_ in ss) for p_ in precs}}
+            if nu:
+                row["nu_max"] = max(nu[s_] for s_ in ss)
+                row["kappa_max"] = max(kap[s_] for s_ in ss)
+            by_depth.append(row)
+        ent = {"b": b, "sources": S, "cells": code.num_cells, "surviving_cells": nsurv,
+               "eps": code.eps, "coded_rows_over_sources": nsurv / S, "max_depth": max(depth.values()),
+               "useful_tflops": tflops, "by_depth": by_depth}
+        if not nu:
+            ent["nu_kappa"] = "not computed (integer expansion over hundreds of waves; its coefficients reach ~1e26)"
+        sweep.append(ent)
+        if b == max(wl["bs"]):
+            head_tflops = tflops.get("bf16x3")
+        del A, Bm
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": head_tflops, "unit": "TFLOP/s", "n_gpus": 1, "steps": 3, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+            "data": "synthetic",
+            "config": {"workload": "mojA_bsweep", "code": CODE_TEXT["mojA_bsweep"], "K": K, "N": N, "h": 1,
+                       "inputs": "U(-1,1) FP32, seed 4; mask seed 4000", "value": "bf16x3 at b = 683",
+                       "reference": "FP64 A_s B (numpy) per sampled source"},
+            "b_sweep": sweep}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _parse()
     from paper_1904_11563_gb300 import workloads as W
@@ -1116,6 +1212,10 @@ def main():
         wl["M"], wl["N"], wl["K"] = (int(x) for x in args.shape.split(","))
     if args.workload == "batch512":
         run_batch(args)
+    elif wl.get("bsweep"):
+        if args.impl == "reference":
+            raise SystemExit("mojA_bsweep is an error report of this library's paths; no reference arm")
+        run_bsweep(args, wl)
     elif wl.get("twod") and args.impl != "reference":
         run_2d(args, wl)
     elif wl.get("straggler") and args.impl != "reference":

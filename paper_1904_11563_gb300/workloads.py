@@ -32,6 +32,10 @@ WORKLOADS = {
     "table3_logu": dict(code=("table3",), h=64, M=576, K=256, N=128, dist="loguniform", seed=3, e=2),
     "mojA_16384": dict(code=("mojette_a", 32, 24, 683), h=1, M=16384, K=16384, N=8192,
                        dist="uniform", seed=4, e=8, mask_seed_base=4000),
+    # the overhead-versus-conditioning sweep of Construction A n = 32, k = 24,
+    # e = 8: grid heights b (S = 24 b one-row sources, A S x K), one seeded mask
+    "mojA_bsweep": dict(code=("mojette_a", 32, 24, 0), bs=(16, 32, 64, 683), h=1, M=0, K=4096, N=1024,
+                        dist="uniform", seed=4, e=8, mask_seed_base=4000, bsweep=True),
     # the benchmark workload with processor-level stragglers: every step draws
     # each cell's task time sigma_c X_c, X_c ~ Exp(mu = 1) (seed 5000 + step),
     # and decodes from the first decodable set of arrived products

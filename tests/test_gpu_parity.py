@@ -581,6 +581,35 @@ def test_construction_a_full_size_integer_bit_exact(libbpx, prec):
     assert np.array_equal(Cn, ref), (prec, np.abs(Cn - ref).max())
 
 
+@pytest.mark.parametrize("b", [16, 32, 64])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3", "mxfp8", "exact"])
+def test_construction_a_b_sweep(libbpx, b, prec):
+    """Construction A n = 32, k = 24, e = 8 over the grid heights of the
+    overhead-versus-conditioning sweep (b = 16: eps 14.4, depth 2; b = 32:
+    depth 13; b = 64: depth 45, expansion coefficients up to ~8e4): every
+    block within its tolerance times its propagation factor against the
+    oracle's FP64 decode, exact slices bit for bit against the oracle's
+    exact-slice decode."""
+    bpx = libbpx
+    code, ref = _pair(bpx, f"A32_24_{b}")
+    h, K, N = 1, 512, 256
+    M = ref.num_sources
+    A, B = W.inputs(M, K, N, "uniform", 4)
+    m = W.erasure_mask(32, 8, 4000)
+    er = list(np.nonzero(m)[0])
+    C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+    assert info[bpx.INFO_STATUS] == bpx.OK
+    if prec == "exact":
+        R, _Q, _s = o.exact_slice_coded_matmul(ref, A, B, h, er)
+        assert np.array_equal(C[:M].view(np.uint32), R[:M].view(np.uint32))
+        return
+    R, sch = _oracle_decode(ref, A, B, h, m)
+    TOLS = dict(TOL, mxfp8=6e-2)
+    err = _rel_block_err(C, R, h, ref.num_sources)
+    nu = _nu(ref, A, B, h, m)
+    assert np.all(err <= TOLS[prec] * np.maximum(1.0, nu)), (prec, b, (err / (TOLS[prec] * np.maximum(1.0, nu))).max())
+
+
 @pytest.mark.parametrize("wl_name,code_name", [("table1_logu", "table1"), ("table3_logu", "table3")])
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp16x3"])
 def test_precision_study_loguniform(libbpx, wl_name, code_name, prec):
