@@ -116,6 +116,8 @@ def _parse():
                     help="M,N,K override of the workload (profiling of reduced cases only)")
     ap.add_argument("--jobs", type=int, default=512,
                     help="jobs of the batch512 workload (fewer: profiling of reduced cases only)")
+    ap.add_argument("--oracle-sample-seconds", type=float, default=0.0,
+                    help=argparse.SUPPRESS)  # internal: time the oracle alone for about this long, print JSON
     return ap.parse_args()
 
 
@@ -310,21 +312,47 @@ def _cores():
     return os.cpu_count()
 
 
-def cpu_baseline(A, B, wl, budget_s=12.0):
-    """The oracle as it stands on a bounded column sample of the workload."""
-    M, K, N, h = wl["M"], wl["K"], wl["N"], wl["h"]
+def _oracle_timed(A, B, wl, budget_s, cols):
+    """Times the oracle's coded path on column samples of `cols` columns until
+    about budget_s seconds have passed; returns (seconds, columns)."""
     from paper_1904_11563_gb300 import workloads as W
     mask = _mask(W, wl, 0)
-    cols = 256
-    t = _oracle_sample(A, B, h, mask, cols, wl)
-    total_t, total_cols = t, cols
-    while total_t < budget_s and total_cols + cols <= N:
-        total_t += _oracle_sample(A, B, h, mask, cols, wl)
+    total_t, total_cols = 0.0, 0
+    while total_cols == 0 or (total_t < budget_s and total_cols + cols <= wl["N"]):
+        total_t += _oracle_sample(A, B, wl["h"], mask, cols, wl)
         total_cols += cols
+    return total_t, total_cols
+
+
+def oracle_single_thread(wl, budget_s=10.0, cols=128):
+    """The oracle on one host thread: a child process with every BLAS / OpenMP
+    pool limited to one thread (set before numpy loads), inputs of the same
+    shapes and distribution from the host generator."""
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", wl["name"],
+           "--oracle-sample-seconds", str(budget_s)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": (r.stderr or r.stdout).strip().splitlines()[-1:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    useful = 2.0 * wl["M"] * wl["K"] * out["cols"]
+    return {"value": useful / out["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle FP64 coded path (numpy BLAS on one thread) on {out['cols']} of {wl['N']} columns "
+                      f"of B, same shapes and distribution (host generator), trial mask seed "
+                      f"{wl['mask_seed_base']}, {out['seconds']:.1f} s"}
+
+
+def cpu_baseline(A, B, wl, budget_s=12.0):
+    """The oracle as it stands on a bounded column sample of the workload."""
+    M, K, N = wl["M"], wl["K"], wl["N"]
+    total_t, total_cols = _oracle_timed(A, B, wl, budget_s, 256)
     useful = 2.0 * M * K * total_cols
     return {"value": useful / total_t / 1e12, "unit": "TFLOP/s", "cores": _cores(), "kind": "oracle",
-            "sample": f"oracle FP64 coded path (numpy BLAS) on {total_cols} of {N} columns of B, "
-                      f"trial mask seed {wl['mask_seed_base']}, {total_t:.1f} s"}
+            "sample": f"oracle FP64 coded path (numpy BLAS, all host cores) on {total_cols} of {N} columns of B, "
+                      f"trial mask seed {wl['mask_seed_base']}, {total_t:.1f} s",
+            "single_thread": oracle_single_thread(wl)}
 
 
 # ------------------------------------------------------------ replicas (N > 1)
@@ -1210,6 +1238,12 @@ def main():
     wl["name"] = args.workload
     if args.shape:
         wl["M"], wl["N"], wl["K"] = (int(x) for x in args.shape.split(","))
+    if args.oracle_sample_seconds > 0:
+        A = W.matrix((wl["M"], wl["K"]), wl["dist"], wl["seed"])
+        B = W.matrix((wl["K"], wl["N"]), wl["dist"], wl["seed"] + 1)
+        secs, cols = _oracle_timed(A, B, wl, args.oracle_sample_seconds, 128)
+        print(json.dumps({"seconds": secs, "cols": cols}), flush=True)
+        return
     if args.workload == "batch512":
         run_batch(args)
     elif wl.get("bsweep"):
