@@ -210,8 +210,13 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
   return r;
 }
 
+// Arrive on a barrier of either CTA of the pair (a shared::cluster address).
+// The epilogue uses it only to say that its TMEM reads, already completed by
+// tcgen05.wait::ld, are done: the default (CTA-scope) release suffices, and a
+// cluster-scope release would also wait for the thread's earlier global
+// stores (the previous tile's output) on every accumulation segment.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
 
 // TMA load into this CTA's shared memory whose completion is counted on a
