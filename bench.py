@@ -246,7 +246,10 @@ class StageEvents:
 
 # ------------------------------------------------------------------ CPU oracle legs
 
-TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5, "bf16": 2e-2, "mxfp8": 6e-2, "exact": 1e-5}
+TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16x3": 1e-5, "bf16": 2e-2, "mxfp8": 6e-2, "exact": 1e-5,
+       "bf16x3-fused": 1e-5}
+# MMA flops executed per useful coded flop by each tensor-core precision
+MMA_MULT = {"bf16x3": 3, "bf16x3-fused": 3, "fp16x3": 3, "bf16": 1, "mxfp8": 1}
 
 
 def _propagation(code, order, Ah, Bh, h, sources, ncols=256, kappa=None):
@@ -448,7 +451,7 @@ def run_ours(args, wl):
     if args.precisions:
         precs = [x for x in args.precisions.split(",") if x]
     elif args.precision == "auto":
-        precs = ["bf16x3", "fp32", "bf16", "mxfp8", "exact", "fp16x3"]
+        precs = ["bf16x3", "fp32", "bf16", "mxfp8", "exact", "fp16x3", "bf16x3-fused"]
     else:
         precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
     results = {}
@@ -466,7 +469,9 @@ def run_ours(args, wl):
         surv_rows.append(int(sum(int(col_cells[j]) for j in range(code.n) if not m[j])) * h)
 
     for prec in precs:
-        P = bpx.PRECISIONS[prec]
+        # "<precision>-fused": the same precision with the encode fused into the GEMM's operand load
+        fused = int(prec.endswith("-fused"))
+        P = bpx.PRECISIONS[prec.replace("-fused", "")]
         try:
             ws = bpx.Workspace(code, M, N, K, h, P, device=dev)
         except bpx.BpxError:
@@ -479,7 +484,7 @@ def run_ours(args, wl):
             if prec in ("bf16x3", "bf16", "exact", "fp16x3"):
                 cfg, _tuned_ms = bpx.autotune(code, A, Bm, h, P, masks[0], ws, C=C)
         tuned[prec] = cfg
-        opts = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth)
+        opts = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth, fused_encode=fused)
         try:
             for i in range(warm):
                 bpx.coded_matmul(code, A, Bm, h, P, masks[i % wl["trials"]], ws, C=C, opts=opts, info=info)
@@ -499,7 +504,7 @@ def run_ours(args, wl):
         clocks.begin()
         t0.record()
         for i in range(steps):
-            o = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth)
+            o = bpx.default_opts(gemm_config=cfg, compensate_depth=args.compensate_depth, fused_encode=fused)
             o.stage_events = sev.ptr(i)
             bpx.coded_matmul(code, A, Bm, h, P, masks[(warm + i) % wl["trials"]], ws, C=C, opts=o, info=info)
         t1.record()
@@ -632,7 +637,7 @@ def run_ours(args, wl):
             S_ex = bpx.exact_params(code, K)["S"]
             mult = S_ex * (S_ex + 1) // 2
         else:
-            mult = {"bf16x3": 3, "fp16x3": 3, "bf16": 1, "mxfp8": 1}[head]
+            mult = MMA_MULT[head]
         flops = 2.0 * rows_mean * N * K * mult
         achieved = flops / (gemm_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0) * (2.0 if head == "mxfp8" else 1.0)
@@ -708,7 +713,7 @@ def run_ours(args, wl):
                 S_ex = bpx.exact_params(code, K)["S"]
                 mult = S_ex * (S_ex + 1) // 2     # digit pairs (i, l) with i + l < S
             else:
-                mult = {"bf16x3": 3, "fp16x3": 3, "bf16": 1, "mxfp8": 1}[prec]
+                mult = MMA_MULT[prec]
             pk = peaks.get("bf16_tflops", 1900.0) * (2.0 if prec == "mxfp8" else 1.0)
             unit = "measured bf16 burst" + (" x 2 (nominal fp8/bf16)" if prec == "mxfp8" else "")
             work = 2.0 * rows_m * N * K * mult
@@ -737,7 +742,7 @@ def run_ours(args, wl):
         line["b_split"] = _hbm(4.0 * K * N + (4 if head == "bf16x3" else 2) * K * N, st_.get("b_prep", 0.0),
                                "read B (4 K N) + write B^T hi (+ lo) bf16")
     line["clocks"] = R["clocks"]
-    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 4, "exact": 7, "fp16x3": 7}[head]
+    per_step = {"bf16x3": 5, "bf16": 5, "mxfp8": 5, "fp32": 4, "exact": 7, "fp16x3": 7, "bf16x3-fused": 4}[head]
     line["gpu_launches"] = per_step * steps
 
     # end to end through the host entry points (pinned host buffers): every

@@ -134,6 +134,13 @@ typedef struct {
   int mask_cells;       /* 0 (default): erasure masks have one byte per code column (a node
                            straggled); 1: one byte per cell (a single processor's output is
                            missing, the straggler model of Section IV) */
+  int fused_encode;     /* 0 (default): the encode (a2) is its own HBM-bound pass writing the
+                           coded bf16 operand before the GEMM; 1: BPX_BF16 / BPX_BF16X3 form
+                           the coded rows inside the GEMM's operand load (transform warps sum
+                           the FP32 source rows and split them on chip; the same bits); needs
+                           gemm_config 0 or a CTA-pair 64-wide config (tile code 0), else
+                           BPX_ERR_INVAL; other precisions and codes with sigma > 8:
+                           BPX_ERR_UNSUPPORTED */
 } bpx_opts;
 
 /* Stages of the hot path, in launch order (for bpx_opts.stage_events). */

@@ -48,7 +48,8 @@ class _CodeInfo(ct.Structure):
 class Opts(ct.Structure):
     _fields_ = [("direct_write", ct.c_int), ("compensate_depth", ct.c_int),
                 ("peel_ctas", ct.c_int), ("gemm_config", ct.c_int),
-                ("stage_events", ct.POINTER(ct.c_void_p)), ("mask_cells", ct.c_int)]
+                ("stage_events", ct.POINTER(ct.c_void_p)), ("mask_cells", ct.c_int),
+                ("fused_encode", ct.c_int)]
 
 
 STAGE_SCHEDULE, STAGE_B_PREP, STAGE_A_PREP, STAGE_GEMM, STAGE_PEEL = range(5)

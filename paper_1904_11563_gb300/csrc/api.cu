@@ -226,6 +226,15 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
   char* base = static_cast<char*>(ws);
   const int config = opts ? opts->gemm_config : 0;
   if (!bpx::gemm_config_ok(config)) return fail(BPX_ERR_INVAL, "bpx_coded_products: gemm_config %d names no tile", config);
+  const bool fused = opts && opts->fused_encode;
+  if (fused && precision != BPX_BF16 && precision != BPX_BF16X3)
+    return fail(BPX_ERR_UNSUPPORTED, "bpx_coded_products: the fused encode is built for BPX_BF16 and BPX_BF16X3");
+  if (fused && c->sigma > 8)
+    return fail(BPX_ERR_UNSUPPORTED, "bpx_coded_products: the fused encode takes cells of at most 8 sources "
+                "(sigma = %d)", c->sigma);
+  if (fused && config != 0 && config % 10 != 0)
+    return fail(BPX_ERR_INVAL, "bpx_coded_products: the fused encode needs gemm_config 0 or tile code 0 (got %d)",
+                config);
   cudaError_t e = cudaSuccess;
   switch (precision) {
     case BPX_FP32: {
@@ -249,10 +258,13 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
       e = bpx::launch_b_split(d_B, K, N, b_hi, b_lo, st);
       stage_mark(opts, BPX_STAGE_B_PREP, 1, st);
       stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
-      if (e == cudaSuccess) e = bpx::launch_encode_split(g, p, d_A, M, K, h, a_hi, a_lo, st);
+      if (e == cudaSuccess && !fused) e = bpx::launch_encode_split(g, p, d_A, M, K, h, a_hi, a_lo, st);
       stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
       stage_mark(opts, BPX_STAGE_GEMM, 0, st);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && fused)
+        e = bpx::launch_gemm_fused(g, p, d_A, M, b_hi, b_lo, c->num_cells, N, K, h, split, d_products, d_C, config,
+                                   d_info, st);
+      else if (e == cudaSuccess)
         e = bpx::launch_gemm_tc(g, p, a_hi, a_lo, b_hi, b_lo, c->num_cells, N, K, h, split,
                                 d_products, d_C, config, d_info, st);
       stage_mark(opts, BPX_STAGE_GEMM, 1, st);

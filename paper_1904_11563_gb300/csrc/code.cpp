@@ -288,6 +288,7 @@ extern "C" bpx_opts bpx_default_opts(void) {
   o.gemm_config = 0;
   o.stage_events = nullptr;
   o.mask_cells = 0;
+  o.fused_encode = 0;
   return o;
 }
 

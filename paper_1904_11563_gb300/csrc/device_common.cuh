@@ -261,6 +261,12 @@ cudaError_t launch_gemm_mx(const DevPlan& p, const void* a8, const void* sfa, co
 cudaError_t launch_gemm_f32(const DevGraph& g, const DevPlan& p, const float* a_coded, const float* B, int N, int K,
                             int h, float* products, float* C_direct, cudaStream_t st);
 // Tensor-core coded GEMM over the staged bf16 operands (split or plain).
+// The encode fused into the GEMM's operand load (BPX_BF16 / BPX_BF16X3,
+// CTA-pair 256 x 256 tiles): the coded rows are summed from A and split on
+// chip; config 0 or a CTA-pair 64-wide config (tile code 0).
+cudaError_t launch_gemm_fused(const DevGraph& g, const DevPlan& p, const float* A, int M, const void* b_hi,
+                              const void* b_lo, int num_cells, int N, int K, int h, bool split3, float* products,
+                              float* C_direct, int config, int32_t* info_out, cudaStream_t st);
 // a_exp / b_exp non-null: the split-fp16 operands of BPX_FP16X3 (a_lo and
 // b_lo required), unscaled by 2^-(a_exp[row] + b_exp[col]) in the epilogue.
 cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi, const void* a_lo,

@@ -708,6 +708,55 @@ def test_mxfp8_many_tiles(libbpx, cfg):
     _check_blocks(C, R, ref, A, B, h, m, "mxfp8")
 
 
+@pytest.mark.parametrize("name,h,M,K,N", [
+    ("table3", 3, 26, 136, 200),       # ragged: M < S h, K and N not tile multiples, cells inside a tile
+    ("sys8_3_8", 128, 8192, 512, 1024),  # the benchmark code: one cell per 128-row tile, many tiles per CTA
+    ("A11_8_12", 1, 96, 264, 132),     # one-row sources of many cells in a tile, deep chains
+    ("table1", 130, 520, 64, 8),       # blocks taller than a tile
+    ("sys6_5_5", 40, 1200, 1000, 516),
+])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_fused_encode_equals_materialized(libbpx, name, h, M, K, N, prec):
+    """The encode fused into the GEMM's operand load forms the same coded
+    sums (ascending sources, FP32 round-to-nearest) and the same bf16 split
+    as the encode pass, so the decoded C is bit for bit the materialized
+    path's -- for every tile shape the fused kernel takes."""
+    bpx = libbpx
+    code, ref = _pair(bpx, name)
+    A, B = W.inputs(M, K, N, "normal", 23)
+    for t, cfg in enumerate([0, 16080, 8020, 4040]):
+        m = W.erasure_mask(code.n, min(code.e, t % 3), 900 + t)
+        want, info0 = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m, opts=bpx.default_opts(gemm_config=cfg))
+        got, info1 = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m,
+                          opts=bpx.default_opts(gemm_config=cfg, fused_encode=1))
+        assert info0[bpx.INFO_STATUS] == info1[bpx.INFO_STATUS]
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), (name, prec, cfg)
+
+
+def test_fused_encode_integer_bit_exact_and_refusals(libbpx):
+    """Small-integer inputs through the fused encode: C equals A B bit for
+    bit; a config other than the CTA-pair 64-wide tiles is refused
+    (ERR_INVAL), and so is a precision the fused kernel does not build
+    (ERR_UNSUPPORTED)."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "B6_8_4_2")
+    h, M, K, N = 2, 64, 32, 260
+    A = W.matrix((M, K), "int", 21)
+    B = W.matrix((K, N), "int", 22)
+    for t in range(4):
+        m = W.erasure_mask(code.n, t % (code.e + 1), 950 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.BF16X3, m, opts=bpx.default_opts(fused_encode=1))
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        assert np.array_equal(C[:M], o.reference_product(A, B))
+    m = W.erasure_mask(code.n, 1, 960)
+    with pytest.raises(bpx.BpxError) as ei:
+        _run(bpx, code, A, B, h, bpx.BF16X3, m, opts=bpx.default_opts(fused_encode=1, gemm_config=8081))
+    assert ei.value.code == bpx.ERR_INVAL
+    with pytest.raises(bpx.BpxError) as ei:
+        _run(bpx, code, A, B, h, bpx.FP32, m, opts=bpx.default_opts(fused_encode=1))
+    assert ei.value.code == bpx.ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16", "mxfp8", "exact"])
 @pytest.mark.parametrize("cfg", [8083, 8084, 4087, 16088, -1])
 def test_configs_without_a_tile_are_refused(libbpx, prec, cfg):
