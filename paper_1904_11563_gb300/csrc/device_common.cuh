@@ -124,7 +124,7 @@ struct GJob {
   int M, N, K, h;
   long long bsplit_base, enc_base, peel_base;
   int peel_chunk;
-  int enc_sblocks;  // grouped encode: row blocks per k-chunk, in groups of kEncGroupRows
+  int enc_sblocks;  // grouped encode: CTAs of the job (kEncGroupRows row blocks each, every k-chunk)
 };
 
 // Index of the last entry of the ascending array bases[0 .. n) that is <= x:
@@ -160,13 +160,13 @@ __host__ __device__ inline int enc_k_chunks(int K) {
 // Grid sizes of the multi-job kernels for one job.
 inline long long bsplit_ctas(int N, int K) { return static_cast<long long>((N + 63) / 64) * ((K + 63) / 64); }
 inline long long encode_ctas(long long rows, int K) { return enc_row_blocks(rows, K) * enc_k_chunks(K); }
-// The grouped encode's CTA takes kEncGroupRows row blocks of one k-chunk, so
-// that its job search and index arithmetic are shared by more rows.
+// The grouped encode's CTA takes kEncGroupRows row blocks over every k-chunk,
+// so that its job search and each row's lookups are shared by more elements.
 constexpr int kEncGroupRows = 8;
 inline long long enc_group_sblocks(long long rows, int K) {
   return (enc_row_blocks(rows, K) + kEncGroupRows - 1) / kEncGroupRows;
 }
-inline long long encode_group_ctas(long long rows, int K) { return enc_group_sblocks(rows, K) * enc_k_chunks(K); }
+inline long long encode_group_ctas(long long rows, int K) { return enc_group_sblocks(rows, K); }
 int peel_chunk_for(long long nv, int ctas_hint);
 
 // Launchers (defined in the .cu files).  All return cudaError_t of the launch.

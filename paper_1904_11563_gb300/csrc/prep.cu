@@ -158,21 +158,66 @@ b_split_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict_
                static_cast<int>(local - by * gx), static_cast<int>(by));
 }
 
+// One row block over every k-chunk (the grouped encode): the row's cell and
+// source range are looked up once, then each of the thread's 8-element
+// chunks along K sums the same sources in the same ascending order (the same
+// bits as encode_body).
+template <int kMode>
+__device__ __forceinline__ void encode_rows_body(const DevGraph& g, const DevPlan& p, const float* __restrict__ A,
+                                                 int M, int K, int h, __nv_bfloat16* out_hi, __nv_bfloat16* out_lo,
+                                                 int rblock) {
+  const int tpr = enc_threads_per_row(K);
+  const int row = rblock * (kEncThreads / tpr) + threadIdx.x / tpr;
+  if (row >= p.ctr[CTR_NSURV] * h) return;
+  const int ci = row / h, j = row - ci * h;
+  const int cell = p.surv[ci];
+  const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
+  const long long obase = static_cast<long long>(row) * K;
+  for (int k8 = (threadIdx.x % tpr) * kEncVec; k8 < K; k8 += tpr * kEncVec) {
+    uint64_t acc2[kEncVec / 2] = {0, 0, 0, 0};
+    for (int e = e0; e < e1; ++e) {
+      const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+      if (arow >= M) continue;
+      const float* src = A + arow * K + k8;
+      uint64_t x[kEncVec / 2];
+      asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(x[0]), "=l"(x[1]) : "l"(src));
+      asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(x[2]), "=l"(x[3]) : "l"(src + 4));
+#pragma unroll
+      for (int q = 0; q < kEncVec / 2; ++q) asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc2[q]) : "l"(x[q]));
+    }
+    float acc[kEncVec];
+#pragma unroll
+    for (int q = 0; q < kEncVec / 2; ++q)
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * q]), "=f"(acc[2 * q + 1]) : "l"(acc2[q]));
+    uint32_t hv[4], lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(acc[2 * q], acc[2 * q + 1]);
+      hv[q] = *reinterpret_cast<const uint32_t*>(&hh);
+      if (kMode == 2) {
+        const float2 f = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(acc[2 * q] - f.x, acc[2 * q + 1] - f.y);
+        lv[q] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
+    }
+    *reinterpret_cast<uint4*>(out_hi + obase + k8) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    if (kMode == 2) *reinterpret_cast<uint4*>(out_lo + obase + k8) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+  }
+}
+
 template <int kMode>
 __global__ void __launch_bounds__(kEncThreads)
 encode_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict__ bases, int njobs) {
   const long long b = blockIdx.x;
   const int j = find_base(bases, njobs, b);
   const GJob& J = jobs[j];
-  // kEncGroupRows row blocks of one k-chunk (row blocks past the job's rows
+  // kEncGroupRows row blocks, every k-chunk (row blocks past the job's rows
   // return at once: their coded rows are beyond the surviving cells')
-  const uint32_t local = static_cast<uint32_t>(b - __ldg(bases + j));  // < 2^31: one launch's CTAs
-  const uint32_t sb = static_cast<uint32_t>(J.enc_sblocks), kc = local / sb;
-  const int rb0 = static_cast<int>(local - kc * sb) * kEncGroupRows;
+  const int rb0 = static_cast<int>(b - __ldg(bases + j)) * kEncGroupRows;
 #pragma unroll 1
   for (int i = 0; i < kEncGroupRows; ++i)
-    encode_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, nullptr, static_cast<__nv_bfloat16*>(J.a_hi),
-                       static_cast<__nv_bfloat16*>(J.a_lo), rb0 + i, static_cast<int>(kc));
+    encode_rows_body<kMode>(J.g, J.p, J.A, J.M, J.K, J.h, static_cast<__nv_bfloat16*>(J.a_hi),
+                            static_cast<__nv_bfloat16*>(J.a_lo), rb0 + i);
 }
 
 // ---- split-fp16 staging (BPX_FP16X3) --------------------------------------
