@@ -509,6 +509,34 @@ def test_fp16x3_wide_dynamic_range(libbpx, name, h, M, K, N):
             _check_blocks(C, R, ref, A, B, h, m, "fp16x3")
 
 
+def test_fp16x3_zero_rows_columns_and_tiny_scales(libbpx):
+    """Split-FP16x3's scale edge cases: a source block and a column of B that
+    are all zero (exponent 0, products exactly zero), a row position scaled
+    by 2^-100 in every source block (coded rows are sums of the same row
+    position, so each keeps one scale) and a column of B by 2^100 (fp16
+    holds neither unscaled): small-integer inputs under those scales stay
+    exact, so C equals the oracle's FP64 decode bit for bit."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "table3")
+    h, K, N = 8, 64, 36
+    M = ref.num_sources * h
+    A = W.matrix((M, K), "int", 31).astype(np.float64)
+    B = W.matrix((K, N), "int", 32).astype(np.float64)
+    A[2 * h:3 * h] = 0.0            # a whole source block of zeros
+    B[:, 5] = 0.0                   # a zero column
+    A[3::h] *= 2.0 ** -100          # row position 3 of every block, near the bottom of FP32's range
+    B[:, 7] *= 2.0 ** 100           # a column near the top
+    A, B = A.astype(np.float32), B.astype(np.float32)
+    for t in range(4):
+        m = W.erasure_mask(code.n, t % (code.e + 1), 60 + t)
+        C, info = _run(bpx, code, A, B, h, bpx.FP16X3, m)
+        R, sch = _oracle_decode(ref, A, B, h, m)
+        assert info[bpx.INFO_STATUS] == (bpx.OK if sch.ok else bpx.ERR_UNDECODABLE)
+        for s in range(ref.num_sources):
+            if sch.depth[s]:
+                assert np.array_equal(C[s * h:(s + 1) * h], R[s * h:(s + 1) * h]), (t, s)
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "mxfp8", "exact", "fp16x3"])
 def test_steps_in_flight_on_two_streams(libbpx, prec):
     """The benchmark's launch configuration: steps in flight on two streams,
@@ -919,7 +947,7 @@ def test_gathered_peel_with_register_waves(libbpx, comp):
     assert [tuple(int(x) for x in r) for r in order.cpu().numpy()] == [tuple(x) for x in sch2.order]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "mxfp8", "exact"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "mxfp8", "exact", "fp16x3", "bf16x3-fused"])
 def test_degenerate_shapes(libbpx, prec):
     """Edge cases of the path: M = 0 (every source block is zero padding, A
     empty: C must be zero), the smallest blocks (h = 1, N = 4, the smallest K
@@ -927,14 +955,16 @@ def test_degenerate_shapes(libbpx, prec):
     decode is a copy of the data cells' products) -- each bit for bit on
     small integers, with the plan's status OK."""
     bpx = libbpx
-    P = bpx.PRECISIONS[prec]
+    fused = prec.endswith("-fused")   # the encode fused into the GEMM's operand load
+    P = bpx.PRECISIONS[prec.replace("-fused", "")]
     kmin = 128 if prec == "mxfp8" else 8
+    opts = bpx.default_opts(fused_encode=int(fused))
     # M = 0
     code = bpx.Code.table1()
     A = torch.empty((0, kmin), device="cuda")
     B = torch.from_numpy(W.matrix((kmin, 4), "int", 71)).cuda()
     ws = bpx.Workspace(code, 0, 4, kmin, 1, P)
-    C, info = bpx.coded_matmul(code, A, B, 1, P, torch.from_numpy(W.erasure_mask(5, 3, 1)).cuda(), ws)
+    C, info = bpx.coded_matmul(code, A, B, 1, P, torch.from_numpy(W.erasure_mask(5, 3, 1)).cuda(), ws, opts=opts)
     torch.cuda.synchronize()
     assert info.cpu().numpy()[bpx.INFO_STATUS] == bpx.OK
     assert C.shape == (4, 4) and not C.abs().sum().item()
@@ -943,13 +973,13 @@ def test_degenerate_shapes(libbpx, prec):
     Bn = W.matrix((kmin, 4), "int", 73)
     for t in range(3):
         m = W.erasure_mask(5, 3, 10 + t)
-        Cn, inf = _run(bpx, code, An, Bn, 1, P, m)
+        Cn, inf = _run(bpx, code, An, Bn, 1, P, m, opts=opts)
         assert inf[bpx.INFO_STATUS] == bpx.OK
         assert np.array_equal(Cn, o.reference_product(An, Bn)), (prec, t)
     # no erasure on a systematic code
     code_s = bpx.Code.systematic(4, 2, 3)
     As = W.matrix((24, 2 * kmin), "int", 74)
     Bs = W.matrix((2 * kmin, 8), "int", 75)
-    Cs, inf = _run(bpx, code_s, As, Bs, 2, P, np.zeros(6, dtype=np.uint8))
+    Cs, inf = _run(bpx, code_s, As, Bs, 2, P, np.zeros(6, dtype=np.uint8), opts=opts)
     assert inf[bpx.INFO_STATUS] == bpx.OK and inf[bpx.INFO_WAVES] == 1
     assert np.array_equal(Cs, o.reference_product(As, Bs))
