@@ -222,13 +222,12 @@ encode_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict__
 
 // ---- split-fp16 staging (BPX_FP16X3) --------------------------------------
 //
-// One CTA per coded row: the 256 threads sum 8 consecutive K-elements of
-// every source of the row's cell at a time (ascending sources, RN FP32 adds,
-// as the other encodes), take the row's largest magnitude with a block
-// reduction, and write the scaled fp16 halves.  Up to kF16Keep chunks per
-// thread (K <= 8192) stay in registers between the two steps; longer rows
-// sum their later chunks a second time.
-constexpr int kF16Threads = 256;
+// One CTA per coded row: the threads sum 8 consecutive K-elements of every
+// source of the row's cell at a time (ascending sources, RN FP32 adds, as the
+// other encodes), take the row's largest magnitude with a block reduction,
+// and write the scaled fp16 halves.  Up to kF16Keep chunks per thread stay in
+// registers between the two steps: 256 threads hold rows of K <= 8192, 512
+// threads K <= 16384; longer rows sum their later chunks a second time.
 constexpr int kF16Keep = 4;
 
 __device__ __forceinline__ void coded_chunk(const DevGraph& g, const float* __restrict__ A, int M, int K, int h,
@@ -262,6 +261,7 @@ __device__ __forceinline__ void f16_split8(const float (&v)[8], int e, __half* h
   *reinterpret_cast<uint4*>(lo) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
 }
 
+template <int kF16Threads>
 __global__ void __launch_bounds__(kF16Threads)
 encode_f16_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, int h, __half* out_hi,
                   __half* out_lo, int32_t* a_exp) {
@@ -596,8 +596,12 @@ cudaError_t launch_encode_f16(const DevGraph& g, const DevPlan& p, const float* 
   const long long rows = static_cast<long long>(g.num_cells) * h;
   if (rows == 0 || K == 0) return cudaSuccess;
   if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
-  encode_f16_kernel<<<static_cast<unsigned>(rows), kF16Threads, 0, st>>>(
-      g, p, A, M, K, h, static_cast<__half*>(a_hi), static_cast<__half*>(a_lo), a_exp);
+  if (K <= 256 * 8 * kF16Keep)
+    encode_f16_kernel<256><<<static_cast<unsigned>(rows), 256, 0, st>>>(
+        g, p, A, M, K, h, static_cast<__half*>(a_hi), static_cast<__half*>(a_lo), a_exp);
+  else
+    encode_f16_kernel<512><<<static_cast<unsigned>(rows), 512, 0, st>>>(
+        g, p, A, M, K, h, static_cast<__half*>(a_hi), static_cast<__half*>(a_lo), a_exp);
   return cudaGetLastError();
 }
 
