@@ -77,6 +77,12 @@ __device__ __forceinline__ void umma_mx(uint32_t d, uint64_t a, uint64_t b, uint
       "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(acc));
 }
 
+// Streaming (.cs) output stores: written once, they should not push the
+// operand tiles other CTAs still read out of L2.
+__device__ __forceinline__ void st_cs4_mx(float* p, float a, float b, float c, float d) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
 __device__ __forceinline__ void raise_mx(const MxParams& P, int code, volatile int* abort_flag) {
   *abort_flag = 1;
   atomicExch(&P.info[BPX_INFO_DEVICE_ERR], code);
@@ -256,8 +262,7 @@ gemm_mx_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
         for (int q = 0; q < 32; ++q) {
           const int n = n0 + 4 * q;
           if (n < P.N)
-            *reinterpret_cast<float4*>(dst + n) =
-                make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+            st_cs4_mx(dst + n, accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
         }
       }
     }
@@ -487,8 +492,7 @@ gemm_mx_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_cons
         for (int q = 0; q < 32; ++q) {
           const int n = n0 + 4 * q;
           if (n < P.N)
-            *reinterpret_cast<float4*>(dst + n) =
-                make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+            st_cs4_mx(dst + n, accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
         }
       }
     }

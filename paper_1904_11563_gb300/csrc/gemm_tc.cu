@@ -89,6 +89,13 @@ struct Stage {
   static constexpr uint32_t kBlo = kBhi + kB;
 };
 
+// Output stores of the epilogue: streaming (.cs), so that the products and
+// C blocks written once per tile do not push the operand tiles other CTAs
+// are still reading out of L2.
+__device__ __forceinline__ void st_cs4(float* p, float a, float b, float c, float d) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
 __device__ __forceinline__ void raise_error(const TcJob& J, int code, volatile int* abort_flag) {
   *abort_flag = 1;
   atomicExch(&J.info[BPX_INFO_DEVICE_ERR], code);
@@ -470,8 +477,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           for (int q = 0; q < kCols / 4; ++q) {
             const int n = n0 + 4 * q;
             if (n < J.w2)
-              *reinterpret_cast<float4*>(dst + n) =
-                  make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+              st_cs4(dst + n, accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
           }
         }
       } else if (r < T.Mc) {
@@ -509,8 +515,7 @@ gemm_tc_kernel(const __grid_constant__ TcJob single, const TcJob* __restrict__ t
           for (int q = 0; q < kCols / 4; ++q) {
             const int n = n0 + 4 * q;
             if (n < J.N)
-              *reinterpret_cast<float4*>(dst + n) =
-                  make_float4(accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
+              st_cs4(dst + n, accum[4 * q], accum[4 * q + 1], accum[4 * q + 2], accum[4 * q + 3]);
           }
         }
       }
