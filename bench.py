@@ -50,8 +50,8 @@ CODE_TEXT = {
 # precision, config and the SHA-256 of the GEMM sources it was taken with: a
 # changed kernel reports null until it is captured again.
 TRAFFIC = {
-    ("sysmoj_8192", "bf16x3", 0): ("c276f4b8c49d129856a712990abfaa594302506a5315bd5270f74e3d02df4490",
-                                   2650650112 + 298668288),
+    ("sysmoj_8192", "bf16x3", 0): ("b653608ba7325866b23c715fd20a2f60acb16d7b16b30ed9f30d539d646aa41b",
+                                   2741324288 + 301022720),
 }
 
 
