@@ -267,6 +267,38 @@ def systematic_mojette(k: int, e: int, b: int) -> Code:
                             systematic_slopes(e), data_columns=k, e=e)
 
 
+def xcode(p: int) -> Code:
+    """X-code of Xu and Bruck (1999) on p columns, p prime: an equal-height
+    MDS array code whose two-column erasure decoding is a peeling chain, so
+    an array BP-XOR code in the sense of the Section III-A definition with
+    n = p, k = p - 2, b = p, t = 2 and sigma = p - 2.  Column j stores its
+    p - 2 data symbols (row r is source j (p - 2) + r) and two parity
+    symbols; the data symbol of row r in column j enters the first parity
+    of column j - r - 2 and the second parity of column j + r + 2 (mod p).
+    Written here from the data symbols' side: each symbol is dropped into
+    the two parities that contain it."""
+    if p < 3 or any(p % d == 0 for d in range(2, int(p ** 0.5) + 1)):
+        raise ValueError("X-code needs a prime p >= 3")
+    k = p - 2
+    first = [[] for _ in range(p)]
+    second = [[] for _ in range(p)]
+    for j in range(p):
+        for r in range(k):
+            s = j * k + r
+            first[(j - r - 2) % p].append(s)
+            second[(j + r + 2) % p].append(s)
+    cells, col_of_cell = [], []
+    for i in range(p):
+        for r in range(k):
+            cells.append((i * k + r,))
+            col_of_cell.append(i)
+        cells.append(tuple(sorted(first[i])))
+        cells.append(tuple(sorted(second[i])))
+        col_of_cell += [i, i]
+    return Code(name=f"xcode_p{p}", n=p, k=k, b=p, num_sources=p * k, cells=cells, col_of_cell=col_of_cell,
+                heights=[p] * p, proj=[None] * p, e=2)
+
+
 def lemma_a1_closed_form(t: int) -> int:
     """Lemma A.1: sum of |p_i| over the t slopes of Construction A equals
     (t^2 - 1)/4 for odd t and t^2/4 for even t."""

@@ -842,3 +842,41 @@ def test_array_bpxor_check_on_known_codes():
     bad = o.code_from_columns("rep", 2, 2, [[(0,), (1,)], [(2,), (3,)], [(0, 1), (2, 3)], [(0, 2), (1, 3)],
                                              [(0,), (3,)]])
     assert not o.is_array_bpxor(bad)
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 11])
+def test_xcode_is_an_mds_array_bpxor_code(p):
+    """The X-code on p columns peels from every set of p - 2 columns (brute
+    force over all pairs of erased columns: the MDS-by-peeling property Xu and
+    Bruck prove, which is the Section III-A definition with t = 2), has equal
+    column heights b = p, maximum degree sigma = p - 2 = k, and sits inside
+    the k = sigma bound on n.  Parities taken along one diagonal twice, or at
+    offset 0 or 3, break the property, so a wrong index or sign fails here."""
+    c = o.xcode(p)
+    assert (c.n, c.k, c.b, c.num_sources, c.e) == (p, p - 2, p, p * (p - 2), 2)
+    assert all(h == p for h in c.heights) and c.sigma == p - 2
+    assert o.is_array_bpxor(c)
+    assert c.n <= o.bound_k_equals_sigma(c.k, c.b)
+    # every source sits in its own column's degree-one cell and in exactly
+    # two parity cells of two other columns (p = 3: the parities have degree
+    # one as well)
+    for s in range(c.num_sources if p >= 5 else 0):
+        holders = [j for j, cell in enumerate(c.cells) if s in cell]
+        cols = [c.col_of_cell[j] for j in holders]
+        ones = [c.col_of_cell[j] for j in holders if len(c.cells[j]) == 1]
+        assert len(holders) == 3 and len(set(cols)) == 3 and ones == [s // (p - 2)]
+    if p >= 5:
+        k = p - 2
+
+        def mutated(off, sign):
+            cols = []
+            for i in range(p):
+                col = [(i * k + r,) for r in range(k)]
+                col.append(tuple(sorted(((i + r + 2) % p) * k + r for r in range(k))))
+                col.append(tuple(sorted(((i + sign * (r + off)) % p) * k + r for r in range(k))))
+                cols.append(col)
+            return o.code_from_columns("mutated", k, p, cols)
+
+        assert not o.is_array_bpxor(mutated(2, +1))
+        assert not o.is_array_bpxor(mutated(0, -1))
+        assert not o.is_array_bpxor(mutated(3, -1))
