@@ -61,7 +61,11 @@ enum bpx_variant {
                          p = -floor((n-1)/2)..ceil((n-1)/2) of the k x b grid; e = n - k */
   BPX_MOJETTE_B = 4,  /* Construction B (cons35): n projections q=2^q_e, p = n consecutive
                          odd integers from ceil_odd(1-n); e = n - ceil(k / 2^q_e) */
-  BPX_LITERAL = 5     /* a code given by its cells (bpx_code_from_cells, bpx_code_search) */
+  BPX_LITERAL = 5,    /* a code given by its cells (bpx_code_from_cells, bpx_code_search) */
+  BPX_XCODE = 6       /* X-code of Xu and Bruck (1999), an equal-height MDS array code whose
+                         two-column erasure decoding is a peeling chain, so an array BP-XOR
+                         code in the sense of Section III-A: n = p prime, b = p, k = p - 2,
+                         e = 2, sigma = p - 2 */
 };
 
 /* Arithmetic of the coded products.  FP32 accumulation in every case. */
@@ -159,6 +163,10 @@ enum bpx_stage {
  *   Table I / III: (n,k,b) must be (5,2,2) / (5,3,3); e may be -1.
  *   BPX_SYSTEMATIC: n = k + e data + parity columns on the k x b grid.
  *   BPX_MOJETTE_A / _B: n projections of the k x b grid; q_e >= 1 for _B.
+ *   BPX_XCODE: n = p prime, k = p - 2, b = p.  Column i holds the sources of
+ *     grid row i, s = i k + r (r < k), as degree-one cells, then the two
+ *     diagonal parities {((i + r + 2) mod p) k + r} and {((i - r - 2) mod p) k + r}
+ *     over r < k.
  * e = -1 derives the tolerated erasures; otherwise it must match.
  * Cell numbering: column ascending, then processor row / bin label ascending;
  * bins are placed by Eq. (moj1): pixel (z,l), z in [0,b), l in [0,k), is source

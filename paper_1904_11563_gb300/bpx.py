@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbpx.so")
 
 # enums of bpx.h
-TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B, LITERAL = 0, 1, 2, 3, 4, 5
+TABLE1, TABLE3, SYSTEMATIC, MOJETTE_A, MOJETTE_B, LITERAL, XCODE = 0, 1, 2, 3, 4, 5, 6
 SEARCH_SYSTEMATIC = 1  # bpx_code_search_ex flag
 FP32, BF16, BF16X3, MXFP8, EXACT, FP16X3 = 0, 1, 2, 3, 4, 5
 OK, ERR_INVAL, ERR_UNSUPPORTED, ERR_UNDECODABLE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = range(7)
@@ -213,6 +213,11 @@ class Code:
     @classmethod
     def mojette_b(cls, n, k, b, q_e):
         return cls(MOJETTE_B, n, k, b, q_e=q_e)
+
+    @classmethod
+    def xcode(cls, p):
+        """The X-code on p (prime) columns: k = p - 2, b = p, e = 2."""
+        return cls(XCODE, p, p - 2, p)
 
     @classmethod
     def from_columns(cls, n, k, b, columns, e):

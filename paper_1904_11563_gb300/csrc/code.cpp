@@ -140,6 +140,22 @@ struct Builder {
     }
   }
 
+  // X-code column i of n = p columns (k = p - 2 rows of data): the k sources
+  // of grid row i as degree-one cells, then the parities along the two
+  // diagonals, data row r of column (i + r + 2) mod p and of (i - r - 2) mod p.
+  void xcode_column(int p, int i) {
+    const int k = p - 2;
+    begin_column(p, 0, 0);
+    for (int r = 0; r < k; ++r) add_cell({i * k + r});
+    std::vector<int32_t> up, down;
+    for (int r = 0; r < k; ++r) {
+      up.push_back(((i + r + 2) % p) * k + r);
+      down.push_back((((i - r - 2) % p + p) % p) * k + r);
+    }
+    add_cell(std::move(up));
+    add_cell(std::move(down));
+  }
+
   void finish() {
     c->col_ptr.push_back(static_cast<int32_t>(cells.size()));
     bpx::finish_code(c, cells, c->col_of_cell);
@@ -237,6 +253,17 @@ extern "C" int bpx_code_build(int variant, int n, int k, int e, int b, int q_e, 
       const int lo = ceil_odd(1 - n);
       for (int i = 0; i < n; ++i) B.projection(k, b, lo + 2 * i, q);
       derived_e = n - need;
+      break;
+    }
+    case BPX_XCODE: {
+      bool prime = n >= 3;
+      for (int d = 2; prime && d * d <= n; ++d) prime = n % d != 0;
+      if (!prime || k != n - 2 || b != n) {
+        delete c;
+        return fail(BPX_ERR_INVAL, "X-code needs n = p prime >= 3, k = p - 2, b = p");
+      }
+      for (int i = 0; i < n; ++i) B.xcode_column(n, i);
+      derived_e = 2;
       break;
     }
     default:
@@ -357,11 +384,10 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision,
   L.p_direct = take(C * i32);
   L.p_front0 = take(C * i32);
   L.p_front1 = take(C * i32);
-  L.p_cand = take(C * i32);
+  L.p_word = take(C * sizeof(unsigned long long));
   L.p_depth = take(S * i32);
   L.p_resolver = take(S * i32);
   L.p_order = take(S * i32);
-  L.p_newsrc = take(S * i32);
   L.p_wave_ptr = take((S + 2) * i32);
   L.p_cursor = take((S + 2) * i32);
   L.p_pl_res = take(S * i32);

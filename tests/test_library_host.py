@@ -225,6 +225,41 @@ def test_code_from_columns_and_search(libbpx):
         bpx.Code.from_columns(2, 1, 1, [[(0,)], [(1,)]], e=1)     # source 1 out of range
 
 
+def test_search_finds_codes_of_degree_four_to_six(libbpx):
+    """Equal-height array BP-XOR codes beyond Tables I / III at sigma >= 4:
+    the multi-chain search finds [n, k, b] = [6, 4, 4] with sigma = 4 and
+    [5, 3, 4] with sigma = 5 and 6 (n - k = 2 erased columns), each verified
+    by the oracle's brute force over every erasure pattern."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    for n, k, b, s, th in [(6, 4, 4, 4, 4), (5, 3, 4, 5, 4), (5, 3, 4, 6, 2)]:
+        code, used = bpx.Code.search(n, k, b, s, iters=1500000, seed=1, threads=th)
+        assert code is not None, (n, k, b, s, used)
+        assert code.sigma == s and code.e == n - k and all(h == b for h in code.heights)
+        ref = o.code_from_columns("found", k, b, code.columns())
+        assert ref.sigma == s and o.is_array_bpxor(ref)
+        assert n <= o.bound_paterson(k, b, s) if s < k else n <= o.bound_k_equals_sigma(k, b)
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 11, 13])
+def test_xcode_graph_matches_oracle(libbpx, p):
+    """The library's X-code (built column by column) has the oracle's cells
+    (built from the data symbols' side), columns and parameters."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    c, ref = bpx.Code.xcode(p), o.xcode(p)
+    assert (c.n, c.k, c.b, c.e, c.sigma, c.num_cells) == (ref.n, ref.k, ref.b, ref.e, ref.sigma, len(ref.cells))
+    assert c.cells == ref.cells
+    assert list(c.col_of_cell) == list(ref.col_of_cell) and list(c.heights) == [p] * p
+
+
+def test_xcode_parameters_rejected(libbpx):
+    bpx = libbpx
+    for n, k, b in [(9, 7, 9), (7, 4, 7), (7, 5, 6), (2, 0, 2)]:
+        with pytest.raises(bpx.BpxError):
+            bpx.Code(bpx.XCODE, n, k, b)
+
+
 def test_code_search_ex_threads_and_flags(libbpx):
     """The multi-chain search: a [7, 2] code with b = 3 (n meets the k = sigma
     bound 2 b + 1) is found and verified by brute force; the result does not
