@@ -43,8 +43,8 @@ struct WsLayout {
   size_t g_hdr, g_col_of_cell, g_cell_ptr, g_cell_src, g_src_ptr, g_src_cell;
   size_t g_t2_ptr, g_t2_a, g_t2_b, g_a2_ptr, g_a2_blk, g_b2_ptr, g_b2_blk, g_t2_order;
   // plan (int32)
-  size_t p_info, p_ctr, p_cnt, p_surv, p_direct, p_front0, p_front1, p_cand;
-  size_t p_depth, p_resolver, p_order, p_newsrc, p_wave_ptr, p_cursor;
+  size_t p_info, p_ctr, p_cnt, p_surv, p_direct, p_front0, p_front1, p_word;
+  size_t p_depth, p_resolver, p_order, p_wave_ptr, p_cursor;
   size_t p_pl_res, p_pl_ptr, p_pl_list;  // peel list: resolver and subtrahends per order entry
   size_t plan_end;
   // products (float, num_cells * h * N)

@@ -33,16 +33,15 @@ struct DevGraph {
 struct DevPlan {
   int32_t* info;      // BPX_INFO_LEN
   int32_t* ctr;       // CTR_LEN counters
-  int32_t* cnt;       // unknown sources per cell (-1: erased column)
+  int32_t* cnt;       // sources per surviving cell (-1: erased column)
   int32_t* surv;      // surviving cells, ascending
   int32_t* direct;    // per cell: the source it resolves at depth 1, or -1
   int32_t* front0;    // frontier scratch
   int32_t* front1;
-  int32_t* cand;      // per frontier entry: its unknown source
+  unsigned long long* word;  // per cell: unknown count << 32 | XOR of unknown ids + 1 (large codes)
   int32_t* depth;     // per source: round of recovery (0 = not recovered)
   int32_t* resolver;  // per source: resolving cell (INT32_MAX = none)
   int32_t* order;     // recovered sources sorted by (depth, source)
-  int32_t* newsrc;    // sources recovered in the current round
   int32_t* wave_ptr;  // order[wave_ptr[d-1] .. wave_ptr[d]) = sources of depth d
   int32_t* cursor;    // placement cursors (scratch)
   // Peel list, one entry per position i of `order`: the resolver of order[i]
@@ -52,6 +51,21 @@ struct DevPlan {
   int32_t* pl_ptr;
   int32_t* pl_list;
 };
+
+// The schedule's per-cell word holds the cell's unknown-source count above
+// the XOR of its unknown sources' ids + 1 (values 1 .. S).  sched_id_bits:
+// the bits of S; a 32-bit word (kept in shared memory) fits when the largest
+// cell degree stays below the remaining 31 - bits (the top bit marks an
+// erased cell), else the plan keeps 64-bit words in global memory.
+inline __host__ __device__ int sched_id_bits(int S) {
+  int b = 0;
+  while (b < 31 && (S >> b) != 0) ++b;
+  return b;
+}
+inline __host__ __device__ bool sched_packable32(int S, int sigma) {
+  const int b = sched_id_bits(S);
+  return b <= 30 && sigma < (1 << (31 - b));
+}
 
 inline DevGraph make_graph(const bpx_code* c, const void* ws, const WsLayout& L) {
   auto base = static_cast<const char*>(ws);
@@ -91,11 +105,10 @@ inline DevPlan make_plan(const void* ws, const WsLayout& L) {
   p.direct = at(L.p_direct);
   p.front0 = at(L.p_front0);
   p.front1 = at(L.p_front1);
-  p.cand = at(L.p_cand);
+  p.word = reinterpret_cast<unsigned long long*>(base + L.p_word);
   p.depth = at(L.p_depth);
   p.resolver = at(L.p_resolver);
   p.order = at(L.p_order);
-  p.newsrc = at(L.p_newsrc);
   p.wave_ptr = at(L.p_wave_ptr);
   p.cursor = at(L.p_cursor);
   p.pl_res = at(L.p_pl_res);
@@ -170,7 +183,12 @@ inline long long encode_group_ctas(long long rows, int K) { return enc_group_sbl
 int peel_chunk_for(long long nv, int ctas_hint);
 
 // Launchers (defined in the .cu files).  All return cudaError_t of the launch.
-cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, cudaStream_t st);
+// max_state_bytes: the largest job's (cells + sources) x 4 bytes;
+// max_want_bytes: the same with room for full ready lists (cells + 3 x
+// sources); packable: every job passes sched_packable32 (else the plans'
+// state stays in global memory).
+cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, size_t max_want_bytes,
+                                  bool packable, cudaStream_t st);
 // d_bases: the jobs' first CTA in the launch, ascending (job order).
 cudaError_t launch_b_split_group(const GJob* d_jobs, const long long* d_bases, int njobs, long long total_ctas,
                                  cudaStream_t st);

@@ -19,8 +19,9 @@ struct bpx_group {
   std::vector<bpx::WsLayout> layouts;
   std::vector<size_t> offsets;
   size_t gjob_off = 0, tc_off = 0, total = 0;
-  size_t max_state_bytes = 0;
+  size_t max_state_bytes = 0, max_want_bytes = 0;
   int max_sigma = 1;
+  bool sched_packable = true;  // every job's schedule state fits 32-bit cell words
   long long bsplit_total = 0, enc_total = 0, peel_total = 0, tiles_total = 0;
   void* ws = nullptr;
   int table_config = -1;  // tile config the device GEMM table was built for
@@ -149,7 +150,7 @@ int run_group(bpx_group* G, const bpx_opts* o, int config, cudaStream_t st) {
   // after it so that the schedule's CTAs are placed first.
   if ((e = cudaEventRecord(G->fork_b, st)) != cudaSuccess) return cuda_fail(e, "grouped B split fork");
   mark(o, BPX_STAGE_SCHEDULE, 0, st);
-  if ((e = bpx::launch_schedule_group(gj, njobs, G->max_state_bytes, st)) != cudaSuccess)
+  if ((e = bpx::launch_schedule_group(gj, njobs, G->max_state_bytes, G->max_want_bytes, G->sched_packable, st)) != cudaSuccess)
     return cuda_fail(e, "grouped schedule");
   mark(o, BPX_STAGE_SCHEDULE, 1, st);
   if ((e = cudaStreamWaitEvent(G->side, G->fork_b, 0)) != cudaSuccess) return cuda_fail(e, "grouped B split fork");
@@ -203,7 +204,10 @@ extern "C" int bpx_group_create(const bpx_job* jobs, int njobs, int precision, b
     off = bpx::align_up(off + L.total, 256);
     G->max_state_bytes =
         std::max(G->max_state_bytes, (static_cast<size_t>(c->num_cells) + c->S) * sizeof(int32_t));
+    G->max_want_bytes =
+        std::max(G->max_want_bytes, (static_cast<size_t>(c->num_cells) + 3 * static_cast<size_t>(c->S)) * sizeof(int32_t));
     G->max_sigma = std::max(G->max_sigma, c->sigma);
+    G->sched_packable = G->sched_packable && bpx::sched_packable32(c->S, c->sigma);
   }
   G->gjob_off = off;
   off = bpx::align_up(off + sizeof(bpx::GJob) * njobs, 256);

@@ -4,12 +4,23 @@
 // parallel rounds).  Resolver = lowest such cell id; depth = the round; the
 // recovered sources are then listed in (depth, source) order.
 //
-// Each round only touches the cells whose unknown count just dropped to one
-// (a warp-parallel ready queue: one warp per ready cell, one warp per newly
-// recovered source), so the cost is linear in the graph edges plus one short
-// barrier sequence per round.  The plan also carries a flat "peel list" (per
+// Each cell keeps one word: its count of unknown sources above the XOR of
+// its unknown sources' ids + 1.  A round walks only the sources recovered in
+// the round before (one warp per source, lanes over its cells): each lane
+// XORs the source out of the cell's word and then decrements the count; the
+// lane that takes a count from two to one reads, in the word its decrement
+// returned, the one source the cell still lacks -- unless a source of the
+// same round is still on its way out, in which case the id found is that
+// source's (already recovered, so no claim) or zero.  Every source recovered
+// in a round already carries its depth when the round's decrements start, so
+// the claim test (depth 0, or depth = next round when another cell got there
+// first) is exact, and the claims for round r + 1 happen inside round r:
+// one barrier per round, two dependent graph loads (the source's cell range
+// and its cells).  The ready lists live in shared memory (overflow in the
+// plan's frontier arrays).  The plan also carries a flat "peel list" (per
 // recovered source: its resolver and the blocks to subtract) for the numeric
 // peel.
+#include <algorithm>
 #include <climits>
 #include <mutex>
 
@@ -19,7 +30,8 @@ namespace bpx {
 namespace {
 
 constexpr int kThreads = 1024;
-constexpr size_t kSmemStateMax = 200 * 1024;  // bytes of per-cell + per-source state kept on chip
+constexpr size_t kSmemMax = 224 * 1024;  // dynamic shared memory of a plan's CTA (state + ready lists)
+constexpr size_t kSmemSmall = 16 * 1024;  // the same for the 256-thread CTA of small codes
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -48,9 +60,20 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
   return before + x - v;
 }
 
-// kSmem: the per-cell unknown counts and per-source depths (the state every
-// round reads and updates) live in shared memory when they fit, else in the
-// plan's global arrays.
+// The per-cell word: 32 bits in shared memory (when the count fits above the
+// id bits), 64 bits in the plan otherwise.
+template <bool kSmem>
+struct CellWord {
+  using T = uint32_t;
+};
+template <>
+struct CellWord<false> {
+  using T = unsigned long long;
+};
+
+// kSmem: the per-cell words and per-source depths (the state every round
+// reads and updates) live in shared memory, followed by the two ready lists
+// (list_cap entries each); otherwise in the plan's global arrays.
 // cell_mask: the mask has one byte per cell (a processor whose output is
 // missing) instead of one per column (a node).
 // part: 0 = the whole plan; 1 = what the products need (surviving cells,
@@ -60,21 +83,44 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* tot
 template <bool kSmem>
 __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& p,
                                               const uint8_t* __restrict__ mask, int32_t* peel_order,
-                                              uint8_t* recovered, int32_t* info_out, bool cell_mask = false,
-                                              int part = 0) {
+                                              uint8_t* recovered, int32_t* info_out, bool cell_mask, int part,
+                                              int list_cap) {
+  using W = typename CellWord<kSmem>::T;
+  constexpr int kTop = static_cast<int>(sizeof(W)) * 8 - 1;  // set only in an erased cell's word
   extern __shared__ int32_t dyn_smem[];
   __shared__ int s_warp[32];
-  __shared__ int s_nf, s_new[2], s_next[2];  // per-round counters, by round parity
+  __shared__ int s_cnt[3];  // ready-list lengths, round r at r % 3
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-  int32_t* cnt = kSmem ? dyn_smem : p.cnt;
+  const int shift = kSmem ? sched_id_bits(g.S) : 32;
+  const W xmask = (W(1) << shift) - 1;
+  const W erased = ~W(0);
+  const W dec = W(0) - (W(1) << shift);
+  W* word = kSmem ? reinterpret_cast<W*>(dyn_smem) : reinterpret_cast<W*>(p.word);
   int32_t* depth = kSmem ? dyn_smem + g.num_cells : p.depth;
+  int32_t* lists = kSmem ? dyn_smem + g.num_cells + g.S : nullptr;
+  if (!kSmem) list_cap = 0;
+  // entry i of ready list q (round r's list is q = r & 1)
+  auto list_at = [&](int q, int i) -> int32_t* {
+    return i < list_cap ? lists + q * list_cap + i : (q ? p.front1 : p.front0) + i;
+  };
+  // cell c, with w its one unknown source, claims w for round r
+  auto claim = [&](int c, int w, int r) {
+    atomicMin(&p.resolver[w], c);
+    if (atomicCAS(&depth[w], 0, r) == 0) *list_at(r & 1, atomicAdd(&s_cnt[r % 3], 1)) = w;
+  };
 
   for (int c = tid; c < g.num_cells; c += nt) {
     const bool alive = (cell_mask ? mask[c] : mask[g.col_of_cell[c]]) == 0;
-    const int v = alive ? (g.cell_ptr[c + 1] - g.cell_ptr[c]) : -1;
-    cnt[c] = v;
-    if (kSmem) p.cnt[c] = v;  // the sign (erased column) is read by the two-dimensional GEMM
+    const int e0 = g.cell_ptr[c], e1 = g.cell_ptr[c + 1];
+    W v = erased;
+    if (alive) {
+      W x = 0;
+      for (int e = e0; e < e1; ++e) x ^= static_cast<W>(g.cell_src[e] + 1);
+      v = (static_cast<W>(e1 - e0) << shift) | x;
+    }
+    word[c] = v;
+    p.cnt[c] = alive ? e1 - e0 : -1;  // the sign (erased column) is read by the two-dimensional GEMM
     if (part != 2) p.direct[c] = -1;
   }
   for (int s = tid; s < g.S; s += nt) {
@@ -82,94 +128,64 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
     p.resolver[s] = INT_MAX;
   }
   if (tid == 0) {
-    s_nf = 0;
-    s_new[0] = s_new[1] = s_next[0] = s_next[1] = 0;
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
     p.wave_ptr[0] = 0;
   }
   __syncthreads();
 
-  // Surviving cells in ascending id, and the first ready queue (degree one).
+  // Surviving cells in ascending id; the degree-one ones claim their source
+  // for round 1.
   int nsurv = 0;
   for (int base = 0; base < g.num_cells; base += nt) {
     const int c = base + tid;
-    const int f = (c < g.num_cells && cnt[c] >= 0) ? 1 : 0;
+    const W v = c < g.num_cells ? word[c] : erased;
+    const int f = (v >> kTop) == 0 ? 1 : 0;
     int total;
     const int ex = block_exclusive_scan(f, s_warp, &total);
     if (f) {
       if (part != 2) p.surv[nsurv + ex] = c;
-      if (cnt[c] == 1) p.front0[atomicAdd(&s_nf, 1)] = c;
+      if ((v >> shift) == 1) claim(c, static_cast<int>(v & xmask) - 1, 1);
     }
     nsurv += total;
   }
   __syncthreads();
 
-  int32_t* fr = p.front0;
-  int32_t* nx = p.front1;
-  int round = 0, nrec = 0;
-  int nf = s_nf;
-  // Two barriers per round.  Counters of round r live at parity r & 1 and the
-  // other parity is cleared during round r, after every thread has read it.
   const int max_rounds = part == 1 ? 1 : INT_MAX;
-  while (nf > 0 && round < max_rounds) {
-    ++round;
-    const int q = round & 1;
-    // A: one warp per ready cell (exactly one unknown source at the start of
-    // the round): the lanes scan its support together for that source -- one
-    // with depth 0, or depth == round if another cell of this round has
-    // already claimed it -- the lowest cell id becomes its resolver, and the
-    // first claim records it as recovered in this round.
-    for (int i = warp; i < nf; i += nwarps) {
-      const int c = fr[i];
-      int found = -1;
-      if (cnt[c] == 1) {
-        const int e0 = g.cell_ptr[c], e1 = g.cell_ptr[c + 1];
-        for (int base = e0; base < e1; base += 32) {
-          const int e = base + lane;
-          const int t = e < e1 ? g.cell_src[e] : -1;
-          int dt = 0;
-          if (t >= 0) dt = depth[t];
-          const unsigned m = __ballot_sync(0xffffffffu, t >= 0 && (dt == 0 || dt == round));
-          if (m) {
-            found = __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
-            break;
-          }
-        }
-      }
-      if (lane == 0 && found >= 0) {
-        atomicMin(&p.resolver[found], c);
-        if (atomicCAS(&depth[found], 0, round) == 0) p.newsrc[atomicAdd(&s_new[q], 1)] = found;
-      }
-    }
-    __syncthreads();
-    const int nnew = s_new[q];
-    if (nnew == 0) {
+  int round = 1, nrec = 0;
+  for (;;) {
+    const int nr = s_cnt[round % 3];
+    if (nr == 0) {
       --round;
       break;
     }
-    nrec += nnew;
+    nrec += nr;
     if (tid == 0) {
       p.wave_ptr[round] = nrec;
-      s_new[q ^ 1] = 0;
-      s_next[q ^ 1] = 0;
+      s_cnt[(round + 2) % 3] = 0;  // round - 1's length: every thread read it before the last barrier
     }
-    // B: one warp per recovered source drops it from its cells; a cell whose
-    // unknown count reaches one joins the next ready queue.
-    for (int j = warp; j < nnew; j += nwarps) {
-      const int s = p.newsrc[j];
+    if (round >= max_rounds) break;
+    const int q = round & 1;
+    for (int j = warp; j < nr; j += nwarps) {
+      const int s = *list_at(q, j);
       const int e1 = g.src_ptr[s + 1];
       for (int e = g.src_ptr[s] + lane; e < e1; e += 32) {
         const int c = g.src_cell[e];
-        if (cnt[c] >= 0) {
-          const int old = atomicSub(&cnt[c], 1);
-          if (old == 2) nx[atomicAdd(&s_next[q], 1)] = c;
+        if ((word[c] >> kTop) == 0) {  // a surviving cell (its top bit never changes)
+          atomicXor(&word[c], static_cast<W>(s + 1));
+          const W old = atomicAdd(&word[c], dec);
+          if ((old >> shift) == 2) {
+            const W x = old & xmask;
+            if (x != 0 && x <= static_cast<W>(g.S)) {
+              const int w = static_cast<int>(x) - 1;
+              const int dw = *reinterpret_cast<volatile int32_t*>(&depth[w]);
+              if (dw == 0 || dw == round + 1) claim(c, w, round + 1);
+            }
+          }
         }
       }
     }
     __syncthreads();
-    nf = s_next[q];
-    int32_t* tmp = fr;
-    fr = nx;
-    nx = tmp;
+    ++round;
   }
 
   if (part == 1) {
@@ -186,8 +202,10 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   }
 
   // Place the recovered sources in (depth, source) order: one warp walks the
-  // sources in ascending id; lanes of equal depth share one cursor bump.
-  for (int d = 1 + tid; d <= round; d += nt) p.cursor[d] = p.wave_ptr[d - 1];
+  // sources in ascending id; lanes of equal depth share one cursor bump.  The
+  // cursors take the ready lists' shared memory when they fit.
+  int32_t* cur = (kSmem && round + 1 <= 2 * list_cap) ? lists : p.cursor;
+  for (int d = 1 + tid; d <= round; d += nt) cur[d] = p.wave_ptr[d - 1];
   __syncthreads();
   if (tid < 32) {
     for (int base = 0; base < g.S; base += 32) {
@@ -198,8 +216,8 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
       const int rank = __popc(peers & ((1u << lane) - 1u));
       int pos = 0;
       if (lane == leader && d > 0) {
-        pos = p.cursor[d];
-        p.cursor[d] = pos + __popc(peers);
+        pos = cur[d];
+        cur[d] = pos + __popc(peers);
       }
       pos = __shfl_sync(0xffffffffu, pos, leader);
       if (d > 0) p.order[pos + rank] = s;
@@ -218,29 +236,29 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
   int lbase = 0;
   for (int base = 0; base < nrec; base += nt) {
     const int i = base + tid;
-    int len = 0, r = 0;
+    int len = 0, r = 0, s = 0, e0 = 0, e1 = 0;
     if (i < nrec) {
-      r = p.resolver[p.order[i]];
-      len = g.cell_ptr[r + 1] - g.cell_ptr[r] - 1;
+      s = p.order[i];
+      r = p.resolver[s];
+      e0 = g.cell_ptr[r];
+      e1 = g.cell_ptr[r + 1];
+      len = e1 - e0 - 1;
     }
     int total;
     const int ex = block_exclusive_scan(len, s_warp, &total);
     if (i < nrec) {
+      int o = lbase + ex;
       p.pl_res[i] = r;
-      p.pl_ptr[i] = lbase + ex;
+      p.pl_ptr[i] = o;
+#pragma unroll 4
+      for (int e = e0; e < e1; ++e) {
+        const int t = g.cell_src[e];
+        if (t != s) p.pl_list[o++] = t;
+      }
     }
     lbase += total;
   }
   if (tid == 0) p.pl_ptr[nrec] = lbase;
-  __syncthreads();
-  for (int i = warp; i < nrec; i += nwarps) {
-    const int s = p.order[i], r = p.pl_res[i], o = p.pl_ptr[i];
-    const int e0 = g.cell_ptr[r], e1 = g.cell_ptr[r + 1];
-    for (int e = e0 + lane; e < e1; e += 32) {
-      const int t = g.cell_src[e];
-      if (t != s) p.pl_list[o + (e - e0) - (t > s ? 1 : 0)] = t;
-    }
-  }
   if (peel_order) {
     for (int i = tid; i < g.S; i += nt) {
       if (i < nrec) {
@@ -284,29 +302,33 @@ __device__ __forceinline__ void schedule_body(const DevGraph& g, const DevPlan& 
 template <bool kSmem>
 __global__ void __launch_bounds__(kThreads, 1)
 schedule_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ mask, int32_t* peel_order,
-                uint8_t* recovered, int32_t* info_out, bool cell_mask, int part) {
-  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
+                uint8_t* recovered, int32_t* info_out, bool cell_mask, int part, int list_cap) {
+  schedule_body<kSmem>(g, p, mask, peel_order, recovered, info_out, cell_mask, part, list_cap);
 }
 
-// Grouped launch: CTA j plans job j.
+// Grouped launch: CTA j plans job j; smem_ints: the launch's dynamic shared
+// memory in int32 words (each job's ready lists take what its state leaves).
 template <bool kSmem>
-__global__ void __launch_bounds__(kThreads, 1) schedule_group_kernel(const GJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(kThreads, 1) schedule_group_kernel(const GJob* __restrict__ jobs, int smem_ints) {
   const GJob& J = jobs[blockIdx.x];
-  schedule_body<kSmem>(J.g, J.p, J.mask, nullptr, nullptr, J.info_out);
+  int cap = 0;
+  if (kSmem) cap = max(0, min(J.g.S, (smem_ints - J.g.num_cells - J.g.S) / 2));
+  schedule_body<kSmem>(J.g, J.p, J.mask, nullptr, nullptr, J.info_out, false, 0, cap);
 }
 
 }  // namespace
 
-cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, cudaStream_t st) {
+cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_state_bytes, size_t max_want_bytes,
+                                  bool packable, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  if (max_state_bytes <= kSmemStateMax) {
+  if (packable && max_state_bytes <= kSmemMax) {
+    const size_t smem = std::min(kSmemMax, std::max(max_state_bytes, max_want_bytes));
     cudaError_t e = cudaFuncSetAttribute(schedule_group_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kSmemStateMax));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemMax));
     if (e != cudaSuccess) return e;
-    schedule_group_kernel<true><<<njobs, kThreads, max_state_bytes, st>>>(d_jobs);
+    schedule_group_kernel<true><<<njobs, kThreads, smem, st>>>(d_jobs, static_cast<int>(smem / 4));
   } else {
-    schedule_group_kernel<false><<<njobs, kThreads, 0, st>>>(d_jobs);
+    schedule_group_kernel<false><<<njobs, kThreads, 0, st>>>(d_jobs, 0);
   }
   return cudaGetLastError();
 }
@@ -314,18 +336,23 @@ cudaError_t launch_schedule_group(const GJob* d_jobs, int njobs, size_t max_stat
 cudaError_t launch_schedule(const DevGraph& g, const DevPlan& p, const uint8_t* mask,
                             int32_t* peel_order, uint8_t* recovered, int32_t* info_out,
                             cudaStream_t st, bool cell_mask, int part) {
-  const size_t smem = (static_cast<size_t>(g.num_cells) + g.S) * sizeof(int32_t);
-  // Small codes take a 256-thread block: it fits beside a resident GEMM CTA
-  // (registers), so the schedule of one multiplication can run while the
-  // GEMM of another still holds every SM.
-  const int threads = g.num_cells + g.S <= 4096 ? 256 : kThreads;
-  if (smem <= kSmemStateMax) {
+  const long long state = static_cast<long long>(g.num_cells) + g.S;  // int32 words
+  // Small codes take a 256-thread block with at most 16 KB of shared memory:
+  // it fits beside a resident GEMM CTA, so the schedule of one
+  // multiplication can run while the GEMM of another still holds every SM.
+  const bool small = state <= 4096;
+  const int threads = small ? 256 : kThreads;
+  const long long room = static_cast<long long>((small ? kSmemSmall : kSmemMax) / 4);
+  if (sched_packable32(g.S, g.sigma) && state <= room) {
+    const int cap = static_cast<int>(std::min<long long>(g.S, (room - state) / 2));
+    const size_t smem = static_cast<size_t>(state + 2LL * cap) * sizeof(int32_t);
     cudaError_t e = cudaFuncSetAttribute(schedule_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kSmemStateMax));
+                                         static_cast<int>(kSmemMax));
     if (e != cudaSuccess) return e;
-    schedule_kernel<true><<<1, threads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
+    schedule_kernel<true><<<1, threads, smem, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part,
+                                                    cap);
   } else {
-    schedule_kernel<false><<<1, threads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part);
+    schedule_kernel<false><<<1, threads, 0, st>>>(g, p, mask, peel_order, recovered, info_out, cell_mask, part, 0);
   }
   return cudaGetLastError();
 }

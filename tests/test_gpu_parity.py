@@ -37,6 +37,9 @@ def _pair(bpx, name):
     if name.startswith("B"):
         n, k, b, q = (int(x) for x in name[1:].split("_"))
         return bpx.Code.mojette_b(n, k, b, q), o.construction_b(n, k, b, q)
+    if name.startswith("xcode"):
+        p = int(name[5:])
+        return bpx.Code.xcode(p), o.xcode(p)
     raise ValueError(name)
 
 
@@ -86,7 +89,7 @@ def _rel_block_err(C, R, h, S):
 
 # ---------------------------------------------------------------- a1: schedule
 
-SCHED_CODES = ["table1", "table3", "sys8_3_8", "sys6_5_5", "A7_4_10", "A11_8_12", "B6_8_4_2"]
+SCHED_CODES = ["table1", "table3", "sys8_3_8", "sys6_5_5", "A7_4_10", "A11_8_12", "B6_8_4_2", "xcode7", "xcode13"]
 
 
 @pytest.mark.parametrize("name", SCHED_CODES)
@@ -128,6 +131,30 @@ def test_schedule_large_construction_a(libbpx):
         assert sch.ok
         assert np.array_equal(got, np.array(sch.order, dtype=np.int32))
         assert info.cpu().numpy()[bpx.INFO_WAVES] == sch.num_waves
+
+
+def test_schedule_state_in_global_memory(libbpx):
+    """A projection code too large for the plan's on-chip state (Construction
+    A n = 16, k = 12, b = 2800: 33600 sources and ~45k cells, whose per-cell
+    words and depths exceed the CTA's shared memory) plans with 64-bit cell
+    words in global memory: bit-exact against the oracle, decodable and
+    undecodable masks."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "A16_12_2800")
+    assert (code.num_cells + code.num_sources) * 4 > 224 * 1024
+    ws = bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32)
+    for t, e in [(0, 4), (1, 4), (2, 5)]:
+        m = W.erasure_mask(code.n, e, 4100 + t)
+        order, rec, info = bpx.schedule(code, torch.from_numpy(m).cuda(), ws)
+        sch = o.wave_schedule(ref, o.surviving_cells(ref, np.nonzero(m)[0]))
+        exp = np.full((code.num_sources, 3), -1, dtype=np.int32)
+        for i, (s_, r, d) in enumerate(sch.order):
+            exp[i] = (s_, r, d)
+        assert np.array_equal(order.cpu().numpy(), exp)
+        assert list(rec.cpu().numpy()) == sch.recovered
+        inf = info.cpu().numpy()
+        assert inf[bpx.INFO_STATUS] == (bpx.OK if sch.ok else bpx.ERR_UNDECODABLE) and sch.ok == (e <= 4)
+        assert inf[bpx.INFO_WAVES] == sch.num_waves
 
 
 # ---------------------------------------------------------------- a2: encode
@@ -813,6 +840,38 @@ def test_searched_code_on_the_gpu(libbpx, prec):
     M = ref.num_sources * h
     A, B = W.inputs(M, K, N, "normal", 91)
     for m in _masks(ref, 2):
+        er = list(np.nonzero(m)[0])
+        C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        if prec == "exact":
+            R, _Q, _s = o.exact_slice_coded_matmul(ref, A, B, h, er)
+            assert np.array_equal(C[:M].view(np.uint32), R[:M].view(np.uint32))
+        else:
+            R, _s = _oracle_decode(ref, A, B, h, m)
+            _check_blocks(C, R, ref, A, B, h, m, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3", "exact"])
+@pytest.mark.parametrize("which", ["xcode7", "search_6_4_4_4"])
+def test_codes_of_degree_four_and_more_on_the_gpu(libbpx, prec, which):
+    """Equal-height array BP-XOR codes with sigma >= 4 beyond Tables I / III --
+    the X-code on 7 columns (sigma = 5, 35 sources) and the [6, 4, 4] code
+    the search finds at sigma = 4 -- through the whole GPU path under every
+    pattern of two erased columns: within tolerance of the oracle per block
+    (bit-exact for exact slices)."""
+    bpx = libbpx
+    if which == "xcode7":
+        code, ref = bpx.Code.xcode(7), o.xcode(7)
+    else:
+        code, _ = bpx.Code.search(6, 4, 4, 4, iters=1500000, seed=1, threads=4)
+        assert code is not None and code.sigma == 4
+        ref = o.code_from_columns("found", 4, 4, code.columns())
+    h, K, N = 8, 136, 68
+    M = ref.num_sources * h - 3
+    A, B = W.inputs(M, K, N, "normal", 93)
+    for m in _masks(ref, 2):
+        if m.sum() != 2:
+            continue
         er = list(np.nonzero(m)[0])
         C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
         assert info[bpx.INFO_STATUS] == bpx.OK
