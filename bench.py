@@ -38,6 +38,8 @@ CODE_TEXT = {
                       "in the two-dimensional scheme (source (z, l) = A_z B_l, 1024 x 1024 blocks)",
     "sysmoj_8192_straggler": "systematic Mojette array n=11 (k=8 data columns, 8x8 grid, e=3 parities q=1, "
                              "slopes 0,+1,-1); processor-level stragglers, task times sigma_c X_c, X_c ~ Exp(1)",
+    "mojA_16384_straggler": "Mojette Construction A n=32 (k=24 x b=683 grid, q=1, p=-15..16); processor-level "
+                            "stragglers, task times sigma_c X_c, X_c ~ Exp(1)",
     "mojA_bsweep": "Mojette Construction A n=32 (k=24 x b grid, q=1, p=-15..16), e=8, b in {16, 32, 64, 683}",
     "batch512": "512 jobs: half array codes (Table I, Table III, systematic Mojette n=6..32, e=2..3), "
                 "half Construction A (n=6..32, e=n//4); each job its own seeded mask",
@@ -1064,7 +1066,7 @@ def run_straggler(args, wl):
     code = _lib_code(bpx, wl)
     M, N, K, h = wl["M"], wl["N"], wl["K"], wl["h"]
     A, Bm = W.device_inputs(M, K, N, wl["dist"], wl["seed"], device=str(dev))
-    prec = args.precision if args.precision in ("bf16", "bf16x3", "fp32", "exact") else "bf16x3"
+    prec = args.precision if args.precision in ("bf16", "bf16x3", "fp16x3", "fp32", "exact") else "bf16x3"
     P = bpx.PRECISIONS[prec]
     ws = bpx.Workspace(code, M, N, K, h, P, device=dev)
     C = bpx.alloc_C(code, h, N, dev)
@@ -1077,7 +1079,7 @@ def run_straggler(args, wl):
         order, first, t_par, _rec = st.arrivals(code, T)
         mask = np.ones(code.num_cells, dtype=np.uint8)
         mask[order[:first]] = 0
-        plans.append(dict(mask=torch.from_numpy(mask).to(dev), first=first, t_par=t_par))
+        plans.append(dict(mask=torch.from_numpy(mask).to(dev), first=first, t_par=t_par, order=order))
     col_of = np.repeat(np.arange(code.n), np.diff(code.col_ptr))
     o_ = bpx.default_opts(mask_cells=1)
     for i in range(warm):
@@ -1113,7 +1115,7 @@ def run_straggler(args, wl):
         S_ex = bpx.exact_params(code, K)["S"]
         mult = S_ex * (S_ex + 1) // 2     # digit pairs (i, l) with i + l < S
     else:
-        mult = {"bf16x3": 3, "bf16": 1, "fp32": 1}[prec]
+        mult = {"bf16x3": 3, "fp16x3": 3, "bf16": 1, "fp32": 1}[prec]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     ach = 2.0 * float(np.mean(rows)) * N * K * mult / (stage["gemm"] * 1e-3) / 1e12
@@ -1128,13 +1130,38 @@ def run_straggler(args, wl):
         roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": None, "kernel": "coded FP32 SIMT GEMM", "work_per_launch": "2 x coded rows x N x K"}
     H = sum(1.0 / j for j in range(1, code.num_cells + 1))
+    # How much of the peel could have overlapped the products (outside the
+    # timed region, on the first timed steps): the decodable set's arrivals in
+    # eight runs; per run, the peel positions the plan could run once it is
+    # in, and the sources an arrival-ordered peel would recover with it.
+    nch = 8
+    ws_s = bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32, device=dev)
+    ready, online = np.zeros(nch), np.zeros(nch)
+    sample = timed[:min(3, len(timed))]
+    for p_ in sample:
+        po, _r, _i = bpx.schedule(code, p_["mask"], ws_s, cells=True)
+        ready += st.overlap_bound(code, p_["order"], p_["first"], po.cpu().numpy(), nch)
+        online += st.online_recovery(code, p_["order"], p_["first"], ws_s, nch, device=dev)
+    ready, online = ready / len(sample), online / len(sample)
+    before = float(ready[:-1].sum() / max(1.0, ready.sum()))
+    overlap = {"chunks": nch, "steps_sampled": len(sample),
+               "peel_positions_ready_by_chunk": [round(float(x), 1) for x in ready],
+               "peel_positions_ready_before_last_chunk": before,
+               "online_sources_recovered_by_chunk": [round(float(x), 1) for x in online],
+               "online_recovered_before_last_chunk": float(online[:-1].sum() / max(1.0, online.sum())),
+               "peel_ms": stage.get("peel", 0.0),
+               "peel_ms_overlappable_bound": stage.get("peel", 0.0) * before,
+               "note": "peel positions (non-direct) by the arrival run after which the plan could run them "
+                       "(their resolver's product and every block they subtract are in); the GPU runs all "
+                       "arrived products in one launch and the peel after them"}
     line = {"metric": METRIC, "value": useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
             "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": wl["name"], "code": CODE_TEXT[wl["name"]], "M": M, "N": N, "K": K, "h": h,
                        "mu": wl["mu"], "task_time_seeds": "%d + step" % wl["mask_seed_base"],
-                       "inputs": "A, B iid N(0,1) FP32, seeded", "l2": "inputs larger than L2"},
-            "stages_ms": stage,
+                       "inputs": "A, B iid %s FP32, seeded" % {"normal": "N(0,1)", "uniform": "U(-1,1)"}.get(
+                           wl["dist"], wl["dist"]), "l2": "inputs larger than L2"},
+            "stages_ms": stage, "overlap": overlap,
             "model": {"t_par_mean": float(np.mean([p_["t_par"] for p_ in timed])),
                       "arrivals_to_decode_mean": float(np.mean([p_["first"] for p_ in timed])),
                       "cells": code.num_cells,
@@ -1142,7 +1169,7 @@ def run_straggler(args, wl):
                       "units": "1 / mu; T_c = sigma_c X_c"},
             "computed_cells_mean": float(np.mean(rows)) / h,
             "roofline": roof, "clocks": ck,
-            "gpu_launches": {"bf16x3": 5, "bf16": 5, "fp32": 4, "exact": 7}[prec] * steps}
+            "gpu_launches": {"bf16x3": 5, "bf16": 5, "fp16x3": 7, "fp32": 4, "exact": 7}[prec] * steps}
     print(json.dumps(line), flush=True)
 
 

@@ -550,7 +550,8 @@ void bpx_group_free(bpx_group* group);
  *     (cudaDeviceReset, or anything else that replaces the device's primary
  *     context) do not call this entry point again in that process.
  *   - Codes whose scratch exceeds 8 MiB are rejected with BPX_ERR_INVAL
- *     (roughly 3 num_edges + 8 num_cells + 9 num_sources int32 words).
+ *     (roughly 3 num_edges + 9 num_cells + 8 num_sources int32 words, plus
+ *     the code's two-dimensional term lists).
  *   - Every call uploads its code's graph into the shared array and reuses
  *     it, so calls that overlap on the GPU (other streams, other threads)
  *     race on it: serialise them.  The plan stays in the array until the next

@@ -59,3 +59,51 @@ def emulate(code: "bpx.Code", A, B, h: int, precision: int, X, scale_by_degree: 
     dmask = torch.from_numpy(mask).to(A.device)
     C, info = bpx.coded_matmul(code, A, B, h, precision, dmask, ws, C=C, opts=o)
     return dict(T=T, order=order, first=first, t_par=t_par, recovered_after=rec, cell_mask=mask, C=C, info=info)
+
+
+def overlap_bound(code: "bpx.Code", order, first: int, peel_order, nchunks: int = 8):
+    """How much of the peel could run while products still arrive.
+
+    The first ``first`` cells of the arrival ``order`` (the decodable set)
+    are cut into ``nchunks`` equal runs of arrivals.  A non-direct position
+    of the peel plan (``peel_order``: rows (source, resolver, depth) in
+    (depth, source) order, as ``bpx.schedule`` returns them) can be peeled
+    once its resolver's product and every block it subtracts are there: its
+    ready run is the latest of its resolver's run and the ready runs of the
+    sources it subtracts (a direct source is ready with its resolver).
+    Returns the count of non-direct positions per ready run: everything
+    before the last run could overlap the products, the rest cannot."""
+    order = np.asarray(order)
+    po = np.asarray(peel_order)
+    chunk = np.full(code.num_cells, -1, dtype=np.int64)
+    if first > 0:
+        chunk[order[:first]] = np.arange(first, dtype=np.int64) * nchunks // first
+    ready = np.full(code.num_sources, -1, dtype=np.int64)
+    counts = np.zeros(nchunks, dtype=np.int64)
+    ptr, src = code.cell_ptr, code.cell_src
+    for s, r, d in po:
+        if s < 0:
+            break
+        rc = int(chunk[r])
+        for t in src[ptr[r]:ptr[r + 1]]:
+            if t != s:
+                rc = max(rc, int(ready[t]))
+        ready[s] = rc
+        if d > 1:
+            counts[rc] += 1
+    return counts
+
+
+def online_recovery(code: "bpx.Code", order, first: int, ws, nchunks: int = 8, device=None):
+    """Sources the peel recovers from the arrivals so far, after each of the
+    ``nchunks`` runs of the decodable set (the GPU schedule over each prefix:
+    resolvers taken among the cells that have arrived)."""
+    import torch
+    out = []
+    for j in range(nchunks):
+        n_j = (j + 1) * first // nchunks
+        mask = np.ones(code.num_cells, dtype=np.uint8)
+        mask[np.asarray(order)[:n_j]] = 0
+        _o, _r, info = bpx.schedule(code, torch.from_numpy(mask).to(device), ws, cells=True)
+        out.append(int(info[bpx.INFO_RECOVERED].item()))
+    return np.diff(np.asarray([0] + out, dtype=np.int64))

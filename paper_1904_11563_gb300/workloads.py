@@ -17,6 +17,9 @@ Named workloads (the paper has no dataset; every input is synthetic):
   576 x 256) with magnitudes log-uniform on [1e-3, 1e3] and random signs.
 * ``mojA_16384``: Construction A n = 32, k = 24, b = 683 (16392 one-row
   sources), A 16384 x 16384, B 16384 x 8192, U(-1,1); 8 erased columns.
+* ``sysmoj_8192_straggler`` / ``mojA_16384_straggler``: the same shapes with
+  processor-level stragglers: cell task times sigma_c X_c, X_c ~ Exp(1) per
+  step, decoded from the first decodable set of arrivals.
 """
 from __future__ import annotations
 
@@ -42,6 +45,11 @@ WORKLOADS = {
     "sysmoj_8192_straggler": dict(code=("systematic", 8, 3, 8), h=128, M=8192, K=8192, N=8192,
                                   dist="normal", seed=2, e=0, trials=100, mask_seed_base=5000, mu=1.0,
                                   straggler=True),
+    # Construction A (n = 32, k = 24, b = 683) with processor-level stragglers:
+    # the same task-time model over its ~27.7k cells (seed 6000 + step)
+    "mojA_16384_straggler": dict(code=("mojette_a", 32, 24, 683), h=1, M=16384, K=16384, N=8192,
+                                 dist="uniform", seed=4, e=0, trials=100, mask_seed_base=6000, mu=1.0,
+                                 straggler=True),
     # the benchmark code in the paper's two-dimensional scheme: 8 x 8 output
     # blocks of 1024 x 1024 (A in 8 row blocks, B in 8 column blocks)
     "sysmoj_8192_2d": dict(code=("systematic", 8, 3, 8), h=1024, M=8192, K=8192, N=8192,

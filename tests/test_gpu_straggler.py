@@ -116,3 +116,22 @@ def test_host_entry_with_cell_mask(libbpx):
             want = R[s * h:(s + 1) * h]
             err = np.linalg.norm(hC.numpy()[s * h:(s + 1) * h] - want) / np.linalg.norm(want)
             assert err <= 1e-5 * max(1.0, nu.get(s, 1.0)), (s, err, nu.get(s, 1.0))
+
+
+def test_online_recovery_matches_oracle(libbpx):
+    """Sources recovered from each run of the decodable set's arrivals (the
+    GPU schedule over each prefix of the arrival order) equal the oracle's
+    wave schedule over the same prefixes, and sum to every source."""
+    bpx = libbpx
+    from paper_1904_11563_gb300 import straggler as st
+    code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
+    ws = bpx.Workspace(code, 0, 0, 0, 1, bpx.FP32)
+    for seed in (6001, 6003):
+        T = st.task_times(code, W.exponential_draws(code.num_cells, 1.0, seed))
+        order, first, _t, _rec = st.arrivals(code, T)
+        got = st.online_recovery(code, order, first, ws, 8, device=torch.device("cuda"))
+        want = []
+        for j in range(8):
+            n_j = (j + 1) * first // 8
+            want.append(sum(o.wave_schedule(ref, sorted(int(c) for c in order[:n_j])).recovered))
+        assert list(got) == list(np.diff([0] + want)) and int(got.sum()) == ref.num_sources

@@ -189,6 +189,59 @@ def test_straggler_arrivals_match_brute_force(libbpx):
             assert t_par == o.parallel_task_time_brute(ref, Tref)
 
 
+def test_overlap_bound_counts_and_the_peeling_cliff(libbpx):
+    """The emulator's overlap bound -- per run of the decodable set's
+    arrivals, the peel positions whose resolver and subtracted blocks have
+    all arrived -- matches a count by closure (a position is ready after run
+    j when every resolver in its dependency tree arrived by then), on the
+    oracle's plan for Construction A [12, 9, 120] under the task-time model.
+    And it shows why products and peel barely overlap on such codes: most
+    non-direct positions need the last eighth of the arrivals, and even an
+    arrival-ordered peel (resolvers among the cells in so far) recovers most
+    sources only then (the peeling avalanche at the decodability threshold)."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    from paper_1904_11563_gb300 import straggler as st
+    from paper_1904_11563_gb300 import workloads as W
+    code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
+    nch = 8
+    for seed in (6001, 6002):
+        T = st.task_times(code, W.exponential_draws(code.num_cells, 1.0, seed))
+        order, first, _t, _rec = st.arrivals(code, T)
+        arrived = sorted(int(c) for c in order[:first])
+        sch = o.wave_schedule(ref, arrived)
+        assert sch.ok
+        po = np.full((ref.num_sources, 3), -1, dtype=np.int32)
+        for i, row in enumerate(sch.order):
+            po[i] = row
+        got = st.overlap_bound(code, order, first, po, nch)
+        run = {int(c): i * nch // first for i, c in enumerate(order[:first])}
+        res = {s_: r for s_, r, _d in sch.order}
+
+        def tree(s_, seen):  # every source the block of s_ depends on
+            if s_ in seen:
+                return
+            seen.add(s_)
+            for t in ref.cells[res[s_]]:
+                if t != s_:
+                    tree(t, seen)
+
+        want = np.zeros(nch, dtype=np.int64)
+        for s_, _r, d in sch.order:
+            if d > 1:
+                seen = set()
+                tree(s_, seen)
+                want[max(run[res[t]] for t in seen)] += 1
+        assert np.array_equal(got, want), (got, want)
+        assert got[-1] >= 0.8 * got.sum()
+        online = []
+        for j in range(nch):
+            n_j = (j + 1) * first // nch
+            online.append(sum(o.wave_schedule(ref, sorted(int(c) for c in order[:n_j])).recovered))
+        gain = np.diff([0] + online)
+        assert gain[-1] >= 0.5 * ref.num_sources
+
+
 def test_bounds_match_oracle(libbpx):
     """The library's bounds on n equal the oracle's, and Tables I / III meet
     them with equality."""
