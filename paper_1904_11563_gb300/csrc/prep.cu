@@ -229,6 +229,9 @@ encode_group_kernel(const GJob* __restrict__ jobs, const long long* __restrict__
 // registers between the two steps: 256 threads hold rows of K <= 8192, 512
 // threads K <= 16384; longer rows sum their later chunks a second time.
 constexpr int kF16Keep = 4;
+// Codes with at least this many sources per cell on average take the
+// K-chunked form (below).
+constexpr int kF16ChunkedDegree = 4;
 
 __device__ __forceinline__ void coded_chunk(const DevGraph& g, const float* __restrict__ A, int M, int K, int h,
                                             int e0, int e1, int j, int k8, float (&acc)[8]) {
@@ -332,6 +335,75 @@ encode_f16_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int
     coded_chunk(g, A, M, K, h, e0, e1, j, 8 * c, v);
     f16_split8(v, e, out_hi + base + 8 * c, out_lo + base + 8 * c);
   }
+}
+
+// High-degree codes (sources in many cells) take a K-chunked form instead, in
+// the encode grid (coded rows fastest, so that CTAs resident together read
+// the same K-chunk of A and a source chunk read for one cell is still in L2
+// for the next cells that contain it).  One CTA per coded row reads every
+// source row of a cell from DRAM again for each later cell that contains
+// it.  Three steps:
+//   1. each thread's 8 coded sums, stored unscaled as their FP32 bit patterns
+//      (upper halves in the hi buffer, lower halves in the lo buffer); their
+//      largest magnitude, reduced over the row's lanes of a warp, folded into
+//      the row's word by atomicMax on the float bits (non-negative floats
+//      order like their bits);
+//   2. per row, the word becomes the exponent e (f16_scale_exp);
+//   3. per 8 elements, the sums read back, scaled by 2^e and split into fp16
+//      hi / lo in place: the same bits as the one-CTA-per-row form.
+__global__ void __launch_bounds__(kEncThreads)
+encode_f16_sum_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M, int K, int h, uint16_t* out_hi,
+                      uint16_t* out_lo, uint32_t* row_max) {
+  const int tpr = enc_threads_per_row(K);
+  const int row = blockIdx.x * (kEncThreads / tpr) + threadIdx.x / tpr;
+  const bool live = row < p.ctr[CTR_NSURV] * h;
+  const int k8 = (blockIdx.y * tpr + threadIdx.x % tpr) * kEncVec;
+  float m = 0.f;
+  if (live && k8 < K) {
+    const int ci = row / h, j = row - ci * h;
+    const int cell = p.surv[ci];
+    float v[8];
+    coded_chunk(g, A, M, K, h, g.cell_ptr[cell], g.cell_ptr[cell + 1], j, k8, v);
+    uint32_t hv[4], lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t b0 = __float_as_uint(v[2 * q]), b1 = __float_as_uint(v[2 * q + 1]);
+      hv[q] = (b0 >> 16) | (b1 & 0xffff0000u);
+      lv[q] = (b0 & 0xffffu) | (b1 << 16);
+      m = fmaxf(m, fmaxf(fabsf(v[2 * q]), fabsf(v[2 * q + 1])));
+    }
+    const long long o = static_cast<long long>(row) * K + k8;
+    *reinterpret_cast<uint4*>(out_hi + o) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<uint4*>(out_lo + o) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+  }
+  const int span = tpr < 32 ? tpr : 32;  // a row's lanes: an aligned power-of-two group
+  for (int o = 1; o < span; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (live && threadIdx.x % span == 0 && m > 0.f) atomicMax(row_max + row, __float_as_uint(m));
+}
+
+__global__ void __launch_bounds__(256) encode_f16_exp_kernel(DevPlan p, int h, int32_t* a_exp) {
+  const long long row = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x;
+  if (row < static_cast<long long>(p.ctr[CTR_NSURV]) * h)
+    a_exp[row] = f16_scale_exp(__uint_as_float(static_cast<uint32_t>(a_exp[row])));
+}
+
+__global__ void __launch_bounds__(256)
+encode_f16_rescale_kernel(DevPlan p, int K, int h, __half* out_hi, __half* out_lo, const int32_t* __restrict__ a_exp) {
+  const long long c = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x;  // 8-element chunk
+  const int per_row = K / 8;
+  const long long row = c / per_row;
+  if (row >= static_cast<long long>(p.ctr[CTR_NSURV]) * h) return;
+  const long long o = c * 8;
+  const uint4 hv = *reinterpret_cast<const uint4*>(out_hi + o);
+  const uint4 lv = *reinterpret_cast<const uint4*>(out_lo + o);
+  const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+  float v[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[2 * q] = __uint_as_float((hw[q] << 16) | (lw[q] & 0xffffu));
+    v[2 * q + 1] = __uint_as_float((hw[q] & 0xffff0000u) | (lw[q] >> 16));
+  }
+  f16_split8(v, a_exp[row], out_hi + o, out_lo + o);
 }
 
 // max |B| per column: a CTA takes 256 columns (64 float4) x a range of
@@ -596,6 +668,22 @@ cudaError_t launch_encode_f16(const DevGraph& g, const DevPlan& p, const float* 
   const long long rows = static_cast<long long>(g.num_cells) * h;
   if (rows == 0 || K == 0) return cudaSuccess;
   if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (static_cast<long long>(g.num_edges) >= kF16ChunkedDegree * static_cast<long long>(g.num_cells)) {
+    // high mean degree: the K-chunked form
+    cudaError_t e = cudaMemsetAsync(a_exp, 0, sizeof(int32_t) * static_cast<size_t>(rows), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(static_cast<unsigned>(enc_row_blocks(rows, K)), static_cast<unsigned>(enc_k_chunks(K)));
+    encode_f16_sum_kernel<<<grid, kEncThreads, 0, st>>>(g, p, A, M, K, h, static_cast<uint16_t*>(a_hi),
+                                                         static_cast<uint16_t*>(a_lo), reinterpret_cast<uint32_t*>(a_exp));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    encode_f16_exp_kernel<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, st>>>(p, h, a_exp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long chunks = rows * (K / 8);
+    if ((chunks + 255) / 256 > 0x7fffffffLL) return cudaErrorInvalidValue;
+    encode_f16_rescale_kernel<<<static_cast<unsigned>((chunks + 255) / 256), 256, 0, st>>>(
+        p, K, h, static_cast<__half*>(a_hi), static_cast<__half*>(a_lo), a_exp);
+    return cudaGetLastError();
+  }
   if (K <= 256 * 8 * kF16Keep)
     encode_f16_kernel<256><<<static_cast<unsigned>(rows), 256, 0, st>>>(
         g, p, A, M, K, h, static_cast<__half*>(a_hi), static_cast<__half*>(a_lo), a_exp);

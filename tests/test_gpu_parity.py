@@ -536,6 +536,32 @@ def test_fp16x3_wide_dynamic_range(libbpx, name, h, M, K, N):
             _check_blocks(C, R, ref, A, B, h, m, "fp16x3")
 
 
+@pytest.mark.parametrize("h,K,N", [(2, 264, 68), (1, 2056, 36)])
+def test_fp16x3_high_degree_code(libbpx, h, K, N):
+    """A code whose cells hold 7.5 sources on average (Construction A
+    [12, 9, 120]) takes the K-chunked split-FP16x3 encode -- unscaled sums
+    staged, each row's exponent from a max over all its k-chunks, then the
+    rescale in place -- with one ragged k-chunk (K = 264) and with three
+    (K = 2056): small-integer inputs decode to A B bit for bit, normal inputs
+    within 1e-5 times the propagation factor of the oracle."""
+    bpx = libbpx
+    code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
+    assert len(code.cell_src) >= 4 * code.num_cells
+    M = ref.num_sources * h - 1
+    Ai, Bi = W.matrix((M, K), "int", 41), W.matrix((K, N), "int", 42)
+    An, Bn = W.inputs(M, K, N, "normal", 43)
+    exact = o.reference_product(Ai, Bi)
+    for t in range(2):
+        m = W.erasure_mask(12, 3, 70 + t)
+        C, info = _run(bpx, code, Ai, Bi, h, bpx.FP16X3, m)
+        assert info[bpx.INFO_STATUS] == bpx.OK
+        assert np.array_equal(C[:M], exact), t
+        C, info = _run(bpx, code, An, Bn, h, bpx.FP16X3, m)
+        R, sch = _oracle_decode(ref, An, Bn, h, m)
+        assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
+        _check_blocks(C, R, ref, An, Bn, h, m, "fp16x3")
+
+
 def test_fp16x3_zero_rows_columns_and_tiny_scales(libbpx):
     """Split-FP16x3's scale edge cases: a source block and a column of B that
     are all zero (exponent 0, products exactly zero), a row position scaled
