@@ -536,14 +536,15 @@ def test_fp16x3_wide_dynamic_range(libbpx, name, h, M, K, N):
             _check_blocks(C, R, ref, A, B, h, m, "fp16x3")
 
 
-@pytest.mark.parametrize("h,K,N", [(2, 264, 68), (1, 2056, 36)])
+@pytest.mark.parametrize("h,K,N", [(2, 264, 68), (1, 2056, 36), (3, 8, 4)])
 def test_fp16x3_high_degree_code(libbpx, h, K, N):
     """A code whose cells hold 7.5 sources on average (Construction A
     [12, 9, 120]) takes the K-chunked split-FP16x3 encode -- unscaled sums
     staged, each row's exponent from a max over all its k-chunks, then the
-    rescale in place -- with one ragged k-chunk (K = 264) and with three
-    (K = 2056): small-integer inputs decode to A B bit for bit, normal inputs
-    within 1e-5 times the propagation factor of the oracle."""
+    rescale in place -- with one ragged k-chunk (K = 264), with three
+    (K = 2056), and with one 8-wide chunk per row (K = 8, 128 rows a CTA):
+    small-integer inputs decode to A B bit for bit, normal inputs within 1e-5
+    times the propagation factor of the oracle."""
     bpx = libbpx
     code, ref = bpx.Code.mojette_a(12, 9, 120), o.construction_a(12, 9, 120)
     assert len(code.cell_src) >= 4 * code.num_cells
