@@ -879,24 +879,30 @@ def test_searched_code_on_the_gpu(libbpx, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3", "exact"])
-@pytest.mark.parametrize("which", ["xcode7", "search_6_4_4_4"])
+@pytest.mark.parametrize("which", ["xcode7", "xcode13", "search_6_4_4_4", "search_5_3_4_6"])
 def test_codes_of_degree_four_and_more_on_the_gpu(libbpx, prec, which):
     """Equal-height array BP-XOR codes with sigma >= 4 beyond Tables I / III --
-    the X-code on 7 columns (sigma = 5, 35 sources) and the [6, 4, 4] code
-    the search finds at sigma = 4 -- through the whole GPU path under every
-    pattern of two erased columns: within tolerance of the oracle per block
-    (bit-exact for exact slices)."""
+    the X-code on 7 columns (sigma = 5, 35 sources) and on 13 (sigma = 11,
+    143 sources), and the [6, 4, 4] and [5, 3, 4] codes the search finds at
+    sigma = 4 and 6 -- through the whole GPU path under every pattern of two
+    erased columns (a spread of 23 of the 78 for the 13-column X-code): within
+    tolerance of the oracle per block (bit-exact for exact slices)."""
     bpx = libbpx
-    if which == "xcode7":
-        code, ref = bpx.Code.xcode(7), o.xcode(7)
+    if which.startswith("xcode"):
+        p = int(which[5:])
+        code, ref = bpx.Code.xcode(p), o.xcode(p)
     else:
-        code, _ = bpx.Code.search(6, 4, 4, 4, iters=1500000, seed=1, threads=4)
-        assert code is not None and code.sigma == 4
-        ref = o.code_from_columns("found", 4, 4, code.columns())
-    h, K, N = 8, 136, 68
+        n, k, b, sg = (int(x) for x in which.split("_")[1:])
+        code, _ = bpx.Code.search(n, k, b, sg, iters=1500000, seed=1, threads=4 if sg == 4 else 2)
+        assert code is not None and code.sigma == sg
+        ref = o.code_from_columns("found", k, b, code.columns())
+    h, K, N = (8, 136, 68) if ref.num_sources < 100 else (2, 72, 36)
     M = ref.num_sources * h - 3
     A, B = W.inputs(M, K, N, "normal", 93)
-    for m in _masks(ref, 2):
+    pairs = [m for m in _masks(ref, 2) if m.sum() == 2]
+    if len(pairs) > 24:  # the 13-column X-code: the first 12 pairs, then every sixth
+        pairs = pairs[:12] + pairs[12::6]
+    for m in pairs:
         if m.sum() != 2:
             continue
         er = list(np.nonzero(m)[0])
