@@ -42,8 +42,20 @@ __device__ __forceinline__ int exponent_of(uint32_t amax_bits) {
 }
 
 // rint(x 2^shift): exact power-of-two scaling (|result| <= 2^24), then round
-// to nearest even.
-__device__ __forceinline__ int to_fixed(float x, int shift) { return __float2int_rn(ldexpf(x, shift)); }
+// to nearest even.  The scale is two power-of-two factors computed once per
+// row or column (each within the float exponent range for |shift| <= 252).
+// A product can round only when it falls below the normal range; for the
+// shifts this path makes (bits minus a float exponent: |shift| < 250) the
+// final value is then far below 1/2 and rounds to 0 either way, so the
+// result equals rint of the exact x 2^shift.
+struct Pow2Pair {
+  float a, b;
+};
+__device__ __forceinline__ Pow2Pair pow2_pair(int shift) {
+  const int s1 = shift >> 1;
+  return {pow2f(s1), pow2f(shift - s1)};
+}
+__device__ __forceinline__ int to_fixed(float x, const Pow2Pair& f) { return __float2int_rn((x * f.a) * f.b); }
 
 // Balanced base-2^w digits of x, most significant first: d[1..S-1] in
 // [-2^(w-1), 2^(w-1)), d[0] takes the rest.
@@ -134,10 +146,10 @@ exact_b_digits_kernel(const float* __restrict__ B, int K, int N, const uint32_t*
     const int r = t >> 3, kc = t & 7;
     const int n = n0 + r, k = k0 + 8 * kc;
     if (n >= N) continue;
-    const int shift = bits - exponent_of(amax_b[n]);
+    const Pow2Pair f = pow2_pair(bits - exponent_of(amax_b[n]));
     int dg[8][S];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) balanced_digits<S>(to_fixed(tile[8 * kc + q][r], shift), w, dg[q]);
+    for (int q = 0; q < 8; ++q) balanced_digits<S>(to_fixed(tile[8 * kc + q][r], f), w, dg[q]);
     __nv_bfloat16* dst = bt + static_cast<long long>(n) * row_len + k;
 #pragma unroll
     for (int l = 0; l < S; ++l)
@@ -167,7 +179,7 @@ exact_a_digits_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M,
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[l][q] = 0;
   if (k8 < K) {  // K % 8 == 0: a chunk is inside K or in the padding
-    const int shift = bits - exponent_of(amax_a[j]);
+    const Pow2Pair f = pow2_pair(bits - exponent_of(amax_a[j]));
     const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
     for (int e = e0; e < e1; ++e) {
       const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
@@ -178,7 +190,7 @@ exact_a_digits_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M,
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         int dg[S];
-        balanced_digits<S>(to_fixed(x[q], shift), w, dg);
+        balanced_digits<S>(to_fixed(x[q], f), w, dg);
 #pragma unroll
         for (int l = 0; l < S; ++l) acc[l][q] += dg[l];
       }
