@@ -294,6 +294,21 @@ def test_search_finds_codes_of_degree_four_to_six(libbpx):
         assert n <= o.bound_paterson(k, b, s) if s < k else n <= o.bound_k_equals_sigma(k, b)
 
 
+def test_search_finds_a_three_erasure_code(libbpx):
+    """An equal-height array BP-XOR code that tolerates three erased columns
+    with more than two data columns: the search finds [n, k, b] = [6, 3, 4]
+    at sigma = 4 (8 chains of 6 M moves; about half a minute on 8 host
+    threads), and the oracle's brute force confirms that every set of three
+    columns peels all 12 sources."""
+    bpx = libbpx
+    from oracle import bpx_oracle as o
+    code, used = bpx.Code.search(6, 3, 4, 4, iters=6000000, seed=7, threads=8)
+    assert code is not None, used
+    assert code.sigma == 4 and code.e == 3 and all(h == 4 for h in code.heights)
+    ref = o.code_from_columns("found", 3, 4, code.columns())
+    assert o.is_array_bpxor(ref) and ref.n - ref.k == 3
+
+
 @pytest.mark.parametrize("p", [3, 5, 7, 11, 13])
 def test_xcode_graph_matches_oracle(libbpx, p):
     """The library's X-code (built column by column) has the oracle's cells
