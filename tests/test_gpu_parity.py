@@ -157,6 +157,29 @@ def test_schedule_state_in_global_memory(libbpx):
         assert inf[bpx.INFO_WAVES] == sch.num_waves
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_whole_path_with_plan_state_in_global_memory(libbpx, prec):
+    """The whole path on a code whose plan state does not fit on chip
+    (Construction A n = 16, k = 12, b = 2800: 33600 one-row sources, ~45k
+    cells, ~2800 waves; the schedule keeps 64-bit cell words in global memory
+    and, as for every code of more than 4096 sources, plans in two parts, the
+    second beside the products): small-integer inputs decode to A B bit for
+    bit on every row, with the plan equal to the oracle's."""
+    bpx = libbpx
+    code, ref = _pair(bpx, "A16_12_2800")
+    h, K, N = 1, 64, 32
+    M = ref.num_sources * h - 5
+    A = W.matrix((M, K), "int", 51)
+    B = W.matrix((K, N), "int", 52)
+    exact = o.reference_product(A, B)
+    m = W.erasure_mask(code.n, 4, 4200)
+    C, info = _run(bpx, code, A, B, h, bpx.PRECISIONS[prec], m)
+    assert info[bpx.INFO_STATUS] == bpx.OK and info[bpx.INFO_WAVES] > 1000
+    assert np.array_equal(C[:M], exact)
+    sch = o.wave_schedule(ref, o.surviving_cells(ref, np.nonzero(m)[0]))
+    assert info[bpx.INFO_WAVES] == sch.num_waves and info[bpx.INFO_RECOVERED] == ref.num_sources
+
+
 # ---------------------------------------------------------------- a2: encode
 
 @pytest.mark.parametrize("name,h", [("table3", 3), ("sys8_3_8", 2), ("A7_4_10", 1)])
