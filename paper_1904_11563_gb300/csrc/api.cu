@@ -321,7 +321,8 @@ int products_impl(const bpx_code* c, const float* d_A, const float* d_B, int M, 
       e = bpx::launch_exact_b(d_B, K, N, P, amax + h, b_pl, st);
       stage_mark(opts, BPX_STAGE_B_PREP, 1, st);
       stage_mark(opts, BPX_STAGE_A_PREP, 0, st);
-      if (e == cudaSuccess) e = bpx::launch_exact_a(g, p, d_A, M, K, h, P, amax, a_pl, st);
+      if (e == cudaSuccess)
+        e = bpx::launch_exact_a(g, p, d_A, M, K, h, P, amax, a_pl, st, L.ex_src ? base + L.ex_src : nullptr);
       stage_mark(opts, BPX_STAGE_A_PREP, 1, st);
       stage_mark(opts, BPX_STAGE_GEMM, 0, st);
       if (e == cudaSuccess)

@@ -55,6 +55,9 @@ struct WsLayout {
   // exact-slice: max |A| per row position (h words) then max |B| per column
   // (N words), as float bits; decoded sources as exact int64 (S h N)
   size_t ex_amax, ex_c64;
+  // exact-slice, digits narrower than 8 bits: every source row's digit planes
+  // as int8, computed once (0 = no such region)
+  size_t ex_src;
   size_t total;
 };
 

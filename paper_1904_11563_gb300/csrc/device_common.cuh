@@ -297,8 +297,11 @@ cudaError_t launch_gemm_tc(const DevGraph& g, const DevPlan& p, const void* a_hi
 // position + coded A digit planes), digit-product GEMM and exact peel.
 cudaError_t launch_exact_b(const float* B, int K, int N, const ExactParams& P, uint32_t* amax_b, void* bt,
                            cudaStream_t st);
+// src_digits: the workspace's int8 source-digit region (ex_src) when the
+// layout has one, else nullptr.
 cudaError_t launch_exact_a(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
-                           const ExactParams& P, uint32_t* amax_a, void* a_planes, cudaStream_t st);
+                           const ExactParams& P, uint32_t* amax_a, void* a_planes, cudaStream_t st,
+                           void* src_digits = nullptr);
 cudaError_t launch_gemm_exact(const DevPlan& p, const void* a_planes, const void* b_planes, int num_cells, int N,
                               int K, int h, const ExactParams& P, int32_t* planes, int config, int32_t* info_out,
                               cudaStream_t st);

@@ -204,6 +204,113 @@ exact_a_digits_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M,
                    bf16x2_of(acc[l][4], acc[l][5]), bf16x2_of(acc[l][6], acc[l][7]));
 }
 
+// Digits narrower than 8 bits (S >= 4) of a code whose cells hold many
+// sources: the balanced digits of every source row are cut once, stored as
+// bytes biased by kBias(w) = 2^(w-1) + 1 (a digit lies in [-2^(w-1) - 1,
+// 2^(w-1) + 1], so the biased byte is in [0, 2^w + 2]), laid out per row and
+// 8-column chunk as S planes of 8 bytes.  The coded rows then add their
+// sources' biased bytes in 16-bit lanes of 32-bit words (two digits per add:
+// at most sigma (2^w + 2) <= 2^(9 - ceil(log2 sigma)) sigma + 2 sigma < 2^16,
+// so no lane carries into the next) and remove the bias once: the same
+// integer sums, so the same planes, without cutting every source element
+// again for each cell that holds it.
+template <int S>
+__global__ void __launch_bounds__(256)
+exact_src_digits_kernel(const float* __restrict__ A, int M, int K, int h, const uint32_t* __restrict__ amax_a,
+                        int w, int bits, int Kp, long long src_rows, uint8_t* out) {
+  const long long c = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x;  // (row, 8-column chunk)
+  const int per_row = Kp / 8;
+  const long long r = c / per_row;
+  if (r >= src_rows) return;
+  const int k8 = static_cast<int>(c - r * per_row) * 8;
+  float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (r < M && k8 < K) {  // K % 8 == 0: a chunk is inside K or in the padding
+    const float4* src = reinterpret_cast<const float4*>(A + r * K + k8);
+    const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+    x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+    x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+  }
+  const Pow2Pair f = pow2_pair(bits - exponent_of(amax_a[r % h]));
+  const int bias = (1 << (w - 1)) + 1;
+  uint32_t lo[S], hi[S];
+#pragma unroll
+  for (int l = 0; l < S; ++l) lo[l] = hi[l] = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int dg[S];
+    balanced_digits<S>(to_fixed(x[q], f), w, dg);
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+      const uint32_t b = static_cast<uint32_t>(dg[l] + bias);  // in [0, 2^w + 2]
+      if (q < 4)
+        lo[l] |= b << (8 * q);
+      else
+        hi[l] |= b << (8 * (q - 4));
+    }
+  }
+  uint2* dst = reinterpret_cast<uint2*>(out) + c * S;
+#pragma unroll
+  for (int l = 0; l < S; ++l) dst[l] = make_uint2(lo[l], hi[l]);
+}
+
+// The coded digit planes from the int8 source digits (same grid as
+// exact_a_digits_kernel).
+template <int S>
+__global__ void __launch_bounds__(kExThreads)
+exact_a_digits_src_kernel(DevGraph g, DevPlan p, const uint8_t* __restrict__ src_digits, int M, int h, int Kp,
+                          int K, int w, __nv_bfloat16* out) {
+  const int tpr = enc_threads_per_row(Kp);
+  const int row = blockIdx.x * (kExThreads / tpr) + threadIdx.x / tpr;
+  const int nsurv = p.ctr[CTR_NSURV];
+  if (row >= nsurv * h) return;
+  const int ci = row / h, j = row - ci * h;
+  const int cell = p.surv[ci];
+  const int k8 = (blockIdx.y * tpr + threadIdx.x % tpr) * 8;
+  if (k8 >= Kp) return;
+  // per plane, four words of two 16-bit lanes: columns (0, 2), (1, 3), (4, 6), (5, 7)
+  uint32_t acc[S][4];
+#pragma unroll
+  for (int l = 0; l < S; ++l)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[l][q] = 0u;
+  int count = 0;
+  if (k8 < K) {
+    const int per_row = Kp / 8;
+    const int e0 = g.cell_ptr[cell], e1 = g.cell_ptr[cell + 1];
+    for (int e = e0; e < e1; ++e) {
+      const long long arow = static_cast<long long>(__ldg(g.cell_src + e)) * h + j;
+      if (arow >= M) continue;
+      ++count;
+      const uint2* src = reinterpret_cast<const uint2*>(src_digits) + (arow * per_row + k8 / 8) * S;
+      uint2 v[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) v[l] = __ldg(src + l);
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        acc[l][0] += __byte_perm(v[l].x, 0u, 0x4240);  // bytes 0, 2 into the two lanes
+        acc[l][1] += __byte_perm(v[l].x, 0u, 0x4341);  // bytes 1, 3
+        acc[l][2] += __byte_perm(v[l].y, 0u, 0x4240);
+        acc[l][3] += __byte_perm(v[l].y, 0u, 0x4341);
+      }
+    }
+  }
+  const int off = count * ((1 << (w - 1)) + 1);  // the bias of every summed digit
+  __nv_bfloat16* dst = out + static_cast<long long>(row) * S * Kp + k8;
+#pragma unroll
+  for (int l = 0; l < S; ++l) {
+    int d[8];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      d[4 * q + 0] = static_cast<int>(acc[l][2 * q] & 0xffffu) - off;
+      d[4 * q + 2] = static_cast<int>(acc[l][2 * q] >> 16) - off;
+      d[4 * q + 1] = static_cast<int>(acc[l][2 * q + 1] & 0xffffu) - off;
+      d[4 * q + 3] = static_cast<int>(acc[l][2 * q + 1] >> 16) - off;
+    }
+    *reinterpret_cast<uint4*>(dst + static_cast<long long>(l) * Kp) =
+        make_uint4(bf16x2_of(d[0], d[1]), bf16x2_of(d[2], d[3]), bf16x2_of(d[4], d[5]), bf16x2_of(d[6], d[7]));
+  }
+}
+
 // Peel on exact integers.  As in the FP32 peel, each CTA owns one slice of
 // the block's 4-element groups and walks every wave over it; __syncthreads
 // between waves is the only synchronisation.
@@ -305,13 +412,47 @@ cudaError_t launch_exact_b(const float* B, int K, int N, const ExactParams& P, u
 }
 
 cudaError_t launch_exact_a(const DevGraph& g, const DevPlan& p, const float* A, int M, int K, int h,
-                           const ExactParams& P, uint32_t* amax_a, void* a_planes, cudaStream_t st) {
+                           const ExactParams& P, uint32_t* amax_a, void* a_planes, cudaStream_t st,
+                           void* src_digits) {
   cudaError_t e = cudaMemsetAsync(amax_a, 0, sizeof(uint32_t) * h, st);
   if (e != cudaSuccess) return e;
   if (M > 0) exact_amax_a_kernel<<<(M + 7) / 8, 256, 0, st>>>(A, M, K, h, amax_a);
   const long long rows = static_cast<long long>(g.num_cells) * h;
   const dim3 grid(static_cast<unsigned>(enc_row_blocks(rows, P.Kp)), enc_k_chunks(P.Kp));
   auto* out = static_cast<__nv_bfloat16*>(a_planes);
+  // the source-digit form pays off when cells hold many sources (a source row
+  // is cut once instead of once per cell that holds it)
+  if (src_digits && P.S >= 4 && static_cast<long long>(g.num_edges) >= 4LL * g.num_cells) {
+    const long long src_rows = static_cast<long long>(g.S) * h;
+    const long long chunks = src_rows * (P.Kp / 8);
+    if ((chunks + 255) / 256 > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned sg = static_cast<unsigned>((chunks + 255) / 256);
+    auto* sd = static_cast<uint8_t*>(src_digits);
+    switch (P.S) {
+      case 4:
+        exact_src_digits_kernel<4><<<sg, 256, 0, st>>>(A, M, K, h, amax_a, P.w, P.bits, P.Kp, src_rows, sd);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        exact_a_digits_src_kernel<4><<<grid, kExThreads, 0, st>>>(g, p, sd, M, h, P.Kp, K, P.w, out);
+        break;
+      case 5:
+        exact_src_digits_kernel<5><<<sg, 256, 0, st>>>(A, M, K, h, amax_a, P.w, P.bits, P.Kp, src_rows, sd);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        exact_a_digits_src_kernel<5><<<grid, kExThreads, 0, st>>>(g, p, sd, M, h, P.Kp, K, P.w, out);
+        break;
+      case 6:
+        exact_src_digits_kernel<6><<<sg, 256, 0, st>>>(A, M, K, h, amax_a, P.w, P.bits, P.Kp, src_rows, sd);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        exact_a_digits_src_kernel<6><<<grid, kExThreads, 0, st>>>(g, p, sd, M, h, P.Kp, K, P.w, out);
+        break;
+      case 8:
+        exact_src_digits_kernel<8><<<sg, 256, 0, st>>>(A, M, K, h, amax_a, P.w, P.bits, P.Kp, src_rows, sd);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        exact_a_digits_src_kernel<8><<<grid, kExThreads, 0, st>>>(g, p, sd, M, h, P.Kp, K, P.w, out);
+        break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (P.S) {
     case 3: exact_a_digits_kernel<3><<<grid, kExThreads, 0, st>>>(g, p, A, M, K, h, amax_a, P.w, P.bits, P.Kp, out); break;
     case 4: exact_a_digits_kernel<4><<<grid, kExThreads, 0, st>>>(g, p, A, M, K, h, amax_a, P.w, P.bits, P.Kp, out); break;

@@ -116,6 +116,26 @@ def test_exact_tall_code(libbpx, peel_ctas):
     _assert_bits(C, R, sch, h, M, ("A12_9_120", peel_ctas))
 
 
+@pytest.mark.parametrize("args,e", [((7, 6, 32), 1), ((24, 18, 40), 6)])
+def test_exact_source_digit_form(libbpx, args, e):
+    """Codes whose cells hold four or more sources on average cut each source
+    row's digits once (int8, biased) and sum them per coded row in 16-bit
+    lanes: Construction A [7, 6, 32] (sigma 6: 6-bit digits, S = 4) and
+    [24, 18, 40] (sigma 18: 4-bit digits, S = 6), M short of S h, K with a
+    padded tail: bit for bit equal to the oracle's exact-slice decode."""
+    bpx = libbpx
+    code, ref = bpx.Code.mojette_a(*args), o.construction_a(*args)
+    assert len(code.cell_src) >= 4 * code.num_cells
+    h, K, N = 2, 136, 68
+    M = ref.num_sources * h - 3
+    A, B = W.inputs(M, K, N, "normal", 71)
+    m = W.erasure_mask(ref.n, e, 9)
+    C, info = _run(bpx, code, A, B, h, m)
+    R, _Q, sch = o.exact_slice_coded_matmul(ref, A, B, h, list(np.nonzero(m)[0]))
+    assert sch.ok and info[bpx.INFO_STATUS] == bpx.OK
+    _assert_bits(C, R, sch, h, M, args)
+
+
 def test_exact_planes_then_peel(libbpx):
     """a3 alone: the S int32 diagonal planes of every surviving cell equal
     the oracle's exact digit products; then a4 alone from those planes."""
