@@ -451,9 +451,11 @@ WsLayout ws_layout(const bpx_code* c, int M, int N, int K, int h, int precision,
     take((planes - 1) * C * hN * sizeof(int32_t));  // products: S int32 planes from L.products on
     L.a_hi = take(rowsA * planes * kp * 2);
     L.b_hi = take(Np * planes * kp * 2);
-    // digits of at most 7 bits (S >= 4) fit int8: each source row's planes are
-    // cut once, then summed per coded row
-    if (P.S >= 4) L.ex_src = take(S * static_cast<size_t>(h > 0 ? h : 0) * planes * kp);
+    // digits of at most 7 bits (S >= 4) fit a byte: for codes whose cells hold
+    // four or more sources on average each source row's planes are cut once,
+    // then summed per coded row
+    if (P.S >= 4 && c->num_edges >= 4LL * c->num_cells)
+      L.ex_src = take(S * static_cast<size_t>(h > 0 ? h : 0) * planes * kp);
   } else if (precision == BPX_MXFP8) {
     // E4M3 operands (K-major rows) and UE8M0 scales, one per 32 K-elements,
     // stored per (tile, 128-wide K stage) in the order the GEMM copies them
