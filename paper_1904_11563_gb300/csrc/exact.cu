@@ -206,14 +206,14 @@ exact_a_digits_kernel(DevGraph g, DevPlan p, const float* __restrict__ A, int M,
 
 // Digits narrower than 8 bits (S >= 4) of a code whose cells hold many
 // sources: the balanced digits of every source row are cut once, stored as
-// bytes biased by kBias(w) = 2^(w-1) + 1 (a digit lies in [-2^(w-1) - 1,
-// 2^(w-1) + 1], so the biased byte is in [0, 2^w + 2]), laid out per row and
-// 8-column chunk as S planes of 8 bytes.  The coded rows then add their
-// sources' biased bytes in 16-bit lanes of 32-bit words (two digits per add:
-// at most sigma (2^w + 2) <= 2^(9 - ceil(log2 sigma)) sigma + 2 sigma < 2^16,
-// so no lane carries into the next) and remove the bias once: the same
-// integer sums, so the same planes, without cutting every source element
-// again for each cell that holds it.
+// bytes biased by 2^(w-1) + 1 (a digit lies in [-2^(w-1) - 1, 2^(w-1) + 1],
+// so the biased byte is in [0, 2^w + 2]), laid out per row and 8-column
+// chunk as S planes of 8 bytes.  The coded rows then add their sources'
+// biased bytes in 16-bit lanes of 32-bit words, two digits per add: a lane
+// reaches at most sigma (2^w + 2) <= 512 + 128 (w <= 9 - ceil(log2 sigma),
+// sigma <= 64), far below 2^16, so no lane carries into the next.  The bias
+// comes off once per sum: the same integers, so the same planes, without
+// cutting every source element again for each cell that holds it.
 template <int S>
 __global__ void __launch_bounds__(256)
 exact_src_digits_kernel(const float* __restrict__ A, int M, int K, int h, const uint32_t* __restrict__ amax_a,
@@ -253,7 +253,7 @@ exact_src_digits_kernel(const float* __restrict__ A, int M, int K, int h, const 
   for (int l = 0; l < S; ++l) dst[l] = make_uint2(lo[l], hi[l]);
 }
 
-// The coded digit planes from the int8 source digits (same grid as
+// The coded digit planes from the biased source-digit bytes (same grid as
 // exact_a_digits_kernel).
 template <int S>
 __global__ void __launch_bounds__(kExThreads)
